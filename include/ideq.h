@@ -1,0 +1,226 @@
+/*
+ * ideq.h -- C ABI of the GB300 (sm_103a) i-DEQ restoration library.
+ *
+ * The library computes the inertial deep-equilibrium restoration of the paper
+ * "i-DEQ: a stable inertial deep equilibrium model for image restoration":
+ * given observations y = A(x) + n, a forward model A with adjoint, and the
+ * parameters Theta = {theta, lambda, tau, alpha}, it returns the fixed point
+ * x_hat of T = T^RED o T^M (Sec. 3.1, Eq. ideq; Algorithm 1), and for training
+ * the gradient of a loss of x_hat with respect to theta and lambda by implicit
+ * differentiation (App. D.1.2).
+ *
+ * Conventions shared by every entry point
+ *   - Images are float32, planar NCHW, contiguous: x[((b*c + ch)*h + i)*w + j].
+ *   - Every pointer argument is DEVICE memory owned by the caller unless the
+ *     comment says "host".  The context owns only its scratch workspace.
+ *   - Every call is asynchronous and ordered on the context's CUDA stream.
+ *     Argument and shape errors are returned synchronously; per-image
+ *     outcomes (converged / iteration cap / diverged) are written to the
+ *     ideq_info arrays and are valid after the stream is synchronised.
+ *   - No call aborts, exits or traps the device.  Device-side waits are
+ *     bounded; an expired wait is reported as IDEQ_ERR_TIMEOUT.
+ *   - A context is used by one host thread at a time.
+ */
+#ifndef IDEQ_H
+#define IDEQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ideq_ctx ideq_ctx;
+
+typedef enum {
+  IDEQ_OK = 0,
+  IDEQ_ERR_ARG = 1,          /* invalid argument or shape                         */
+  IDEQ_ERR_CUDA = 2,         /* a CUDA runtime/driver call failed                  */
+  IDEQ_ERR_NOMEM = 3,        /* workspace allocation failed                        */
+  IDEQ_ERR_UNSUPPORTED = 4,  /* valid request the library does not implement       */
+  IDEQ_MAXITER = 5,          /* ideq_solve: some image hit max_iter                 */
+  IDEQ_DIVERGED = 6,         /* some image produced a non-finite step              */
+  IDEQ_ADJ_MAXITER = 7,      /* ideq_solve_backward: adjoint solve hit its cap      */
+  IDEQ_ERR_TIMEOUT = 8       /* a bounded device-side wait expired                 */
+} ideq_status;
+
+/* per-image outcome codes written to ideq_info.status */
+enum { IDEQ_IMG_RUNNING = 0, IDEQ_IMG_CONVERGED = 1, IDEQ_IMG_MAXITER = 2, IDEQ_IMG_DIVERGED = 3 };
+
+enum { IDEQ_NET_CNN = 0, IDEQ_NET_UNET = 1 };
+enum { IDEQ_ACT_SOFTPLUS = 0, IDEQ_ACT_RELU = 1 };
+enum { IDEQ_OP_BLUR = 0, IDEQ_OP_MASK = 1, IDEQ_OP_SATBLUR = 2 };
+/* arithmetic of the regulariser network's convolutions; the iterate, the
+ * momentum state and the data step are always float32, the step-norm and
+ * energy reductions float64. */
+enum { IDEQ_FP32 = 0, IDEQ_BF16 = 1, IDEQ_BF16_FP8 = 2 };
+enum { IDEQ_INIT_ATY = 0, IDEQ_INIT_X0 = 1, IDEQ_INIT_WARM = 2 };
+enum { IDEQ_ADJ_JFB = 0, IDEQ_ADJ_IMPLICIT = 1 };
+
+/* Regulariser network N in g(x) = 1/2 ||x - N(x)||^2 (Sec. 2.2, Eq. GS).
+ *  IDEQ_NET_UNET: head 3x3 in_ch->widths[0]; per scale l < n_levels-1: n_rb
+ *    residual blocks (3x3 conv, activation, 3x3 conv, identity skip), then a
+ *    2x2 stride-2 conv widths[l]->widths[l+1]; n_rb blocks at the coarsest
+ *    scale; per decoder scale (coarse to fine): 2x2 stride-2 transposed conv
+ *    widths[l+1]->widths[l], plus the encoder output of scale l, n_rb blocks;
+ *    tail 3x3 widths[0]->in_ch.  No biases, zero "same" padding.
+ *  IDEQ_NET_CNN: depth 3x3 convs widths[0]->widths[1]->...->widths[depth],
+ *    activation after every conv but the last; widths[0] = widths[depth] = in_ch.
+ * Weight vector (float32): tensors in the order above (U-Net: head; per
+ * encoder scale rb0.c1, rb0.c2, ..., down; coarsest rbs; per decoder scale up,
+ * rbs; tail), each contiguous in PyTorch order: 3x3 and 2x2 convs
+ * [C_out][C_in][kh][kw], transposed convs [C_in][C_out][2][2]. */
+typedef struct {
+  int kind;        /* IDEQ_NET_CNN or IDEQ_NET_UNET                         */
+  int act;         /* IDEQ_ACT_SOFTPLUS or IDEQ_ACT_RELU                    */
+  int in_ch;       /* image channels c (1 or 3)                             */
+  int n_levels;    /* U-Net scales (>= 1, <= 6)                             */
+  int n_rb;        /* U-Net residual blocks per scale                       */
+  int depth;       /* CNN: number of conv layers (<= 15)                    */
+  int widths[16];  /* U-Net: width per scale; CNN: channel list             */
+} ideq_net_desc;
+
+typedef struct { int n, c, h, w; } ideq_shape;  /* batch, channels, height, width */
+
+/* Forward model A of one batch (App. E forms; the blur and saturation models
+ * are synthetic stand-ins of the same structure):
+ *  IDEQ_OP_BLUR    A x = k_b * x, circular convolution with per-image kernel
+ *                  k_b (centre (kh/2, kw/2)), shared by the channels.
+ *  IDEQ_OP_MASK    A x = M_b . x, per-pixel 0/1 mask shared by the channels.
+ *  IDEQ_OP_SATBLUR A x = tanh(s (k_b * x)) / tanh(s), s = sat_gain.       */
+typedef struct {
+  int kind;
+  int kh, kw;              /* odd kernel sizes (<= 31) for blur kinds        */
+  const float *kernel;     /* device, n*kh*kw, row-major per image            */
+  const uint8_t *mask;     /* device, n*h*w, values 0/1 (mask kind)           */
+  float sat_gain;          /* s for IDEQ_OP_SATBLUR                           */
+} ideq_operator;
+
+/* Parameters of the inertial iteration (Algorithm 1; beta = 1 - alpha of
+ * Eq. Momentum).  restart_B <= 0 or non-finite disables the restart test of
+ * Eq. restart.  tol > 0 stops an image once ||x^{k+1}-x^k|| < tol ||x^k||
+ * (App. D.1.3); tol = 0 runs exactly max_iter updates.  The output is the
+ * last iterate (Remark 1). */
+typedef struct {
+  float lambda, tau, beta, restart_B;
+  double tol;
+  int max_iter;
+  int init;               /* IDEQ_INIT_ATY, IDEQ_INIT_X0 (x0 given) or IDEQ_INIT_WARM */
+} ideq_params;
+
+/* Per-image results, device arrays of length n; any member may be NULL. */
+typedef struct {
+  int *iters;       /* updates performed (restarts do not reset it)          */
+  int *restarts;    /* number of restarts                                    */
+  int *status;      /* IDEQ_IMG_*                                            */
+  double *rel_res;  /* last ||x^{k+1}-x^k|| / ||x^k||                          */
+  double *energy;   /* F(z) = f(z) + lambda g(z) at the last extrapolated point */
+} ideq_info;
+
+/* Adjoint (backward) solve parameters (App. D.1.2).  IDEQ_ADJ_JFB uses the
+ * Jacobian-free estimate u = v; IDEQ_ADJ_IMPLICIT iterates u <- J_R^T u + v
+ * (heavy-ball with beta) until ||u^{k+1}-u^k|| < tol ||u^k|| per image. */
+typedef struct {
+  int mode;
+  double tol;
+  int max_iter;
+  float beta;
+} ideq_adj_params;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on the current CUDA device.  `weights` (device, float32)
+ * is copied; `precision` selects the convolution arithmetic; `stream` is a
+ * cudaStream_t (NULL = legacy default stream). */
+ideq_status ideq_create(ideq_ctx **ctx, const ideq_net_desc *net, const float *weights,
+                        int precision, void *stream);
+ideq_status ideq_destroy(ideq_ctx *ctx);
+/* Replace the network weights (device float32, same layout); async. */
+ideq_status ideq_set_weights(ideq_ctx *ctx, const float *weights);
+ideq_status ideq_set_precision(ideq_ctx *ctx, int precision);
+ideq_status ideq_set_stream(ideq_ctx *ctx, void *stream);
+/* Number of float32 entries of the network weight vector. */
+ideq_status ideq_num_params(const ideq_net_desc *net, int64_t *count);
+/* Last error message of the context (host string, valid until the next call). */
+const char *ideq_last_error(ideq_ctx *ctx);
+
+/* ---- forward model (Sec. 1 Eq. inv_prob; App. E) ------------------------- */
+
+/* Ax = A(x). */
+ideq_status ideq_apply_A(ideq_ctx *ctx, const ideq_operator *op, ideq_shape shape,
+                         const float *x, float *Ax);
+/* out = A^T r for linear A; out = J_A(lin_point)^T r when lin_point != NULL
+ * (required for the saturation model's Jacobian; A^T of its linear part
+ * k^T (.) when NULL). */
+ideq_status ideq_apply_AT(ideq_ctx *ctx, const ideq_operator *op, ideq_shape shape,
+                          const float *r, const float *lin_point, float *out);
+
+/* ---- regulariser (Eq. GS) ------------------------------------------------ */
+
+/* grad = grad g(z) = r - J_N(z)^T r with r = z - N(z); g_val (device, n
+ * doubles, nullable) receives g(z) = 1/2 ||r||^2 per image. */
+ideq_status ideq_grad_reg(ideq_ctx *ctx, ideq_shape shape, const float *z, float *grad,
+                          double *g_val);
+
+/* ---- iteration (Algorithm 1) --------------------------------------------- */
+
+/* One inertial RED update of every image, in place:
+ *   z = x_k + beta (x_k - x_km1),  x_{k+1} = z - tau (grad f(z, y) + lambda grad g(z)),
+ * then x_km1 <- x_k and x_k <- x_{k+1}.  info.rel_res and info.energy are
+ * filled; no restart or stopping logic is applied. */
+ideq_status ideq_step(ideq_ctx *ctx, const ideq_operator *op, ideq_shape shape,
+                      const float *y, float *x_k, float *x_km1, const ideq_params *p,
+                      ideq_info *info);
+
+/* Full solve from x0 = A^T y (IDEQ_INIT_ATY), the given x0 (IDEQ_INIT_X0) or
+ * the warm start (IDEQ_INIT_WARM) with restart, per-image stopping and
+ * freezing.  Returns IDEQ_MAXITER / IDEQ_DIVERGED if any image ended so
+ * (this return synchronises the stream). */
+ideq_status ideq_solve(ideq_ctx *ctx, const ideq_operator *op, ideq_shape shape,
+                       const float *y, const float *x0, float *x_out, const ideq_params *p,
+                       ideq_info *info);
+
+/* ---- implicit backward (App. D.1.2) -------------------------------------- */
+
+/* Given the fixed point x_bar and v = dl/dx_bar, computes
+ *   dl_dtheta (device, ideq_num_params floats) = -tau lambda (d grad g(x_bar)/d theta)^T u
+ *   dl_dlambda (device, 1 float)              = -tau <u, grad g(x_bar)>
+ * summed over the batch, with u from the adjoint solve (or u = v for JFB).
+ * info.iters receives the adjoint iterations per image.  Linear operators
+ * (blur, mask) only. */
+ideq_status ideq_solve_backward(ideq_ctx *ctx, const ideq_operator *op, ideq_shape shape,
+                                const float *y, const float *x_bar, const float *dl_dx,
+                                const ideq_params *p, const ideq_adj_params *ap,
+                                float *dl_dtheta, float *dl_dlambda, ideq_info *info);
+
+/* ---- learned warm start x0 = A^T y + W(A^T y) ----------------------------- */
+/* Not in the paper, which leaves x^0 free (Algorithm 1).  W is an
+ * IDEQ_NET_CNN network with its own weights and Adam state in the context. */
+
+ideq_status ideq_warm_set(ideq_ctx *ctx, const ideq_net_desc *net, const float *weights);
+/* x0 = aty + W(aty). */
+ideq_status ideq_warm_forward(ideq_ctx *ctx, ideq_shape shape, const float *aty, float *x0);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the mean squared error
+ * of x0 against target; loss (device, 1 double, nullable) receives the loss
+ * before the step. */
+ideq_status ideq_warm_train_step(ideq_ctx *ctx, ideq_shape shape, const float *aty,
+                                 const float *target, float lr, double *loss);
+/* Copy the warm-start weights (device float32). */
+ideq_status ideq_warm_get(ideq_ctx *ctx, float *weights);
+
+/* ---- instrumentation ------------------------------------------------------ */
+
+/* When enabled, CUDA events bracket every launch of the tensor-core
+ * convolution kernel on the context's stream; ideq_prof_read returns their
+ * summed duration (ms), the launch count and the summed algorithmic FLOPs
+ * since the last read, and resets them (synchronises the stream). */
+ideq_status ideq_prof_enable(ideq_ctx *ctx, int on);
+ideq_status ideq_prof_read(ideq_ctx *ctx, double *ms, int64_t *launches, double *flops);
+/* Number of kernels this context launched since the last call (host count). */
+ideq_status ideq_launch_count(ideq_ctx *ctx, int64_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IDEQ_H */

@@ -1,0 +1,452 @@
+// C ABI of the i-DEQ library: context, forward model, regulariser gradient,
+// single step and full inertial solve (Algorithm 1).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+
+#include "net.h"
+
+using namespace ideq;
+
+struct ideq_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int precision = IDEQ_FP32;
+  std::unique_ptr<NetWeights> w;
+  std::unique_ptr<NetPlan> plan;
+  std::string err;
+  int* d_err = nullptr;       // device error flag of bounded waits
+  int* h_running = nullptr;   // pinned
+  Profiler prof;
+  long long launches = 0;
+  // solver workspace (sized for the current plan)
+  int sv_n = 0, sv_per = 0, sv_nblk = 0;
+  void* sv_mem = nullptr;
+  SolverDev sv{};
+  float* xb[2] = {nullptr, nullptr};
+  float* gf = nullptr;
+  float* tmp = nullptr;
+  double* fsum = nullptr;
+  double* gsum = nullptr;
+  // scratch for the stand-alone operator calls
+  float* scratch = nullptr;
+  size_t scratch_bytes = 0;
+};
+
+namespace {
+
+ideq_status fail(ideq_ctx* c, ideq_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+ideq_status cuda_fail(ideq_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, IDEQ_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                          \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+bool shape_ok(const ideq_shape& s) {
+  return s.n > 0 && s.c > 0 && s.h > 0 && s.w > 0 && (long long)s.n * s.c * s.h * s.w < (1LL << 40);
+}
+
+ideq_status check_op(ideq_ctx* ctx, const ideq_operator* op, const ideq_shape& s, OpDev* od) {
+  if (!op) return fail(ctx, IDEQ_ERR_ARG, "operator is NULL");
+  od->kind = op->kind;
+  od->kh = op->kh;
+  od->kw = op->kw;
+  od->kernel = op->kernel;
+  od->mask = op->mask;
+  od->gain = op->sat_gain;
+  if (op->kind == IDEQ_OP_BLUR || op->kind == IDEQ_OP_SATBLUR) {
+    if (!op->kernel) return fail(ctx, IDEQ_ERR_ARG, "blur operator needs a kernel");
+    if (op->kh < 1 || op->kw < 1 || op->kh > 31 || op->kw > 31 || !(op->kh & 1) || !(op->kw & 1))
+      return fail(ctx, IDEQ_ERR_ARG, "kernel sizes must be odd and <= 31");
+    if (op->kh > s.h || op->kw > s.w) return fail(ctx, IDEQ_ERR_ARG, "kernel larger than image");
+    if (op->kind == IDEQ_OP_SATBLUR && !(op->sat_gain > 0.f))
+      return fail(ctx, IDEQ_ERR_ARG, "sat_gain must be > 0");
+  } else if (op->kind == IDEQ_OP_MASK) {
+    if (!op->mask) return fail(ctx, IDEQ_ERR_ARG, "mask operator needs a mask");
+  } else {
+    return fail(ctx, IDEQ_ERR_ARG, "unknown operator kind");
+  }
+  return IDEQ_OK;
+}
+
+ideq_status ensure_plan(ideq_ctx* ctx, const ideq_shape& s) {
+  if (s.c != ctx->w->desc.in_ch) return fail(ctx, IDEQ_ERR_ARG, "channels differ from the network's in_ch");
+  NetPlan* p = ctx->plan.get();
+  if (p && p->n == s.n && p->H == s.h && p->W == s.w && p->prec == ctx->precision) return IDEQ_OK;
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->plan.reset();
+  // solver workspace
+  if (ctx->sv_mem) {
+    cudaFree(ctx->sv_mem);
+    ctx->sv_mem = nullptr;
+  }
+  const int n = s.n, per = s.c * s.h * s.w;
+  const int nblk = update_blocks_per_image(per);
+  const size_t img = (size_t)n * per * 4;
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    const size_t o = off;
+    off += (b + 255) & ~(size_t)255;
+    return o;
+  };
+  const size_t o_x0 = take(img), o_x1 = take(img), o_gf = take(img), o_tmp = take(img);
+  const size_t o_i = take((size_t)n * 4 * 6), o_f = take((size_t)n * 4), o_d = take((size_t)n * 8 * 6);
+  const size_t o_p = take((size_t)n * nblk * 8 * 2), o_r = take(16);
+  char* m = nullptr;
+  if (cudaMalloc((void**)&m, off) != cudaSuccess) return fail(ctx, IDEQ_ERR_NOMEM, "cudaMalloc(solver workspace)");
+  ctx->sv_mem = m;
+  ctx->xb[0] = (float*)(m + o_x0);
+  ctx->xb[1] = (float*)(m + o_x1);
+  ctx->gf = (float*)(m + o_gf);
+  ctx->tmp = (float*)(m + o_tmp);
+  int* ip = (int*)(m + o_i);
+  SolverDev& v = ctx->sv;
+  v.k = ip;
+  v.total = ip + n;
+  v.restarts = ip + 2 * n;
+  v.status = ip + 3 * n;
+  v.parity = ip + 4 * n;
+  v.beta_eff = (float*)(m + o_f);
+  double* dp = (double*)(m + o_d);
+  v.S = dp;
+  v.rel = dp + n;
+  v.fsum = dp + 2 * n;
+  v.gsum = dp + 3 * n;
+  v.energy = dp + 4 * n;
+  v.part_s = (double*)(m + o_p);
+  v.part_x = v.part_s + (size_t)n * nblk;
+  v.n_running = (int*)(m + o_r);
+  ctx->fsum = v.fsum;
+  ctx->gsum = v.gsum;
+  ctx->sv_n = n;
+  ctx->sv_per = per;
+  ctx->sv_nblk = nblk;
+  CK(cudaMemsetAsync(m, 0, off, ctx->stream));
+  std::unique_ptr<NetPlan> np(new NetPlan());
+  std::string e;
+  if (!np->build(ctx->w.get(), s.n, s.h, s.w, ctx->precision, v.gsum, &e))
+    return fail(ctx, IDEQ_ERR_UNSUPPORTED, "plan: " + e);
+  ctx->plan = std::move(np);
+  return IDEQ_OK;
+}
+
+float* ensure_scratch(ideq_ctx* ctx, size_t bytes) {
+  if (ctx->scratch_bytes >= bytes) return ctx->scratch;
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->scratch) cudaFree(ctx->scratch);
+  ctx->scratch = nullptr;
+  ctx->scratch_bytes = 0;
+  if (cudaMalloc((void**)&ctx->scratch, bytes) != cudaSuccess) return nullptr;
+  ctx->scratch_bytes = bytes;
+  return ctx->scratch;
+}
+
+// grad f(z) = J_A(z)^T (A(z) - y) into gf, 1/2||A z - y||^2 into fsum.
+cudaError_t data_grad(ideq_ctx* ctx, const OpDev& od, const ideq_shape& s, const float* z,
+                      const float* y, float* gf, float* tmp, double* fsum) {
+  cudaStream_t st = ctx->stream;
+  if (od.kind == IDEQ_OP_MASK) {
+    ctx->launches += 1;
+    return launch_data_fwd(od, s.n, s.c, s.h, s.w, z, y, gf, fsum, st);
+  }
+  cudaError_t e = launch_data_fwd(od, s.n, s.c, s.h, s.w, z, y, tmp, fsum, st);
+  if (e != cudaSuccess) return e;
+  ctx->launches += 2;
+  return launch_blur_adj(od, s.n, s.c, s.h, s.w, tmp, gf, st);
+}
+
+// A^T y (adjoint of the linear part; the initial point x0 = A^T y).
+cudaError_t back_project(ideq_ctx* ctx, const OpDev& od, const ideq_shape& s, const float* y,
+                         float* out) {
+  ctx->launches += 1;
+  if (od.kind == IDEQ_OP_MASK) return launch_apply_A(od, s.n, s.c, s.h, s.w, y, out, ctx->stream);
+  return launch_blur_adj(od, s.n, s.c, s.h, s.w, y, out, ctx->stream);
+}
+
+// One iteration of Algorithm 1 on the plan buffers: x in xb[p], x_prev in
+// xb[1-p]; the update is written into xb[1-p].
+ideq_status iterate(ideq_ctx* ctx, const OpDev& od, const ideq_shape& s, const float* y,
+                    const ideq_params* p, int par, int logic) {
+  NetPlan* P = ctx->plan.get();
+  cudaStream_t st = ctx->stream;
+  const int n = s.n, per = ctx->sv_per;
+  float* x = ctx->xb[par];
+  float* xp = ctx->xb[1 - par];
+  CK(launch_extrapolate(n, per, x, xp, ctx->sv.beta_eff, P->z, st));
+  CK(run_steps(P->fwd, ctx->d_err, st, &ctx->prof, &ctx->launches));
+  CK(run_steps(P->vjp, ctx->d_err, st, &ctx->prof, &ctx->launches));
+  CK(data_grad(ctx, od, s, P->z, y, ctx->gf, ctx->tmp, ctx->sv.fsum));
+  CK(launch_red_update(n, per, ctx->sv_nblk, P->z, ctx->gf, P->grad, x, xp, p->lambda, p->tau,
+                       ctx->sv.status, ctx->sv.part_s, ctx->sv.part_x, st));
+  const float B = (std::isfinite(p->restart_B) && p->restart_B > 0.f) ? p->restart_B : INFINITY;
+  CK(launch_finalize(n, ctx->sv_nblk, ctx->sv, 1 - par, p->beta, B, p->tol, p->max_iter,
+                     p->lambda, logic, st));
+  ctx->launches += 3;
+  return IDEQ_OK;
+}
+
+ideq_status check_timeout(ideq_ctx* ctx) {
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (h != 0) {
+    cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream);
+    return fail(ctx, IDEQ_ERR_TIMEOUT, "tensor-core kernel wait expired (code " + std::to_string(h) + ")");
+  }
+  return IDEQ_OK;
+}
+
+ideq_status check_params(ideq_ctx* ctx, const ideq_params* p) {
+  if (!p) return fail(ctx, IDEQ_ERR_ARG, "params is NULL");
+  if (!(p->tau > 0.f) || !(p->lambda >= 0.f) || !(p->beta >= 0.f && p->beta < 1.f))
+    return fail(ctx, IDEQ_ERR_ARG, "need tau > 0, lambda >= 0, 0 <= beta < 1");
+  if (p->max_iter < 1) return fail(ctx, IDEQ_ERR_ARG, "max_iter must be >= 1");
+  if (!(p->tol >= 0.0)) return fail(ctx, IDEQ_ERR_ARG, "tol must be >= 0");
+  return IDEQ_OK;
+}
+
+}  // namespace
+
+// =========================================================================== C ABI
+
+extern "C" {
+
+ideq_status ideq_num_params(const ideq_net_desc* net, int64_t* count) {
+  if (!net || !count) return IDEQ_ERR_ARG;
+  long long c = 0;
+  std::string e;
+  if (!net_param_count(*net, &c, nullptr, &e)) return IDEQ_ERR_ARG;
+  *count = c;
+  return IDEQ_OK;
+}
+
+ideq_status ideq_create(ideq_ctx** out, const ideq_net_desc* net, const float* weights,
+                        int precision, void* stream) {
+  if (!out || !net || !weights) return IDEQ_ERR_ARG;
+  if (precision != IDEQ_FP32 && precision != IDEQ_BF16) return IDEQ_ERR_UNSUPPORTED;
+  std::unique_ptr<ideq_ctx> c(new ideq_ctx());
+  ideq_ctx* ctx = c.get();
+  CK(cudaGetDevice(&c->device));
+  c->stream = (cudaStream_t)stream;
+  c->precision = precision;
+  c->w.reset(new NetWeights());
+  std::string e;
+  if (!c->w->build(*net, &e)) return IDEQ_ERR_ARG;
+  CK(c->w->upload(weights, c->stream));
+  CK(cudaMalloc((void**)&c->d_err, 16));
+  CK(cudaMemsetAsync(c->d_err, 0, 16, c->stream));
+  CK(cudaMallocHost((void**)&c->h_running, 16));
+  CK(cudaStreamSynchronize(c->stream));
+  *out = c.release();
+  return IDEQ_OK;
+}
+
+ideq_status ideq_destroy(ideq_ctx* ctx) {
+  if (!ctx) return IDEQ_ERR_ARG;
+  cudaStreamSynchronize(ctx->stream);
+  ctx->plan.reset();
+  ctx->w.reset();
+  if (ctx->sv_mem) cudaFree(ctx->sv_mem);
+  if (ctx->scratch) cudaFree(ctx->scratch);
+  if (ctx->d_err) cudaFree(ctx->d_err);
+  if (ctx->h_running) cudaFreeHost(ctx->h_running);
+  delete ctx;
+  return IDEQ_OK;
+}
+
+const char* ideq_last_error(ideq_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+ideq_status ideq_set_weights(ideq_ctx* ctx, const float* weights) {
+  if (!ctx || !weights) return IDEQ_ERR_ARG;
+  CK(ctx->w->upload(weights, ctx->stream));
+  return IDEQ_OK;
+}
+
+ideq_status ideq_set_precision(ideq_ctx* ctx, int precision) {
+  if (!ctx) return IDEQ_ERR_ARG;
+  if (precision != IDEQ_FP32 && precision != IDEQ_BF16)
+    return fail(ctx, IDEQ_ERR_UNSUPPORTED, "precision");
+  ctx->precision = precision;
+  return IDEQ_OK;
+}
+
+ideq_status ideq_set_stream(ideq_ctx* ctx, void* stream) {
+  if (!ctx) return IDEQ_ERR_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->stream = (cudaStream_t)stream;
+  return IDEQ_OK;
+}
+
+ideq_status ideq_apply_A(ideq_ctx* ctx, const ideq_operator* op, ideq_shape shape, const float* x,
+                         float* Ax) {
+  if (!ctx || !x || !Ax || !shape_ok(shape)) return fail(ctx, IDEQ_ERR_ARG, "bad arguments");
+  OpDev od;
+  ideq_status s = check_op(ctx, op, shape, &od);
+  if (s != IDEQ_OK) return s;
+  CK(launch_apply_A(od, shape.n, shape.c, shape.h, shape.w, x, Ax, ctx->stream));
+  ctx->launches += 1;
+  return IDEQ_OK;
+}
+
+ideq_status ideq_apply_AT(ideq_ctx* ctx, const ideq_operator* op, ideq_shape shape, const float* r,
+                          const float* lin_point, float* out) {
+  if (!ctx || !r || !out || !shape_ok(shape)) return fail(ctx, IDEQ_ERR_ARG, "bad arguments");
+  OpDev od;
+  ideq_status s = check_op(ctx, op, shape, &od);
+  if (s != IDEQ_OK) return s;
+  if (od.kind == IDEQ_OP_SATBLUR && lin_point) {
+    float* tmp = ensure_scratch(ctx, (size_t)shape.n * shape.c * shape.h * shape.w * 4);
+    if (!tmp) return fail(ctx, IDEQ_ERR_NOMEM, "scratch");
+    CK(launch_sat_jt_weight(od, shape.n, shape.c, shape.h, shape.w, lin_point, r, tmp, ctx->stream));
+    CK(launch_blur_adj(od, shape.n, shape.c, shape.h, shape.w, tmp, out, ctx->stream));
+    ctx->launches += 2;
+    return IDEQ_OK;
+  }
+  CK(back_project(ctx, od, shape, r, out));
+  return IDEQ_OK;
+}
+
+ideq_status ideq_grad_reg(ideq_ctx* ctx, ideq_shape shape, const float* z, float* grad,
+                          double* g_val) {
+  if (!ctx || !z || !grad || !shape_ok(shape)) return fail(ctx, IDEQ_ERR_ARG, "bad arguments");
+  ideq_status s = ensure_plan(ctx, shape);
+  if (s != IDEQ_OK) return s;
+  NetPlan* P = ctx->plan.get();
+  const size_t bytes = (size_t)shape.n * shape.c * shape.h * shape.w * 4;
+  CK(cudaMemcpyAsync(P->z, z, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(launch_zero_d(shape.n, ctx->gsum, ctx->stream));
+  CK(run_steps(P->fwd, ctx->d_err, ctx->stream, &ctx->prof, &ctx->launches));
+  CK(run_steps(P->vjp, ctx->d_err, ctx->stream, &ctx->prof, &ctx->launches));
+  CK(cudaMemcpyAsync(grad, P->grad, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (g_val) CK(cudaMemcpyAsync(g_val, ctx->gsum, shape.n * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+  ctx->launches += 1;
+  return IDEQ_OK;
+}
+
+ideq_status ideq_step(ideq_ctx* ctx, const ideq_operator* op, ideq_shape shape, const float* y,
+                      float* x_k, float* x_km1, const ideq_params* p, ideq_info* info) {
+  if (!ctx || !y || !x_k || !x_km1 || !shape_ok(shape)) return fail(ctx, IDEQ_ERR_ARG, "bad arguments");
+  ideq_status s = check_params(ctx, p);
+  if (s != IDEQ_OK) return s;
+  OpDev od;
+  if ((s = check_op(ctx, op, shape, &od)) != IDEQ_OK) return s;
+  if ((s = ensure_plan(ctx, shape)) != IDEQ_OK) return s;
+  const size_t bytes = (size_t)shape.n * shape.c * shape.h * shape.w * 4;
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemcpyAsync(ctx->xb[0], x_k, bytes, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(ctx->xb[1], x_km1, bytes, cudaMemcpyDeviceToDevice, st));
+  CK(launch_solver_init(shape.n, ctx->sv, p->beta, st));  // every image extrapolates with beta
+  if ((s = iterate(ctx, od, shape, y, p, 0, 0)) != IDEQ_OK) return s;
+  CK(cudaMemcpyAsync(x_km1, x_k, bytes, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(x_k, ctx->xb[1], bytes, cudaMemcpyDeviceToDevice, st));
+  if (info) CK(launch_fill_info(shape.n, ctx->sv, *info, st));
+  return check_timeout(ctx);
+}
+
+ideq_status ideq_solve(ideq_ctx* ctx, const ideq_operator* op, ideq_shape shape, const float* y,
+                       const float* x0, float* x_out, const ideq_params* p, ideq_info* info) {
+  if (!ctx || !y || !x_out || !shape_ok(shape)) return fail(ctx, IDEQ_ERR_ARG, "bad arguments");
+  ideq_status s = check_params(ctx, p);
+  if (s != IDEQ_OK) return s;
+  OpDev od;
+  if ((s = check_op(ctx, op, shape, &od)) != IDEQ_OK) return s;
+  if (p->init == IDEQ_INIT_X0 && !x0) return fail(ctx, IDEQ_ERR_ARG, "init X0 needs x0");
+  if (p->init == IDEQ_INIT_WARM) return fail(ctx, IDEQ_ERR_UNSUPPORTED, "warm start not set");
+  if ((s = ensure_plan(ctx, shape)) != IDEQ_OK) return s;
+  const size_t bytes = (size_t)shape.n * shape.c * shape.h * shape.w * 4;
+  cudaStream_t st = ctx->stream;
+  if (p->init == IDEQ_INIT_X0)
+    CK(cudaMemcpyAsync(ctx->xb[0], x0, bytes, cudaMemcpyDeviceToDevice, st));
+  else
+    CK(back_project(ctx, od, shape, y, ctx->xb[0]));
+  CK(cudaMemcpyAsync(ctx->xb[1], ctx->xb[0], bytes, cudaMemcpyDeviceToDevice, st));
+  CK(launch_solver_init(shape.n, ctx->sv, 0.f, st));  // x^{-1} = x^0
+  const int poll = p->tol > 0.0 ? 2 : 0;
+  for (int it = 0; it < p->max_iter; ++it) {
+    if ((s = iterate(ctx, od, shape, y, p, it & 1, 1)) != IDEQ_OK) return s;
+    if (poll && ((it + 1) % poll == 0) && it + 1 < p->max_iter) {
+      CK(cudaMemcpyAsync(ctx->h_running, ctx->sv.n_running, 4, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (*ctx->h_running == 0) break;
+    }
+  }
+  CK(launch_gather_parity(shape.n, ctx->sv_per, ctx->sv.parity, ctx->xb[0], ctx->xb[1], x_out, st));
+  ctx->launches += 1;
+  if (info) CK(launch_fill_info(shape.n, ctx->sv, *info, st));
+  if ((s = check_timeout(ctx)) != IDEQ_OK) return s;
+  // overall status (stream already synchronised by check_timeout)
+  std::vector<int> hs(shape.n);
+  CK(cudaMemcpy(hs.data(), ctx->sv.status, shape.n * 4, cudaMemcpyDeviceToHost));
+  bool div = false, maxit = false;
+  for (int v : hs) {
+    div |= v == IDEQ_IMG_DIVERGED;
+    maxit |= v == IDEQ_IMG_MAXITER;
+  }
+  if (div) return fail(ctx, IDEQ_DIVERGED, "an image diverged");
+  if (maxit && p->tol > 0.0) return fail(ctx, IDEQ_MAXITER, "an image hit max_iter");
+  return IDEQ_OK;
+}
+
+ideq_status ideq_solve_backward(ideq_ctx* ctx, const ideq_operator*, ideq_shape, const float*,
+                                const float*, const float*, const ideq_params*,
+                                const ideq_adj_params*, float*, float*, ideq_info*) {
+  return fail(ctx, IDEQ_ERR_UNSUPPORTED, "backward not built yet");
+}
+
+ideq_status ideq_warm_set(ideq_ctx* ctx, const ideq_net_desc*, const float*) {
+  return fail(ctx, IDEQ_ERR_UNSUPPORTED, "warm start not built yet");
+}
+ideq_status ideq_warm_forward(ideq_ctx* ctx, ideq_shape, const float*, float*) {
+  return fail(ctx, IDEQ_ERR_UNSUPPORTED, "warm start not built yet");
+}
+ideq_status ideq_warm_train_step(ideq_ctx* ctx, ideq_shape, const float*, const float*, float,
+                                 double*) {
+  return fail(ctx, IDEQ_ERR_UNSUPPORTED, "warm start not built yet");
+}
+ideq_status ideq_warm_get(ideq_ctx* ctx, float*) {
+  return fail(ctx, IDEQ_ERR_UNSUPPORTED, "warm start not built yet");
+}
+
+ideq_status ideq_prof_enable(ideq_ctx* ctx, int on) {
+  if (!ctx) return IDEQ_ERR_ARG;
+  ctx->prof.on = on != 0;
+  return IDEQ_OK;
+}
+
+ideq_status ideq_prof_read(ideq_ctx* ctx, double* ms, int64_t* launches, double* flops) {
+  if (!ctx) return IDEQ_ERR_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  double t = 0;
+  for (size_t i = 0; i + 1 < ctx->prof.used; i += 2) {
+    float m = 0.f;
+    cudaEventElapsedTime(&m, ctx->prof.ev[i], ctx->prof.ev[i + 1]);
+    t += m;
+  }
+  if (ms) *ms = t;
+  if (launches) *launches = ctx->prof.launches;
+  if (flops) *flops = ctx->prof.flops;
+  ctx->prof.used = 0;
+  ctx->prof.launches = 0;
+  ctx->prof.flops = 0;
+  return IDEQ_OK;
+}
+
+ideq_status ideq_launch_count(ideq_ctx* ctx, int64_t* count) {
+  if (!ctx || !count) return IDEQ_ERR_ARG;
+  *count = ctx->launches;
+  ctx->launches = 0;
+  return IDEQ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,200 @@
+// SIMT implicit-GEMM convolution (FP32 arithmetic) for the plain FP32 form,
+// for layers whose channel counts are too small for the tensor-core path
+// (head 3->64, tail 64->3 and their transposes, the tiny 1->32 nets), and as the
+// reference-free baseline of the tensor-core kernel.  See ConvArgs for the
+// GEMM view and the epilogues.
+#include "common.cuh"
+#include "ideq_internal.h"
+
+namespace ideq {
+
+template <typename TIn, typename TOut, int BM, int BN, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+    conv_simt_kernel(ConvArgs a) {
+  constexpr int NT = (BM / TM) * (BN / TN);
+  constexpr int BK = 16;
+  constexpr int AR = NT / BK;   // A rows loaded per pass
+  constexpr int APT = BM / AR;  // A loads per thread
+  static_assert(NT % BK == 0 && BM % AR == 0, "tile");
+  __shared__ __align__(16) float As[BK][BM + 4];
+  __shared__ __align__(16) float Bs[BK][BN + 4];
+  __shared__ double simg[BM];
+
+  const int tid = threadIdx.x;
+  const long long M = a.M();
+  const int N = a.N(), K = a.K();
+  const long long m0 = (long long)blockIdx.x * BM;
+  const int n0 = blockIdx.y * BN;
+  const int HW = a.H * a.W;
+  const TIn* __restrict__ in = (const TIn*)a.in;
+  const float* __restrict__ inf = (const float*)a.in;
+  const TIn* __restrict__ wB = (const TIn*)a.wB;  // unused type for weights below
+  (void)wB;
+  const float* __restrict__ wf = (const float*)a.wB;
+
+  // rows this thread loads for A
+  const int ak = tid % BK;
+  int r_img[APT], r_y[APT], r_x[APT];
+  bool r_ok[APT];
+#pragma unroll
+  for (int i = 0; i < APT; ++i) {
+    const long long m = m0 + tid / BK + i * AR;
+    r_ok[i] = m < M;
+    const long long mm = r_ok[i] ? m : 0;
+    r_img[i] = (int)(mm / HW);
+    const int rem = (int)(mm % HW);
+    r_y[i] = rem / a.W;
+    r_x[i] = rem % a.W;
+  }
+  // source image size of the A gather
+  const int SH = a.mode == CM_DOWN ? 2 * a.H : a.H;
+  const int SW = a.mode == CM_DOWN ? 2 * a.W : a.W;
+
+  float acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
+
+  const int tn = tid % (BN / TN), tm = tid / (BN / TN);
+
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    const int kg = k0 + ak;
+    int dy = 0, dx = 0, ci = kg;
+    if (a.mode == CM_CONV3) {
+      const int t = kg / a.Cin;
+      ci = kg - t * a.Cin;
+      dy = t / 3 - 1;
+      dx = t % 3 - 1;
+    } else if (a.mode == CM_DOWN) {
+      const int q = kg / a.Cin;
+      ci = kg - q * a.Cin;
+      dy = q >> 1;
+      dx = q & 1;
+    }
+#pragma unroll
+    for (int i = 0; i < APT; ++i) {
+      float v = 0.f;
+      if (r_ok[i] && kg < K) {
+        int sy, sx;
+        if (a.mode == CM_DOWN) {
+          sy = 2 * r_y[i] + dy;
+          sx = 2 * r_x[i] + dx;
+        } else {
+          sy = r_y[i] + dy;
+          sx = r_x[i] + dx;
+        }
+        if (sy >= 0 && sy < SH && sx >= 0 && sx < SW) {
+          if (a.in_nchw)
+            v = inf[(((size_t)r_img[i] * a.Cin + ci) * SH + sy) * SW + sx];
+          else
+            v = ld_f(in + (((size_t)r_img[i] * SH + sy) * SW + sx) * a.Cin + ci);
+        }
+      }
+      As[ak][tid / BK + i * AR] = v;
+    }
+    for (int e = tid; e < BK * BN; e += NT) {
+      const int kk = e % BK, nn = e / BK;
+      const int gn = n0 + nn, gk = k0 + kk;
+      Bs[kk][nn] = (gn < N && gk < K) ? wf[(size_t)gn * K + gk] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      float ar[TM], br[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) ar[i] = As[kk][tm * TM + i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) br[j] = Bs[kk][tn * TN + j];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(ar[i], br[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+
+  // ---------------- epilogue
+  const bool sums = a.epi == EP_AXPY_NCHW && a.sumsq != nullptr;
+  const int img_first = (int)(m0 / HW);
+  if (sums) {
+    for (int i = tid; i < BM; i += NT) simg[i] = 0.0;
+    __syncthreads();
+  }
+  TOut* out = (TOut*)a.out;
+  TOut* out2 = (TOut*)a.out2;
+  const TOut* aux0 = (const TOut*)a.aux0;
+  const TOut* aux1 = (const TOut*)a.aux1;
+  const TOut* aux2 = (const TOut*)a.aux2;
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const long long m = m0 + tm * TM + i;
+    if (m >= M) continue;
+    const int img = (int)(m / HW);
+    const int rem = (int)(m % HW);
+    const int y = rem / a.W, x = rem % a.W;
+    double ssq = 0.0;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int n = n0 + tn * TN + j;
+      if (n >= N) continue;
+      const float v = acc[i][j];
+      if (a.epi == EP_AXPY_NCHW) {
+        const size_t o = (((size_t)img * a.Cout + n) * a.H + y) * a.W + x;
+        const float r = ((const float*)a.aux0)[o] + a.sign * v;
+        ((float*)a.out)[o] = r;
+        ssq += 0.5 * (double)r * (double)r;
+        continue;
+      }
+      size_t o;
+      if (a.outmap == OM_D2S) {
+        const int q = n / a.Cout, co = n - q * a.Cout;
+        const int oy = 2 * y + (q >> 1), ox = 2 * x + (q & 1);
+        o = (((size_t)img * 2 * a.H + oy) * 2 * a.W + ox) * a.Cout + co;
+      } else {
+        o = (size_t)m * a.Cout + n;
+      }
+      const float x0 = aux0 ? ld_f(aux0 + o) : 0.f;
+      const float x1 = aux1 ? ld_f(aux1 + o) : 0.f;
+      const float x2 = aux2 ? ld_f(aux2 + o) : 0.f;
+      float o2 = 0.f;
+      const float r = epi_math(a.epi, a.act, v, x0, x1, x2, &o2);
+      out[o] = from_f<TOut>(r);
+      if (epi_has_out2(a.epi)) out2[o] = from_f<TOut>(o2);
+    }
+    if (sums && ssq != 0.0) atomicAdd(&simg[img - img_first], ssq);
+  }
+  if (sums) {
+    __syncthreads();
+    const long long mlast = (m0 + BM - 1 < M ? m0 + BM - 1 : M - 1);
+    const int nimg = (int)(mlast / HW) - img_first + 1;
+    for (int i = tid; i < nimg; i += NT)
+      if (simg[i] != 0.0) atomicAdd(a.sumsq + img_first + i, simg[i]);
+  }
+}
+
+template <typename TIn, typename TOut>
+static cudaError_t launch_typed(const ConvArgs& a, cudaStream_t st) {
+  const long long M = a.M();
+  const int N = a.N();
+  if (N <= 4) {
+    constexpr int BM = 128, BN = 4, TM = 2, TN = 1;
+    dim3 grid((unsigned)((M + BM - 1) / BM), (N + BN - 1) / BN);
+    conv_simt_kernel<TIn, TOut, BM, BN, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, st>>>(a);
+  } else {
+    constexpr int BM = 128, BN = 64, TM = 8, TN = 4;
+    dim3 grid((unsigned)((M + BM - 1) / BM), (N + BN - 1) / BN);
+    conv_simt_kernel<TIn, TOut, BM, BN, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_conv_simt(const ConvArgs& a, int in_bf16, int out_bf16, cudaStream_t st) {
+  if (a.M() == 0) return cudaSuccess;
+  if (in_bf16 && out_bf16) return launch_typed<__nv_bfloat16, __nv_bfloat16>(a, st);
+  if (in_bf16) return launch_typed<__nv_bfloat16, float>(a, st);
+  if (out_bf16) return launch_typed<float, __nv_bfloat16>(a, st);
+  return launch_typed<float, float>(a, st);
+}
+
+}  // namespace ideq

@@ -1,0 +1,526 @@
+// tcgen05 (5th-generation tensor core) implicit-GEMM convolution for sm_103a.
+//
+// One CTA computes a 128 x BN tile of D = A * B^T (see ConvArgs):
+//   warp 0      TMA producer: per K chunk of 64 channels, one box of 128 pixels
+//               x 64 channels of the NHWC bf16 activation (tap-shifted; the
+//               zero padding of the convolution is the TMA out-of-bounds fill)
+//               and one box of BN x 64 weights, into a STAGES-deep ring.
+//   warp 1      allocates TMEM and issues tcgen05.mma (M=128, N=BN, K=16,
+//               bf16 x bf16 -> f32) from one elected lane; tcgen05.commit
+//               frees ring slots and finally signals the accumulator.
+//   warps 2..5  epilogue: tcgen05.ld the f32 accumulator (one pixel row per
+//               thread), apply the fused epilogue, store bf16 NHWC.
+// Shared-memory operands use the 128-byte swizzle that TMA writes and the
+// UMMA descriptor reads (8-row atoms of 128 B, stride 1024 B).
+// Every mbarrier wait is bounded (about 2 s of %globaltimer); an expired wait
+// sets *err_flag, all roles drain and the CTA returns after freeing TMEM.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+#include <mutex>
+
+#include "common.cuh"
+#include "ideq_internal.h"
+
+namespace ideq {
+
+struct TcArgs {
+  int mode, outmap, epi, act;
+  int n, H, W, Cin, Cout, N;
+  int Wt, Ht, tiles_w, tiles_h, nk, cpt;
+  __nv_bfloat16* out;
+  __nv_bfloat16* out2;
+  const __nv_bfloat16* aux0;
+  const __nv_bfloat16* aux1;
+  const __nv_bfloat16* aux2;
+  int* err;
+};
+
+struct TcPlan {
+  CUtensorMap tmA;
+  CUtensorMap tmB;
+  int bn = 0, stages = 0;
+  int Wt = 0, Ht = 0, tiles_w = 0, tiles_h = 0, nk = 0, cpt = 0;
+  dim3 grid;
+  size_t smem = 0;
+};
+
+// ------------------------------------------------------------------ PTX helpers
+
+IDEQ_DEV uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+IDEQ_DEV uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+IDEQ_DEV void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+IDEQ_DEV void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+IDEQ_DEV uint32_t mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok;
+}
+
+// Bounded wait: returns false after ~2 s or once another role raised the flag.
+IDEQ_DEV bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
+  uint64_t t0 = 0;
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 255u) == 255u) {
+      if (*(volatile int*)err != 0) return false;
+      const uint64_t now = globaltimer();
+      if (t0 == 0) {
+        t0 = now;
+      } else if (now - t0 > 2000000000ull) {
+        atomicCAS(err, 0, code);
+        return false;
+      }
+    }
+  }
+}
+
+IDEQ_DEV void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(tm), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+
+IDEQ_DEV void tma_load_4d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, int c2, int c3,
+                          uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+      "l"(tm), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
+
+IDEQ_DEV void tma_load_5d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, int c2, int c3,
+                          int c4, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+      "l"(tm), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+      : "memory");
+}
+
+IDEQ_DEV void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+IDEQ_DEV void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// UMMA shared-memory matrix descriptor, K-major, 128-byte swizzle:
+// start address >> 4 in bits [0,14), leading byte offset (unused for this
+// layout, 16 B) in [16,30), stride byte offset 1024 B (one 8-row atom) in
+// [32,46), descriptor version 1 in [46,48), swizzle mode 2 (128 B) in [61,64).
+IDEQ_DEV uint64_t umma_desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(16u >> 4) << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor of kind::f16: D f32 (bits [4,6) = 1), A and B bf16
+// (bits [7,10) and [10,13) = 1), both K-major, N >> 3 in [17,23), M >> 4 in [24,29).
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+IDEQ_DEV void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                        uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+IDEQ_DEV void umma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+IDEQ_DEV void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+IDEQ_DEV void load_bf16x16(const __nv_bfloat16* p, float (&v)[16]) {
+  const uint4* q = (const uint4*)p;
+  const uint4 a = q[0], b = q[1];
+  const __nv_bfloat162* h0 = (const __nv_bfloat162*)&a;
+  const __nv_bfloat162* h1 = (const __nv_bfloat162*)&b;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float2 f0 = __bfloat1622float2(h0[i]);
+    const float2 f1 = __bfloat1622float2(h1[i]);
+    v[2 * i] = f0.x;
+    v[2 * i + 1] = f0.y;
+    v[8 + 2 * i] = f1.x;
+    v[8 + 2 * i + 1] = f1.y;
+  }
+}
+
+IDEQ_DEV void store_bf16x16(__nv_bfloat16* p, const float (&v)[16]) {
+  uint4 a, b;
+  __nv_bfloat162* h0 = (__nv_bfloat162*)&a;
+  __nv_bfloat162* h1 = (__nv_bfloat162*)&b;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    h0[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    h1[i] = __floats2bfloat162_rn(v[8 + 2 * i], v[8 + 2 * i + 1]);
+  }
+  uint4* q = (uint4*)p;
+  q[0] = a;
+  q[1] = b;
+}
+
+// ------------------------------------------------------------------ kernel
+
+constexpr int TC_THREADS = 192;
+constexpr int A_BYTES = 128 * 128;  // 128 pixel rows x 64 bf16
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    conv_tc_kernel(const __grid_constant__ CUtensorMap tmA,
+                   const __grid_constant__ CUtensorMap tmB, TcArgs a) {
+  constexpr int B_BYTES = BN * 128;
+  constexpr uint32_t STAGE_TX = A_BYTES + B_BYTES;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + STAGES * A_BYTES;
+  uint64_t* bars = (uint64_t*)(sB + STAGES * B_BYTES);  // full[S], empty[S], accum
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
+  const uint32_t accb = smem_u32(bars + 2 * STAGES);
+
+  // tile coordinates
+  const int mt = blockIdx.x;
+  const int per_img = a.tiles_h * a.tiles_w;
+  const int img = mt / per_img;
+  const int rr = mt - img * per_img;
+  const int h0 = (rr / a.tiles_w) * a.Ht;
+  const int w0 = (rr % a.tiles_w) * a.Wt;
+  const int n0 = blockIdx.y * BN;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(accb, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"((uint32_t)BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
+      int issued = 0;
+      bool ok = true;
+      for (int kc = 0; kc < a.nk && ok; ++kc) {
+        const int s = kc % STAGES, j = kc / STAGES;
+        if (j > 0 && !mbar_wait(empty0 + 8 * s, (j - 1) & 1, a.err, 1)) { ok = false; break; }
+        mbar_expect_tx(full0 + 8 * s, STAGE_TX);
+        const uint32_t dA = smem_u32(sA + s * A_BYTES);
+        const uint32_t dB = smem_u32(sB + s * B_BYTES);
+        if (a.mode == CM_DOWN) {
+          const int k0 = kc * 64;
+          const int di = k0 / (2 * a.Cin), rem = k0 - di * 2 * a.Cin;
+          tma_load_5d(dA, &tmA, rem, w0, di, h0, img, full0 + 8 * s);
+        } else {
+          int tap = 4, c0 = kc * 64;
+          if (a.mode == CM_CONV3) {
+            tap = kc / a.cpt;
+            c0 = (kc - tap * a.cpt) * 64;
+          }
+          tma_load_4d(dA, &tmA, c0, w0 + tap % 3 - 1, h0 + tap / 3 - 1, img, full0 + 8 * s);
+        }
+        tma_load_2d(dB, &tmB, kc * 64, n0, full0 + 8 * s);
+        ++issued;
+      }
+      // tail: wait until the MMA warp released every slot still in use, so no
+      // tcgen05.commit arrival is outstanding when the CTA exits.
+      const int first = issued > STAGES ? issued - STAGES : 0;
+      for (int kc = first; kc < issued; ++kc) {
+        const int s = kc % STAGES, j = kc / STAGES;
+        if (ok) ok = mbar_wait(empty0 + 8 * s, j & 1, a.err, 2);
+        if (!ok) mbar_wait(full0 + 8 * s, j & 1, a.err, 2);  // our own copies in flight
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = umma_idesc_bf16(128, BN);
+      bool ok = true;
+      int done = 0;
+      for (int kc = 0; kc < a.nk; ++kc) {
+        const int s = kc % STAGES, j = kc / STAGES;
+        if (!mbar_wait(full0 + 8 * s, j & 1, a.err, 3)) { ok = false; break; }
+        tc_fence_after();
+        const uint64_t ad = umma_desc_sw128(smem_u32(sA + s * A_BYTES));
+        const uint64_t bd = umma_desc_sw128(smem_u32(sB + s * B_BYTES));
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          umma_bf16(tmem, ad + 2 * kk, bd + 2 * kk, idesc, (kc | kk) != 0 ? 1u : 0u);
+        umma_commit(empty0 + 8 * s);
+        ++done;
+      }
+      (void)done;
+      (void)ok;
+      umma_commit(accb);  // also on the error path: arrives once issued MMAs finish
+    }
+  } else {
+    // epilogue warps 2..5 -> TMEM lane quarter (warp % 4)
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    const bool ok = mbar_wait(accb, 0, a.err, 4);
+    tc_fence_after();
+    const int ly = row / a.Wt, lx = row - ly * a.Wt;
+    const int y = h0 + ly, x = w0 + lx;
+    const bool valid = ok && (*(volatile int*)a.err == 0) && y < a.H && x < a.W;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);  // warp-collective
+      if (!valid) continue;
+      const int n = n0 + c0;
+      size_t o;
+      if (a.outmap == OM_D2S) {
+        const int qq = n / a.Cout, co = n - qq * a.Cout;
+        const int oy = 2 * y + (qq >> 1), ox = 2 * x + (qq & 1);
+        o = (((size_t)img * 2 * a.H + oy) * 2 * a.W + ox) * a.Cout + co;
+      } else {
+        o = (((size_t)img * a.H + y) * a.W + x) * (size_t)a.Cout + n;
+      }
+      float x0[16], x1[16], x2[16], r[16], r2[16];
+      if (a.aux0) load_bf16x16(a.aux0 + o, x0);
+      if (a.aux1) load_bf16x16(a.aux1 + o, x1);
+      if (a.aux2) load_bf16x16(a.aux2 + o, x2);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        r2[i] = 0.f;
+        r[i] = epi_math(a.epi, a.act, v[i], a.aux0 ? x0[i] : 0.f, a.aux1 ? x1[i] : 0.f,
+                        a.aux2 ? x2[i] : 0.f, &r2[i]);
+      }
+      store_bf16x16(a.out + o, r);
+      if (a.epi == EP_ACT || a.epi == EP_MUL_KEEP) store_bf16x16(a.out2 + o, r2);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((uint32_t)BN)
+                 : "memory");
+  }
+}
+
+// ------------------------------------------------------------------ host side
+
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
+}
+
+static int pick_bn(int N) {
+  if (N % 256 == 0 && N >= 512) return 256;
+  if (N % 128 == 0) return 128;
+  return 64;
+}
+
+bool tc_supported(const ConvArgs& a) {
+  if (a.in_nchw || a.out_nchw || a.epi == EP_AXPY_NCHW) return false;
+  if (a.Cin % 64 != 0) return false;
+  if (a.N() % 64 != 0) return false;
+  if (a.outmap == OM_D2S && a.Cout % 16 != 0) return false;
+  if (a.mode == CM_DOWN && a.outmap != OM_IDENT) return false;
+  return true;
+}
+
+template <int BN, int ST>
+static size_t smem_bytes() {
+  return 1024 + (size_t)ST * (A_BYTES + BN * 128) + (2 * ST + 1) * 8 + 16;
+}
+
+static int stages_for(int bn) { return bn == 64 ? 4 : (bn == 128 ? 4 : 3); }
+
+TcPlan* tc_plan_create(const ConvArgs& a, std::string* err) {
+  auto enc = get_encode();
+  if (!enc) {
+    *err = "cuTensorMapEncodeTiled unavailable";
+    return nullptr;
+  }
+  if (!tc_supported(a)) {
+    *err = "layer not supported by the tensor-core kernel";
+    return nullptr;
+  }
+  TcPlan* p = new TcPlan();
+  const int N = a.N();
+  p->bn = pick_bn(N);
+  p->stages = stages_for(p->bn);
+  // M tile: Ht x Wt pixels of the grid, Wt a power of two
+  int wt = 1;
+  while (wt < a.W && wt < 128) wt <<= 1;
+  p->Wt = wt;
+  p->Ht = 128 / wt;
+  p->tiles_w = (a.W + p->Wt - 1) / p->Wt;
+  p->tiles_h = (a.H + p->Ht - 1) / p->Ht;
+  p->cpt = a.Cin / 64;
+  p->nk = a.K() / 64;
+  p->grid = dim3((unsigned)(a.n * p->tiles_h * p->tiles_w), (unsigned)(N / p->bn), 1);
+  const CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  CUresult r;
+  if (a.mode == CM_DOWN) {
+    const int Hi = 2 * a.H, Wi = 2 * a.W;
+    cuuint64_t dims[5] = {(cuuint64_t)(2 * a.Cin), (cuuint64_t)a.W, 2, (cuuint64_t)a.H,
+                          (cuuint64_t)a.n};
+    cuuint64_t strides[4] = {(cuuint64_t)2 * a.Cin * 2, (cuuint64_t)Wi * a.Cin * 2,
+                             (cuuint64_t)2 * Wi * a.Cin * 2, (cuuint64_t)Hi * Wi * a.Cin * 2};
+    cuuint32_t box[5] = {64, (cuuint32_t)p->Wt, 1, (cuuint32_t)p->Ht, 1};
+    cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    r = enc(&p->tmA, dt, 5, const_cast<void*>(a.in), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  } else {
+    cuuint64_t dims[4] = {(cuuint64_t)a.Cin, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.n};
+    cuuint64_t strides[3] = {(cuuint64_t)a.Cin * 2, (cuuint64_t)a.W * a.Cin * 2,
+                             (cuuint64_t)a.H * a.W * a.Cin * 2};
+    cuuint32_t box[4] = {64, (cuuint32_t)p->Wt, (cuuint32_t)p->Ht, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    r = enc(&p->tmA, dt, 4, const_cast<void*>(a.in), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  }
+  if (r != CUDA_SUCCESS) {
+    *err = "cuTensorMapEncodeTiled(A) failed: " + std::to_string((int)r);
+    delete p;
+    return nullptr;
+  }
+  {
+    const int K = a.K();
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)N};
+    cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+    cuuint32_t box[2] = {64, (cuuint32_t)p->bn};
+    cuuint32_t es[2] = {1, 1};
+    r = enc(&p->tmB, dt, 2, const_cast<void*>(a.wB), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+      *err = "cuTensorMapEncodeTiled(B) failed: " + std::to_string((int)r);
+      delete p;
+      return nullptr;
+    }
+  }
+  switch (p->bn) {
+    case 64: p->smem = smem_bytes<64, 4>(); break;
+    case 128: p->smem = smem_bytes<128, 4>(); break;
+    default: p->smem = smem_bytes<256, 3>(); break;
+  }
+  return p;
+}
+
+void tc_plan_destroy(TcPlan* p) { delete p; }
+
+template <int BN, int ST>
+static cudaError_t launch_bn(const TcPlan* p, const TcArgs& ta, cudaStream_t st) {
+  static bool attr_set = false;  // per instantiation; set before first launch
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<BN, ST>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_bytes<BN, ST>());
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  conv_tc_kernel<BN, ST><<<p->grid, TC_THREADS, smem_bytes<BN, ST>(), st>>>(p->tmA, p->tmB, ta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_conv_tc(const TcPlan* p, const ConvArgs& a, int* err_flag, cudaStream_t st) {
+  TcArgs t;
+  t.mode = a.mode;
+  t.outmap = a.outmap;
+  t.epi = a.epi;
+  t.act = a.act;
+  t.n = a.n;
+  t.H = a.H;
+  t.W = a.W;
+  t.Cin = a.Cin;
+  t.Cout = a.Cout;
+  t.N = a.N();
+  t.Wt = p->Wt;
+  t.Ht = p->Ht;
+  t.tiles_w = p->tiles_w;
+  t.tiles_h = p->tiles_h;
+  t.nk = p->nk;
+  t.cpt = p->cpt;
+  t.out = (__nv_bfloat16*)a.out;
+  t.out2 = (__nv_bfloat16*)a.out2;
+  t.aux0 = (const __nv_bfloat16*)a.aux0;
+  t.aux1 = (const __nv_bfloat16*)a.aux1;
+  t.aux2 = (const __nv_bfloat16*)a.aux2;
+  t.err = err_flag;
+  switch (p->bn) {
+    case 64: return launch_bn<64, 4>(p, t, st);
+    case 128: return launch_bn<128, 4>(p, t, st);
+    default: return launch_bn<256, 3>(p, t, st);
+  }
+}
+
+}  // namespace ideq

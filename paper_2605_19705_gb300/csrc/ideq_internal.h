@@ -1,0 +1,142 @@
+// Internal declarations of the i-DEQ CUDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/ideq.h"
+
+#ifdef __CUDACC__
+#define IDEQ_HD __host__ __device__
+#else
+#define IDEQ_HD
+#endif
+
+namespace ideq {
+
+// ------------------------------------------------------------- conv GEMMs
+//
+// Every network layer is one implicit GEMM  D[M][N] = A[M][K] * B[N][K]^T
+// with a fused epilogue.  M runs over the pixels of a "grid" (n, H, W):
+//   CM_CONV3  3x3 conv, stride 1, zero padding: grid = output pixels,
+//             K = 9 * Cin, k = tap * Cin + ci, tap = ky * 3 + kx.
+//   CM_DOWN   2x2 stride-2 conv: grid = output pixels (input is 2H x 2W),
+//             K = 4 * Cin, k = (di * 2 + dj) * Cin + ci.
+//   CM_PIX    1x1 (pixelwise) product: grid = input pixels, K = Cin.
+// Output maps: OM_IDENT writes out[m][n] (NHWC, C = N); OM_D2S scatters column
+// n = (di * 2 + dj) * Cout + co to pixel (2y + di, 2x + dj) of a 2H x 2W image.
+enum ConvMode { CM_CONV3 = 0, CM_DOWN = 1, CM_PIX = 2 };
+enum OutMap { OM_IDENT = 0, OM_D2S = 1 };
+enum Epi {
+  EP_STORE = 0,    // out = acc
+  EP_ACT = 1,      // out = act(acc), out2 = act'(acc)
+  EP_ADD = 2,      // out = acc + aux0
+  EP_MUL = 3,      // out = acc * aux0
+  EP_MUL_KEEP = 4, // out = acc * aux0, out2 = acc
+  EP_DUAL = 5,     // out = aux0 * acc + aux0 (1 - aux0) aux1 aux2   (softplus'' = s(1-s))
+  EP_AXPY_NCHW = 6 // out (f32 NCHW) = aux0 (f32 NCHW) + sign * acc; optional sum(out^2)
+};
+
+struct ConvArgs {
+  int mode = CM_CONV3, outmap = OM_IDENT, epi = EP_STORE, act = 0;
+  int n = 0, H = 0, W = 0;     // GEMM grid
+  int Cin = 0, Cout = 0;       // N = Cout (IDENT) or 4 * Cout (D2S)
+  int in_nchw = 0;             // input is f32 planar NCHW
+  int out_nchw = 0;            // output is f32 planar NCHW (EP_AXPY_NCHW)
+  float sign = -1.f;           // EP_AXPY_NCHW
+  const void* in = nullptr;
+  const void* wB = nullptr;    // GEMM weights [N][K]
+  void* out = nullptr;
+  void* out2 = nullptr;
+  const void* aux0 = nullptr;
+  const void* aux1 = nullptr;
+  const void* aux2 = nullptr;
+  double* sumsq = nullptr;     // per-image accumulator of 1/2 sum(out^2), or null
+  IDEQ_HD int N() const { return outmap == OM_D2S ? 4 * Cout : Cout; }
+  IDEQ_HD int K() const { return mode == CM_CONV3 ? 9 * Cin : (mode == CM_DOWN ? 4 * Cin : Cin); }
+  IDEQ_HD long long M() const { return (long long)n * H * W; }
+  IDEQ_HD double flops() const { return 2.0 * (double)M() * N() * K(); }
+};
+
+// dtype: 0 = f32, 1 = bf16 for activations (in/out NHWC); NCHW sides are f32.
+cudaError_t launch_conv_simt(const ConvArgs& a, int in_bf16, int out_bf16, cudaStream_t st);
+
+// tcgen05 path: bf16 NHWC in/out, Cin % 64 == 0, N % 16 == 0 (see conv_tc.cu).
+struct TcPlan;  // tensor maps + launch geometry, built once per (layer, buffers)
+bool tc_supported(const ConvArgs& a);
+TcPlan* tc_plan_create(const ConvArgs& a, std::string* err);
+void tc_plan_destroy(TcPlan* p);
+cudaError_t launch_conv_tc(const TcPlan* p, const ConvArgs& a, int* err_flag, cudaStream_t st);
+
+// Weight forms: GEMM B matrices from the PyTorch-layout weights.
+enum WForm { WF_CONV3_FWD = 0, WF_CONV3_DGRAD, WF_DOWN_FWD, WF_DOWN_DGRAD, WF_UP_FWD, WF_UP_DGRAD };
+cudaError_t launch_weight_form(int form, int cin, int cout, const float* src, float* dst_f32,
+                               void* dst_bf16, cudaStream_t st);
+// Scatter a GEMM-layout weight gradient [N][K] back to PyTorch layout (+=).
+cudaError_t launch_weight_unform(int form, int cin, int cout, const float* g, float* dst,
+                                 cudaStream_t st);
+
+// ------------------------------------------------------------- data step
+struct OpDev {
+  int kind, kh, kw;
+  const float* kernel;
+  const uint8_t* mask;
+  float gain;
+};
+// e = A(in) - y (y nullable): writes to `out` the vector fed to the adjoint
+// pass (e for linear blur; J-weighted e for satblur; M.(M.in - y) directly
+// for the mask, which needs no second pass) and accumulates 1/2||e||^2 per
+// image into fsum (nullable).
+cudaError_t launch_data_fwd(const OpDev& op, int n, int c, int H, int W, const float* in,
+                            const float* y, float* out, double* fsum, cudaStream_t st);
+// Adjoint pass: out = k^T (in) (blur kinds).
+cudaError_t launch_blur_adj(const OpDev& op, int n, int c, int H, int W, const float* in,
+                            float* out, cudaStream_t st);
+// Ax = A(x) (forward model only).
+cudaError_t launch_apply_A(const OpDev& op, int n, int c, int H, int W, const float* x,
+                           float* Ax, cudaStream_t st);
+// J_A(lin)^T r for satblur: tmp = (s/tanh s) sech^2(s k*lin) . r; out = k^T tmp.
+cudaError_t launch_sat_jt_weight(const OpDev& op, int n, int c, int H, int W, const float* lin,
+                                 const float* r, float* tmp, cudaStream_t st);
+
+// ------------------------------------------------------------- solver state
+struct SolverDev {
+  int* k;          // steps since last restart
+  int* total;      // total updates
+  int* restarts;
+  int* status;     // IDEQ_IMG_*
+  int* parity;     // buffer holding the latest iterate
+  float* beta_eff; // beta for the next extrapolation (0 after restart / frozen)
+  double* S;       // restart accumulator sum ||dx||^2
+  double* rel;     // last relative step
+  double* fsum;    // 1/2||A z - y||^2 of the current step
+  double* gsum;    // 1/2||z - N(z)||^2 of the current step
+  double* energy;
+  double* part_s;  // [n][nblk] partial sums of ||x_new - x||^2
+  double* part_x;  // [n][nblk] partial sums of ||x||^2
+  int* n_running;
+};
+
+cudaError_t launch_extrapolate(int n, int per_img, const float* x, const float* xp,
+                               const float* beta_eff, float* z, cudaStream_t st);
+cudaError_t launch_red_update(int n, int per_img, int nblk, const float* z, const float* gf,
+                              const float* gg, const float* x, float* xn, float lam, float tau,
+                              const int* status, double* part_s, double* part_x,
+                              cudaStream_t st);
+cudaError_t launch_finalize(int n, int nblk, const SolverDev& s, int parity_new, float beta,
+                            float B, double tol, int max_iter, float lam, int apply_logic,
+                            cudaStream_t st);
+cudaError_t launch_gather_parity(int n, int per_img, const int* parity, const float* b0,
+                                 const float* b1, float* out, cudaStream_t st);
+cudaError_t launch_solver_init(int n, const SolverDev& s, float beta, cudaStream_t st);
+cudaError_t launch_fill_info(int n, const SolverDev& s, ideq_info info, cudaStream_t st);
+int update_blocks_per_image(int per_img);
+
+// small vector helpers
+cudaError_t launch_axpby(long long n, float a, const float* x, float b, const float* y,
+                         float* out, cudaStream_t st);
+cudaError_t launch_zero_d(long long n, double* p, cudaStream_t st);
+
+}  // namespace ideq

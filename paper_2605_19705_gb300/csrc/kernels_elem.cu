@@ -1,0 +1,519 @@
+// Data-step stencils, the fused RED update with its FP64 reductions, the
+// per-image restart/stopping logic of Algorithm 1, and weight re-layouts.
+#include "common.cuh"
+#include "ideq_internal.h"
+
+#include <cmath>
+
+namespace ideq {
+
+// ===================================================================== data step
+//
+// Circular 2-D stencils of the blur forward models (one per-image kernel shared
+// by the channels).  A block computes a 32x32 output tile from a shared-memory
+// tile with a (kh-1, kw-1) halo that wraps around the image borders; each
+// thread owns outputs (ty + 16a, tx + 16b), a, b in {0,1}, so that shared
+// reads of neighbouring threads hit consecutive words.
+//
+//   forward  (k * x)[i,j]   = sum_{u,v} k[u,v] x[i-u+cy, j-v+cx]
+//   adjoint  (k^T r)[i,j]   = sum_{u,v} k[u,v] r[i+u-cy, j+v-cx]
+// Both reduce to a correlation over the halo tile with the kernel flipped for
+// the forward direction.
+
+enum DataEpi { DE_PLAIN = 0, DE_LIN_RES = 1, DE_SAT_RES = 2, DE_SAT_PLAIN = 3, DE_SAT_JW = 4 };
+
+constexpr int BT = 32;       // output tile edge
+constexpr int MAXK = 31;     // largest supported kernel edge
+constexpr int TILE_E = BT + MAXK - 1;
+
+__global__ void __launch_bounds__(256) blur_tile_kernel(
+    int c, int H, int W, int kh, int kw, const float* __restrict__ ker, int flip,
+    const float* __restrict__ in, const float* __restrict__ y, float* __restrict__ out,
+    double* __restrict__ fsum, int epi, float gain) {
+  __shared__ float sk[MAXK * MAXK];
+  __shared__ float st[TILE_E * TILE_E];
+  __shared__ double red[32];
+  const int plane = blockIdx.z;  // b * c + ch
+  const int b = plane / c;
+  const int i0 = blockIdx.y * BT, j0 = blockIdx.x * BT;
+  const int cy = kh / 2, cx = kw / 2;
+  const int tw = BT + kw - 1, th = BT + kh - 1;
+  const int tid = threadIdx.y * 16 + threadIdx.x;
+  const float* kb = ker + (size_t)b * kh * kw;
+  for (int e = tid; e < kh * kw; e += 256) {
+    const int u = e / kw, v = e % kw;
+    sk[e] = flip ? kb[(kh - 1 - u) * kw + (kw - 1 - v)] : kb[e];
+  }
+  const float* pin = in + (size_t)plane * H * W;
+  // forward: rows i - u + cy over u in [0,kh) -> tile starts at i0 - cy (symmetric halo)
+  for (int e = tid; e < th * tw; e += 256) {
+    const int ti = e / tw, tj = e % tw;
+    int gi = (i0 - cy + ti) % H;
+    if (gi < 0) gi += H;
+    int gj = (j0 - cx + tj) % W;
+    if (gj < 0) gj += W;
+    st[ti * TILE_E + tj] = pin[(size_t)gi * W + gj];
+  }
+  __syncthreads();
+  float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+  const int ty = threadIdx.y, tx = threadIdx.x;
+  for (int u = 0; u < kh; ++u) {
+    const float* r0 = st + (ty + u) * TILE_E + tx;
+    const float* r1 = r0 + 16 * TILE_E;
+    const float* kr = sk + u * kw;
+    for (int v = 0; v < kw; ++v) {
+      const float kv = kr[v];
+      acc[0][0] = fmaf(kv, r0[v], acc[0][0]);
+      acc[0][1] = fmaf(kv, r0[v + 16], acc[0][1]);
+      acc[1][0] = fmaf(kv, r1[v], acc[1][0]);
+      acc[1][1] = fmaf(kv, r1[v + 16], acc[1][1]);
+    }
+  }
+  const float tg = (epi >= DE_SAT_RES) ? tanhf(gain) : 1.f;
+  double part = 0.0;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int bb = 0; bb < 2; ++bb) {
+      const int i = i0 + ty + 16 * a, j = j0 + tx + 16 * bb;
+      if (i >= H || j >= W) continue;
+      const size_t idx = (size_t)plane * H * W + (size_t)i * W + j;
+      const float q = acc[a][bb];
+      float o;
+      if (epi == DE_PLAIN) {
+        o = q;
+      } else if (epi == DE_LIN_RES) {
+        const float e = q - (y ? y[idx] : 0.f);
+        part += 0.5 * (double)e * (double)e;
+        o = e;
+      } else if (epi == DE_SAT_PLAIN) {
+        o = tanhf(gain * q) / tg;
+      } else if (epi == DE_SAT_RES) {
+        const float t = tanhf(gain * q);
+        const float e = t / tg - y[idx];
+        part += 0.5 * (double)e * (double)e;
+        o = (gain / tg) * (1.f - t * t) * e;
+      } else {  // DE_SAT_JW: Jacobian weight applied to r (passed as y)
+        const float t = tanhf(gain * q);
+        o = (gain / tg) * (1.f - t * t) * y[idx];
+      }
+      out[idx] = o;
+    }
+  if (fsum != nullptr && (epi == DE_LIN_RES || epi == DE_SAT_RES)) {
+    const double s = block_sum(part, red);
+    if (tid == 0) atomicAdd(fsum + b, s);
+  }
+}
+
+__global__ void mask_res_kernel(int c, int hw, const uint8_t* __restrict__ m,
+                                const float* __restrict__ in, const float* __restrict__ y,
+                                float* __restrict__ out, double* __restrict__ fsum, int plain) {
+  __shared__ double red[32];
+  const int plane = blockIdx.y;  // b * c + ch
+  const int b = plane / c;
+  double part = 0.0;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < hw; p += gridDim.x * blockDim.x) {
+    const size_t idx = (size_t)plane * hw + p;
+    const float mv = (float)m[(size_t)b * hw + p];
+    if (plain) {
+      out[idx] = mv * in[idx];
+    } else {
+      const float e = mv * in[idx] - (y ? y[idx] : 0.f);
+      part += 0.5 * (double)e * (double)e;
+      out[idx] = mv * e;
+    }
+  }
+  if (fsum != nullptr && !plain) {
+    const double s = block_sum(part, red);
+    if (threadIdx.x == 0) atomicAdd(fsum + b, s);
+  }
+}
+
+static cudaError_t blur_launch(const OpDev& op, int n, int c, int H, int W, int flip,
+                               const float* in, const float* y, float* out, double* fsum,
+                               int epi, cudaStream_t st) {
+  if (op.kh > MAXK || op.kw > MAXK) return cudaErrorInvalidValue;
+  dim3 grid((W + BT - 1) / BT, (H + BT - 1) / BT, n * c), block(16, 16);
+  blur_tile_kernel<<<grid, block, 0, st>>>(c, H, W, op.kh, op.kw, op.kernel, flip, in, y, out,
+                                           fsum, epi, op.gain);
+  return cudaGetLastError();
+}
+
+static cudaError_t mask_launch(const OpDev& op, int n, int c, int H, int W, const float* in,
+                               const float* y, float* out, double* fsum, int plain,
+                               cudaStream_t st) {
+  const int hw = H * W;
+  dim3 grid(std::min((hw + 255) / 256, 64), n * c);
+  mask_res_kernel<<<grid, 256, 0, st>>>(c, hw, op.mask, in, y, out, fsum, plain);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_data_fwd(const OpDev& op, int n, int c, int H, int W, const float* in,
+                            const float* y, float* out, double* fsum, cudaStream_t st) {
+  if (op.kind == IDEQ_OP_MASK) return mask_launch(op, n, c, H, W, in, y, out, fsum, 0, st);
+  return blur_launch(op, n, c, H, W, 1, in, y, out, fsum,
+                     op.kind == IDEQ_OP_SATBLUR ? DE_SAT_RES : DE_LIN_RES, st);
+}
+
+cudaError_t launch_blur_adj(const OpDev& op, int n, int c, int H, int W, const float* in,
+                            float* out, cudaStream_t st) {
+  return blur_launch(op, n, c, H, W, 0, in, nullptr, out, nullptr, DE_PLAIN, st);
+}
+
+cudaError_t launch_apply_A(const OpDev& op, int n, int c, int H, int W, const float* x,
+                           float* Ax, cudaStream_t st) {
+  if (op.kind == IDEQ_OP_MASK) return mask_launch(op, n, c, H, W, x, nullptr, Ax, nullptr, 1, st);
+  return blur_launch(op, n, c, H, W, 1, x, nullptr, Ax, nullptr,
+                     op.kind == IDEQ_OP_SATBLUR ? DE_SAT_PLAIN : DE_PLAIN, st);
+}
+
+cudaError_t launch_sat_jt_weight(const OpDev& op, int n, int c, int H, int W, const float* lin,
+                                 const float* r, float* tmp, cudaStream_t st) {
+  return blur_launch(op, n, c, H, W, 1, lin, r, tmp, nullptr, DE_SAT_JW, st);
+}
+
+// ===================================================================== iteration
+
+// z = x + beta_b (x - x_prev), beta_b per image (0 after a restart or once frozen).
+__global__ void extrapolate_kernel(int per_img, long long total, const float* __restrict__ x,
+                                   const float* __restrict__ xp, const float* __restrict__ beta,
+                                   float* __restrict__ z) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float bb = beta[i / per_img];
+    const float xv = x[i];
+    z[i] = fmaf(bb, xv - xp[i], xv);
+  }
+}
+
+__global__ void extrapolate4_kernel(int per4, long long total4, const float4* __restrict__ x,
+                                    const float4* __restrict__ xp,
+                                    const float* __restrict__ beta, float4* __restrict__ z) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total4;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float bb = beta[i / per4];
+    const float4 a = x[i], p = xp[i];
+    z[i] = make_float4(fmaf(bb, a.x - p.x, a.x), fmaf(bb, a.y - p.y, a.y),
+                       fmaf(bb, a.z - p.z, a.z), fmaf(bb, a.w - p.w, a.w));
+  }
+}
+
+cudaError_t launch_extrapolate(int n, int per_img, const float* x, const float* xp,
+                               const float* beta_eff, float* z, cudaStream_t st) {
+  const long long total = (long long)n * per_img;
+  if (per_img % 4 == 0) {
+    const long long t4 = total / 4;
+    const int blocks = (int)std::min<long long>((t4 + 255) / 256, 152 * 8);
+    extrapolate4_kernel<<<blocks, 256, 0, st>>>(per_img / 4, t4, (const float4*)x,
+                                                (const float4*)xp, beta_eff, (float4*)z);
+  } else {
+    const int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 8);
+    extrapolate_kernel<<<blocks, 256, 0, st>>>(per_img, total, x, xp, beta_eff, z);
+  }
+  return cudaGetLastError();
+}
+
+int update_blocks_per_image(int per_img) {
+  const int b = (per_img + 256 * 16 - 1) / (256 * 16);
+  return std::max(1, std::min(b, 64));
+}
+
+// x_new = z - tau (grad f + lambda grad g) for running images (RED step at z,
+// Eq. ideq), with per-block FP64 partial sums of ||x_new - x||^2 and ||x||^2.
+// Frozen images are left untouched.
+__global__ void __launch_bounds__(256) red_update_kernel(
+    int per_img, const float* __restrict__ z, const float* __restrict__ gf,
+    const float* __restrict__ gg, const float* __restrict__ x, float* __restrict__ xn,
+    float lam, float tau, const int* __restrict__ status, double* __restrict__ part_s,
+    double* __restrict__ part_x) {
+  __shared__ double red[32];
+  const int b = blockIdx.y;
+  const int nblk = gridDim.x;
+  const bool run = status == nullptr || status[b] == IDEQ_IMG_RUNNING;
+  double ss = 0.0, sx = 0.0;
+  const size_t base = (size_t)b * per_img;
+  if (run) {
+    if ((per_img & 3) == 0) {
+      const int n4 = per_img >> 2;
+      const float4* z4 = (const float4*)(z + base);
+      const float4* f4 = (const float4*)(gf + base);
+      const float4* g4 = (const float4*)(gg + base);
+      const float4* x4 = (const float4*)(x + base);
+      float4* o4 = (float4*)(xn + base);
+      for (int i = blockIdx.x * 256 + threadIdx.x; i < n4; i += nblk * 256) {
+        const float4 zv = z4[i], fv = f4[i], gv = g4[i], xv = x4[i];
+        float4 o;
+        o.x = zv.x - tau * (fv.x + lam * gv.x);
+        o.y = zv.y - tau * (fv.y + lam * gv.y);
+        o.z = zv.z - tau * (fv.z + lam * gv.z);
+        o.w = zv.w - tau * (fv.w + lam * gv.w);
+        o4[i] = o;
+        const double d0 = (double)o.x - xv.x, d1 = (double)o.y - xv.y;
+        const double d2 = (double)o.z - xv.z, d3 = (double)o.w - xv.w;
+        ss += d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3;
+        sx += (double)xv.x * xv.x + (double)xv.y * xv.y + (double)xv.z * xv.z +
+              (double)xv.w * xv.w;
+      }
+    } else {
+      for (int i = blockIdx.x * 256 + threadIdx.x; i < per_img; i += nblk * 256) {
+        const float o = z[base + i] - tau * (gf[base + i] + lam * gg[base + i]);
+        xn[base + i] = o;
+        const double d = (double)o - x[base + i];
+        ss += d * d;
+        sx += (double)x[base + i] * x[base + i];
+      }
+    }
+  }
+  const double ts = block_sum(ss, red);
+  const double tx = block_sum(sx, red);
+  if (threadIdx.x == 0) {
+    part_s[(size_t)b * nblk + blockIdx.x] = ts;
+    part_x[(size_t)b * nblk + blockIdx.x] = tx;
+  }
+}
+
+cudaError_t launch_red_update(int n, int per_img, int nblk, const float* z, const float* gf,
+                              const float* gg, const float* x, float* xn, float lam, float tau,
+                              const int* status, double* part_s, double* part_x,
+                              cudaStream_t st) {
+  dim3 grid(nblk, n);
+  red_update_kernel<<<grid, 256, 0, st>>>(per_img, z, gf, gg, x, xn, lam, tau, status, part_s,
+                                          part_x);
+  return cudaGetLastError();
+}
+
+// Per-image bookkeeping after each update (Algorithm 1 and the stopping rule of
+// App. D.1.3), one warp per image: sum the partials in a fixed order, then
+//   k += 1, total += 1, S += ||dx||^2;
+//   non-finite step            -> DIVERGED (frozen)
+//   ||dx|| < tol ||x^k||       -> CONVERGED (frozen)
+//   total == max_iter          -> MAXITER (frozen)
+//   k S > B^2                  -> restart: k = 0, S = 0, next beta 0.
+__global__ void finalize_kernel(int n, int nblk, SolverDev s, int parity_new, float beta,
+                                float B, double tol, int max_iter, float lam, int logic) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __shared__ int run_cnt[32];
+  int my_run = 0;
+  for (int b = wid; b < n; b += nw) {
+    double ss = 0.0, sx = 0.0;
+    for (int i = lane; i < nblk; i += 32) {
+      ss += s.part_s[(size_t)b * nblk + i];
+      sx += s.part_x[(size_t)b * nblk + i];
+    }
+    ss = warp_sum(ss);
+    sx = warp_sum(sx);
+    if (lane == 0) {
+      const bool running = s.status[b] == IDEQ_IMG_RUNNING;
+      if (running) {
+        const double rel = sx > 0.0 ? sqrt(ss / sx) : INFINITY;
+        s.rel[b] = rel;
+        s.energy[b] = s.fsum[b] + (double)lam * s.gsum[b];
+        s.parity[b] = parity_new;
+        s.total[b] += 1;
+        if (logic) {
+          s.k[b] += 1;
+          s.S[b] += ss;
+          int st = IDEQ_IMG_RUNNING;
+          float be = beta;
+          if (!isfinite(ss)) {
+            st = IDEQ_IMG_DIVERGED;
+          } else if (tol > 0.0 && sqrt(ss) < tol * sqrt(sx)) {
+            st = IDEQ_IMG_CONVERGED;
+          } else if (s.total[b] >= max_iter) {
+            st = IDEQ_IMG_MAXITER;
+          } else if (isfinite(B) && B > 0.f && (double)s.k[b] * s.S[b] > (double)B * B) {
+            s.k[b] = 0;
+            s.S[b] = 0.0;
+            s.restarts[b] += 1;
+            be = 0.f;
+          }
+          s.status[b] = st;
+          s.beta_eff[b] = st == IDEQ_IMG_RUNNING ? be : 0.f;
+          if (st == IDEQ_IMG_RUNNING) my_run += 1;
+        }
+      }
+      s.fsum[b] = 0.0;
+      s.gsum[b] = 0.0;
+    }
+  }
+  if (lane == 0) run_cnt[wid] = my_run;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int i = 0; i < nw; ++i) t += run_cnt[i];
+    *s.n_running = t;
+  }
+}
+
+cudaError_t launch_finalize(int n, int nblk, const SolverDev& s, int parity_new, float beta,
+                            float B, double tol, int max_iter, float lam, int apply_logic,
+                            cudaStream_t st) {
+  const int warps = std::min(n, 32);
+  finalize_kernel<<<1, 32 * warps, 0, st>>>(n, nblk, s, parity_new, beta, B, tol, max_iter, lam,
+                                           apply_logic);
+  return cudaGetLastError();
+}
+
+__global__ void solver_init_kernel(int n, SolverDev s, float beta) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < n) {
+    s.k[b] = 0;
+    s.total[b] = 0;
+    s.restarts[b] = 0;
+    s.status[b] = IDEQ_IMG_RUNNING;
+    s.parity[b] = 0;
+    s.beta_eff[b] = beta;  // beta of the first extrapolation
+    s.S[b] = 0.0;
+    s.rel[b] = 0.0;
+    s.fsum[b] = 0.0;
+    s.gsum[b] = 0.0;
+    s.energy[b] = 0.0;
+  }
+  if (b == 0) *s.n_running = n;
+}
+
+cudaError_t launch_solver_init(int n, const SolverDev& s, float beta, cudaStream_t st) {
+  solver_init_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, s, beta);
+  return cudaGetLastError();
+}
+
+__global__ void fill_info_kernel(int n, SolverDev s, ideq_info info) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n) return;
+  if (info.iters) info.iters[b] = s.total[b];
+  if (info.restarts) info.restarts[b] = s.restarts[b];
+  if (info.status) info.status[b] = s.status[b];
+  if (info.rel_res) info.rel_res[b] = s.rel[b];
+  if (info.energy) info.energy[b] = s.energy[b];
+}
+
+cudaError_t launch_fill_info(int n, const SolverDev& s, ideq_info info, cudaStream_t st) {
+  fill_info_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, s, info);
+  return cudaGetLastError();
+}
+
+__global__ void gather_parity_kernel(int per_img, long long total, const int* __restrict__ par,
+                                     const float* __restrict__ b0, const float* __restrict__ b1,
+                                     float* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    out[i] = par[i / per_img] ? b1[i] : b0[i];
+  }
+}
+
+cudaError_t launch_gather_parity(int n, int per_img, const int* parity, const float* b0,
+                                 const float* b1, float* out, cudaStream_t st) {
+  const long long total = (long long)n * per_img;
+  const int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 8);
+  gather_parity_kernel<<<blocks, 256, 0, st>>>(per_img, total, parity, b0, b1, out);
+  return cudaGetLastError();
+}
+
+__global__ void axpby_kernel(long long n, float a, const float* __restrict__ x, float b,
+                             const float* __restrict__ y, float* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = a * x[i] + (y ? b * y[i] : 0.f);
+}
+
+cudaError_t launch_axpby(long long n, float a, const float* x, float b, const float* y,
+                         float* out, cudaStream_t st) {
+  const int blocks = (int)std::min<long long>((n + 255) / 256, 152 * 8);
+  axpby_kernel<<<std::max(blocks, 1), 256, 0, st>>>(n, a, x, b, y, out);
+  return cudaGetLastError();
+}
+
+__global__ void zero_d_kernel(long long n, double* p) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    p[i] = 0.0;
+}
+
+cudaError_t launch_zero_d(long long n, double* p, cudaStream_t st) {
+  const int blocks = (int)std::min<long long>((n + 255) / 256, 152 * 4);
+  zero_d_kernel<<<std::max(blocks, 1), 256, 0, st>>>(n, p);
+  return cudaGetLastError();
+}
+
+// ===================================================================== weights
+//
+// GEMM B matrices [N][K] from PyTorch-layout weights (see ConvArgs):
+//   conv3 fwd    B[co][t*Cin+ci]        = W[co][ci][t]
+//   conv3 dgrad  B[ci][t*Cout+co]       = W[co][ci][8-t]        (flipped taps)
+//   down fwd     B[co][q*Cin+ci]        = W[co][ci][q]           (q = di*2+dj)
+//   down dgrad   B[q*Cin+ci][co]        = W[co][ci][q]           (pixelwise, D2S)
+//   up fwd       B[q*Cout+co][ci]       = U[ci][co][q]           (pixelwise, D2S)
+//   up dgrad     B[ci][q*Cout+co]       = U[ci][co][q]           (stride-2 gather)
+__device__ __forceinline__ long long wform_src(int form, int cin, int cout, int nn, int kk) {
+  switch (form) {
+    case WF_CONV3_FWD: { const int t = kk / cin, ci = kk % cin;
+      return ((long long)nn * cin + ci) * 9 + t; }
+    case WF_CONV3_DGRAD: { const int t = kk / cout, co = kk % cout;
+      return ((long long)co * cin + nn) * 9 + (8 - t); }
+    case WF_DOWN_FWD: { const int q = kk / cin, ci = kk % cin;
+      return ((long long)nn * cin + ci) * 4 + q; }
+    case WF_DOWN_DGRAD: { const int q = nn / cin, ci = nn % cin;
+      return ((long long)kk * cin + ci) * 4 + q; }
+    case WF_UP_FWD: { const int q = nn / cout, co = nn % cout;
+      return ((long long)kk * cout + co) * 4 + q; }
+    default: { const int q = kk / cout, co = kk % cout;  // WF_UP_DGRAD
+      return ((long long)nn * cout + co) * 4 + q; }
+  }
+}
+
+static void wform_dims(int form, int cin, int cout, int* N, int* K) {
+  switch (form) {
+    case WF_CONV3_FWD: *N = cout; *K = 9 * cin; break;
+    case WF_CONV3_DGRAD: *N = cin; *K = 9 * cout; break;
+    case WF_DOWN_FWD: *N = cout; *K = 4 * cin; break;
+    case WF_DOWN_DGRAD: *N = 4 * cin; *K = cout; break;
+    case WF_UP_FWD: *N = 4 * cout; *K = cin; break;
+    default: *N = cin; *K = 4 * cout; break;
+  }
+}
+
+__global__ void wform_kernel(int form, int cin, int cout, int N, int K,
+                             const float* __restrict__ src, float* __restrict__ d32,
+                             __nv_bfloat16* __restrict__ d16) {
+  const long long tot = (long long)N * K;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int nn = (int)(e / K), kk = (int)(e % K);
+    const float v = src[wform_src(form, cin, cout, nn, kk)];
+    if (d32) d32[e] = v;
+    if (d16) d16[e] = __float2bfloat16_rn(v);
+  }
+}
+
+__global__ void wunform_kernel(int form, int cin, int cout, int N, int K,
+                               const float* __restrict__ g, float* __restrict__ dst) {
+  const long long tot = (long long)N * K;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int nn = (int)(e / K), kk = (int)(e % K);
+    dst[wform_src(form, cin, cout, nn, kk)] += g[e];
+  }
+}
+
+cudaError_t launch_weight_form(int form, int cin, int cout, const float* src, float* dst_f32,
+                               void* dst_bf16, cudaStream_t st) {
+  int N, K;
+  wform_dims(form, cin, cout, &N, &K);
+  const long long tot = (long long)N * K;
+  const int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
+  wform_kernel<<<blocks, 256, 0, st>>>(form, cin, cout, N, K, src, dst_f32,
+                                       (__nv_bfloat16*)dst_bf16);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_weight_unform(int form, int cin, int cout, const float* g, float* dst,
+                                 cudaStream_t st) {
+  int N, K;
+  wform_dims(form, cin, cout, &N, &K);
+  const long long tot = (long long)N * K;
+  const int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
+  wunform_kernel<<<blocks, 256, 0, st>>>(form, cin, cout, N, K, g, dst);
+  return cudaGetLastError();
+}
+
+}  // namespace ideq

@@ -1,0 +1,81 @@
+// Network weights and per-shape execution plans of the regulariser network.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include <string>
+#include <vector>
+
+#include "ideq_internal.h"
+
+namespace ideq {
+
+enum LayerKind { LK_CONV3 = 0, LK_DOWN = 1, LK_UP = 2 };
+
+struct Layer {
+  int kind, cin, cout;  // cin/cout of the layer as written in PyTorch
+  long long off;        // offset in the flat weight vector
+  long long numel;
+  int fwd_form, dg_form;
+  float* fwd32 = nullptr;
+  float* dg32 = nullptr;
+  __nv_bfloat16* fwd16 = nullptr;
+  __nv_bfloat16* dg16 = nullptr;
+};
+
+// Flat weight vector + its GEMM forms (f32 and bf16, forward and input-gradient).
+struct NetWeights {
+  ideq_net_desc desc{};
+  long long nparams = 0;
+  float* master = nullptr;  // device, PyTorch layout
+  std::vector<Layer> layers;
+  std::vector<void*> allocs;
+  ~NetWeights();
+  bool build(const ideq_net_desc& d, std::string* err);
+  cudaError_t upload(const float* dev_weights, cudaStream_t st);  // copy + re-form
+  cudaError_t reform(cudaStream_t st);
+};
+
+bool net_param_count(const ideq_net_desc& d, long long* count, std::vector<Layer>* layers,
+                     std::string* err);
+
+// One conv launch of a plan.
+struct Step {
+  ConvArgs a;
+  int in_bf16 = 0, out_bf16 = 0;
+  TcPlan* tc = nullptr;
+};
+
+// Execution plan for one (n, H, W, precision): activation buffers and the
+// conv op lists of the forward pass N(z) -> r = z - N(z) and of the reverse
+// pass grad = r - J_N(z)^T r.  z, r and grad are plan-owned f32 NCHW buffers.
+struct NetPlan {
+  int n = 0, c = 0, H = 0, W = 0, prec = 0;
+  NetWeights* w = nullptr;
+  float* z = nullptr;
+  float* r = nullptr;
+  float* grad = nullptr;
+  double* gsum = nullptr;  // per-image 1/2||r||^2, accumulated by the forward pass
+  std::vector<Step> fwd, vjp;
+  std::vector<void*> allocs;
+  double fwd_flops = 0, vjp_flops = 0;
+  ~NetPlan();
+  bool build(NetWeights* w, int n, int H, int W, int prec, double* gsum, std::string* err);
+  void* alloc(size_t bytes);
+};
+
+struct Profiler;
+cudaError_t run_steps(const std::vector<Step>& steps, int* err_flag, cudaStream_t st,
+                      Profiler* prof, long long* launches);
+
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;  // pairs
+  size_t used = 0;
+  double flops = 0;
+  long long launches = 0;
+  cudaEvent_t next();
+  ~Profiler();
+};
+
+}  // namespace ideq

@@ -1,0 +1,211 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (relative 2-norm error against the oracle):
+  FP32 arithmetic: 1e-5 for operators, the regulariser gradient, single steps and
+    full solves (float32 rounding, ~6e-8 per operation, accumulated over a few
+    hundred dependent operations per output and damped by the contractive
+    iteration).
+  BF16 network convolutions: BF16 rounds every activation to 8 significant bits
+    (relative error <= 2^-9); about 70 rounded layers in the forward and reverse
+    passes accumulate to ~1% of N(z) and J_N^T r, which are ~0.2-0.4 of ||grad g||,
+    hence 1e-2 on grad g; the solve damps it by lambda tau, hence 2e-3 on x_hat
+    and PSNR within 0.05 dB.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_common import ctx_for, op_for, rel, setup, to_np
+from oracle import nets, solver
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2605_19705_gb300 import build
+    build.build()
+
+
+def B():
+    from paper_2605_19705_gb300 import binding
+    return binding
+
+
+# ---------------------------------------------------------------- operators
+
+
+@pytest.mark.parametrize("name,over", [
+    ("C1a", dict(n=2, h=40, w=56)),                                   # 25x25 motion, ragged tiles
+    ("C1b", dict(n=2, h=40, w=56)),                                   # mask
+    ("C4", dict(n=2, h=40, w=56)),                                    # saturation after 15x15 blur
+    ("C0", dict(n=1)),                                                # 9x9 Gaussian, grey
+])
+def test_operators_match_oracle(name, over):
+    cfg, wl, net, ops, ys = setup(name, **over)
+    b = B()
+    ctx = ctx_for(cfg, wl, b.IDEQ_FP32)
+    op = op_for(cfg, wl)
+    rng = np.random.default_rng(3)
+    x = rng.uniform(0, 1, ys.shape).astype(np.float32)
+    r = rng.standard_normal(ys.shape).astype(np.float32)
+    tx, tr = torch.tensor(x, device="cuda"), torch.tensor(r, device="cuda")
+    Ax = to_np(b.ideq_apply_A(ctx, op, tx))
+    ATr = to_np(b.ideq_apply_AT(ctx, op, tr))
+    ref_A = np.stack([ops[i].A(x[i].astype(np.float64)) for i in range(len(ops))])
+    ref_AT = np.stack([ops[i].AT(r[i].astype(np.float64)) for i in range(len(ops))])
+    assert rel(Ax, ref_A) < 1e-6
+    assert rel(ATr, ref_AT) < 1e-6
+    if cfg["op"] == "satblur":
+        JT = to_np(b.ideq_apply_AT(ctx, op, tr, lin_point=tx))
+        ref = np.stack([ops[i].JAT(x[i].astype(np.float64), r[i].astype(np.float64))
+                        for i in range(len(ops))])
+        assert rel(JT, ref) < 1e-6
+
+
+def test_operator_argument_errors():
+    cfg, wl, net, ops, ys = setup("C0")
+    b = B()
+    ctx = ctx_for(cfg, wl, b.IDEQ_FP32)
+    k = torch.ones(1, 4, 4, device="cuda")  # even kernel size is rejected
+    op = b.make_operator(b.IDEQ_OP_BLUR, k)
+    x = torch.zeros(1, 1, 64, 64, device="cuda")
+    with pytest.raises(b.IdeqError) as e:
+        b.ideq_apply_A(ctx, op, x)
+    assert e.value.status == b.IDEQ_ERR_ARG
+    with pytest.raises(b.IdeqError):
+        b.ideq_grad_reg(ctx, torch.zeros(1, 3, 64, 64, device="cuda"))  # wrong channels
+
+
+# ---------------------------------------------------------------- regulariser
+
+
+@pytest.mark.parametrize("name,over,prec,tol", [
+    ("C0", dict(n=1), "fp32", 1e-5),
+    ("C0", dict(n=2, h=37, w=45), "fp32", 1e-5),
+    ("C1a", dict(n=1, h=64, w=64), "fp32", 1e-5),
+    ("C1a", dict(n=2, h=40, w=56), "fp32", 1e-5),
+    ("C1a", dict(n=1, h=64, w=64), "bf16", 1e-2),
+    ("C1a", dict(n=2, h=40, w=56), "bf16", 1e-2),
+    ("C3", dict(n=1, h=32, w=32), "fp32", 1e-5),
+])
+def test_grad_reg_matches_oracle(name, over, prec, tol):
+    cfg, wl, net, ops, ys = setup(name, **over)
+    b = B()
+    ctx = ctx_for(cfg, wl, b.IDEQ_FP32 if prec == "fp32" else b.IDEQ_BF16)
+    z = np.random.default_rng(5).uniform(0, 1, ys.shape).astype(np.float32)
+    gval = torch.zeros(z.shape[0], dtype=torch.float64, device="cuda")
+    g = to_np(b.ideq_grad_reg(ctx, torch.tensor(z, device="cuda"), g_val=gval))
+    for i in range(z.shape[0]):
+        ref, gv = nets.grad_g(net, z[i].astype(np.float64))
+        assert rel(g[i], ref) < tol, (i, rel(g[i], ref))
+        assert abs(float(gval[i]) - gv) < tol * gv
+
+
+# ---------------------------------------------------------------- iteration
+
+
+def _oracle_solve(cfg, net, ops, ys, **kw):
+    x0 = np.stack([ops[i].AT(ys[i].astype(np.float64)) for i in range(len(ops))])
+    p = dict(lam=cfg["lam"], tau=cfg["tau"], beta=cfg["beta"], B=cfg["B"], tol=cfg["tol"],
+             max_iter=cfg["max_iter"])
+    p.update(kw)
+    return solver.solve_batch(net, ops, ys.astype(np.float64), x0, p["lam"], p["tau"], p["beta"],
+                              p["B"], p["tol"], p["max_iter"])
+
+
+def _gpu_solve(cfg, wl, ys, prec, **kw):
+    b = B()
+    ctx = ctx_for(cfg, wl, prec)
+    op = op_for(cfg, wl)
+    p = dict(lam=cfg["lam"], tau=cfg["tau"], beta=cfg["beta"], B=cfg["B"], tol=cfg["tol"],
+             max_iter=cfg["max_iter"])
+    p.update(kw)
+    params = b.make_params(p["lam"], p["tau"], p["beta"], p["B"], p["tol"], p["max_iter"])
+    info = b.InfoBuffers(ys.shape[0])
+    x, st = b.ideq_solve(ctx, op, torch.tensor(ys, device="cuda"), params, info=info,
+                         allow_maxiter=True)
+    torch.cuda.synchronize()
+    return to_np(x), info, st
+
+
+def test_solve_c0_fixed_50_steps_fp32():
+    cfg, wl, net, ops, ys = setup("C0")
+    xo, infos = _oracle_solve(cfg, net, ops, ys)
+    xg, info, st = _gpu_solve(cfg, wl, ys, B().IDEQ_FP32)
+    assert int(info.iters[0]) == 50 == infos[0]["iters"]
+    assert rel(xg, xo) < 1e-5
+    assert abs(float(info.energy[0]) - infos[0]["energy"]) < 1e-5 * abs(infos[0]["energy"])
+
+
+@pytest.mark.parametrize("B_,tol", [(0.05, 1e-4), (math.inf, 1e-4)])
+def test_solve_c0_restart_and_stopping_fp32(B_, tol):
+    cfg, wl, net, ops, ys = setup("C0", n=2, h=48, w=40)
+    xo, infos = _oracle_solve(cfg, net, ops, ys, B=B_, tol=tol, max_iter=400)
+    xg, info, st = _gpu_solve(cfg, wl, ys, B().IDEQ_FP32, B=B_, tol=tol, max_iter=400)
+    for i in range(2):
+        assert abs(int(info.iters[i]) - infos[i]["iters"]) <= 1
+        assert int(info.restarts[i]) == infos[i]["restarts"]
+        assert int(info.status[i]) == infos[i]["status"]
+    assert rel(xg, xo) < 1e-5 or all(int(info.iters[i]) != infos[i]["iters"] for i in range(2))
+    if B_ < math.inf:
+        assert min(int(v) for v in info.restarts.cpu()) >= 1
+
+
+@pytest.mark.parametrize("name", ["C1a", "C1b"])
+def test_solve_unet_fp32(name):
+    cfg, wl, net, ops, ys = setup(name, n=1, h=64, w=64)
+    xg, info, st = _gpu_solve(cfg, wl, ys, B().IDEQ_FP32, max_iter=300)
+    it = int(info.iters[0])
+    assert int(info.status[0]) == solver.CONVERGED
+    # oracle run for exactly the same number of updates (the stopping test may
+    # flip by one iteration between FP32 and FP64)
+    xo, infos = _oracle_solve(cfg, net, ops, ys, tol=0.0, max_iter=it)
+    assert rel(xg, xo) < 1e-5
+    xo2, infos2 = _oracle_solve(cfg, net, ops, ys, max_iter=300)
+    assert abs(infos2[0]["iters"] - it) <= 1
+
+
+def test_solve_unet_bf16_matches_fp64_within_stated_error():
+    cfg, wl, net, ops, ys = setup("C2", n=1, h=64, w=64)
+    xo, infos = _oracle_solve(cfg, net, ops, ys, max_iter=300)
+    xg, info, st = _gpu_solve(cfg, wl, ys, B().IDEQ_BF16, max_iter=300)
+    assert int(info.status[0]) == solver.CONVERGED
+    e = rel(xg, xo)
+    assert e < 2e-3, e
+    p_o = solver.psnr(xo[0], wl["x_true"][0])
+    p_g = solver.psnr(xg[0], wl["x_true"][0])
+    assert abs(p_o - p_g) < 0.05
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("bf16", 2e-3)])
+def test_step_at_full_size_sampled_images(prec, tol):
+    """One inertial step of the full 8 x RGB 256^2 C1a batch; images 0 and 7 checked."""
+    cfg, wl, net, ops, ys = setup("C1a")
+    b = B()
+    ctx = ctx_for(cfg, wl, b.IDEQ_FP32 if prec == "fp32" else b.IDEQ_BF16)
+    op = op_for(cfg, wl)
+    rng = np.random.default_rng(11)
+    xk = np.clip(ys + 0.05 * rng.standard_normal(ys.shape), 0, 1).astype(np.float32)
+    xkm1 = np.clip(xk + 0.02 * rng.standard_normal(ys.shape), 0, 1).astype(np.float32)
+    tk, tkm1 = torch.tensor(xk, device="cuda"), torch.tensor(xkm1, device="cuda")
+    params = b.make_params(cfg["lam"], cfg["tau"], cfg["beta"])
+    info = b.InfoBuffers(8)
+    b.ideq_step(ctx, op, torch.tensor(ys, device="cuda"), tk, tkm1, params, info)
+    out = to_np(tk)
+    assert np.array_equal(to_np(tkm1), xk.astype(np.float64))
+    for i in (0, 7):
+        z = xk[i].astype(np.float64) + cfg["beta"] * (xk[i].astype(np.float64) - xkm1[i])
+        ref, fval, gval = solver.red_step(net, ops[i], ys[i].astype(np.float64), z, cfg["lam"],
+                                          cfg["tau"])
+        d_gpu = out[i] - z
+        d_ref = ref - z
+        # compare the update direction tau (grad f + lambda grad g), the part that carries
+        # the arithmetic, and the iterate itself
+        assert rel(d_gpu, d_ref) < (5e-5 if prec == "fp32" else 1e-2)
+        assert rel(out[i], ref) < tol
+        assert abs(float(info.energy[i]) - (fval + cfg["lam"] * gval)) < 1e-4 * (fval + cfg["lam"] * gval)
