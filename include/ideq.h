@@ -51,10 +51,12 @@ enum { IDEQ_IMG_RUNNING = 0, IDEQ_IMG_CONVERGED = 1, IDEQ_IMG_MAXITER = 2, IDEQ_
 enum { IDEQ_NET_CNN = 0, IDEQ_NET_UNET = 1 };
 enum { IDEQ_ACT_SOFTPLUS = 0, IDEQ_ACT_RELU = 1 };
 enum { IDEQ_OP_BLUR = 0, IDEQ_OP_MASK = 1, IDEQ_OP_SATBLUR = 2 };
-/* arithmetic of the regulariser network's convolutions; the iterate, the
- * momentum state and the data step are always float32, the step-norm and
- * energy reductions float64. */
-enum { IDEQ_FP32 = 0, IDEQ_BF16 = 1, IDEQ_BF16_FP8 = 2 };
+/* Arithmetic of the regulariser network's convolutions: operands in FP32
+ * (SIMT), BF16 or FP16 (tensor cores, FP32 accumulation), activations stored in
+ * the operand type.  The iterate, the momentum state and the data step are
+ * always float32, the step-norm and energy reductions float64.  IDEQ_BF16_FP8
+ * is reserved. */
+enum { IDEQ_FP32 = 0, IDEQ_BF16 = 1, IDEQ_BF16_FP8 = 2, IDEQ_FP16 = 3 };
 enum { IDEQ_INIT_ATY = 0, IDEQ_INIT_X0 = 1, IDEQ_INIT_WARM = 2 };
 enum { IDEQ_ADJ_JFB = 0, IDEQ_ADJ_IMPLICIT = 1 };
 

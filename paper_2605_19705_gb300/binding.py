@@ -28,7 +28,7 @@ IDEQ_IMG_RUNNING, IDEQ_IMG_CONVERGED, IDEQ_IMG_MAXITER, IDEQ_IMG_DIVERGED = 0, 1
 IDEQ_NET_CNN, IDEQ_NET_UNET = 0, 1
 IDEQ_ACT_SOFTPLUS, IDEQ_ACT_RELU = 0, 1
 IDEQ_OP_BLUR, IDEQ_OP_MASK, IDEQ_OP_SATBLUR = 0, 1, 2
-IDEQ_FP32, IDEQ_BF16, IDEQ_BF16_FP8 = 0, 1, 2
+IDEQ_FP32, IDEQ_BF16, IDEQ_BF16_FP8, IDEQ_FP16 = 0, 1, 2, 3
 IDEQ_INIT_ATY, IDEQ_INIT_X0, IDEQ_INIT_WARM = 0, 1, 2
 IDEQ_ADJ_JFB, IDEQ_ADJ_IMPLICIT = 0, 1
 

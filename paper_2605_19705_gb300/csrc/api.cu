@@ -8,6 +8,7 @@
 #include <string>
 
 #include "net.h"
+#include "net_train.h"
 
 using namespace ideq;
 
@@ -17,6 +18,7 @@ struct ideq_ctx {
   int precision = IDEQ_FP32;
   std::unique_ptr<NetWeights> w;
   std::unique_ptr<NetPlan> plan;
+  std::unique_ptr<TrainPlan> train;
   std::string err;
   int* d_err = nullptr;       // device error flag of bounded waits
   int* h_running = nullptr;   // pinned
@@ -29,6 +31,8 @@ struct ideq_ctx {
   float* xb[2] = {nullptr, nullptr};
   float* gf = nullptr;
   float* tmp = nullptr;
+  float* ubuf = nullptr;      // adjoint solution u
+  double* dot_part = nullptr;
   double* fsum = nullptr;
   double* gsum = nullptr;
   // scratch for the stand-alone operator calls
@@ -86,6 +90,7 @@ ideq_status ensure_plan(ideq_ctx* ctx, const ideq_shape& s) {
   if (p && p->n == s.n && p->H == s.h && p->W == s.w && p->prec == ctx->precision) return IDEQ_OK;
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->plan.reset();
+  ctx->train.reset();
   // solver workspace
   if (ctx->sv_mem) {
     cudaFree(ctx->sv_mem);
@@ -102,7 +107,8 @@ ideq_status ensure_plan(ideq_ctx* ctx, const ideq_shape& s) {
   };
   const size_t o_x0 = take(img), o_x1 = take(img), o_gf = take(img), o_tmp = take(img);
   const size_t o_i = take((size_t)n * 4 * 6), o_f = take((size_t)n * 4), o_d = take((size_t)n * 8 * 6);
-  const size_t o_p = take((size_t)n * nblk * 8 * 2), o_r = take(16);
+  const size_t o_p = take((size_t)n * nblk * 8 * 2), o_r = take(16), o_dp = take(128 * 8);
+  const size_t o_u = take(img);
   char* m = nullptr;
   if (cudaMalloc((void**)&m, off) != cudaSuccess) return fail(ctx, IDEQ_ERR_NOMEM, "cudaMalloc(solver workspace)");
   ctx->sv_mem = m;
@@ -127,6 +133,8 @@ ideq_status ensure_plan(ideq_ctx* ctx, const ideq_shape& s) {
   v.part_s = (double*)(m + o_p);
   v.part_x = v.part_s + (size_t)n * nblk;
   v.n_running = (int*)(m + o_r);
+  ctx->dot_part = (double*)(m + o_dp);
+  ctx->ubuf = (float*)(m + o_u);
   ctx->fsum = v.fsum;
   ctx->gsum = v.gsum;
   ctx->sv_n = n;
@@ -234,7 +242,8 @@ ideq_status ideq_num_params(const ideq_net_desc* net, int64_t* count) {
 ideq_status ideq_create(ideq_ctx** out, const ideq_net_desc* net, const float* weights,
                         int precision, void* stream) {
   if (!out || !net || !weights) return IDEQ_ERR_ARG;
-  if (precision != IDEQ_FP32 && precision != IDEQ_BF16) return IDEQ_ERR_UNSUPPORTED;
+  if (precision != IDEQ_FP32 && precision != IDEQ_BF16 && precision != IDEQ_FP16)
+    return IDEQ_ERR_UNSUPPORTED;
   std::unique_ptr<ideq_ctx> c(new ideq_ctx());
   ideq_ctx* ctx = c.get();
   CK(cudaGetDevice(&c->device));
@@ -275,7 +284,7 @@ ideq_status ideq_set_weights(ideq_ctx* ctx, const float* weights) {
 
 ideq_status ideq_set_precision(ideq_ctx* ctx, int precision) {
   if (!ctx) return IDEQ_ERR_ARG;
-  if (precision != IDEQ_FP32 && precision != IDEQ_BF16)
+  if (precision != IDEQ_FP32 && precision != IDEQ_BF16 && precision != IDEQ_FP16)
     return fail(ctx, IDEQ_ERR_UNSUPPORTED, "precision");
   ctx->precision = precision;
   return IDEQ_OK;
@@ -398,10 +407,87 @@ ideq_status ideq_solve(ideq_ctx* ctx, const ideq_operator* op, ideq_shape shape,
   return IDEQ_OK;
 }
 
-ideq_status ideq_solve_backward(ideq_ctx* ctx, const ideq_operator*, ideq_shape, const float*,
-                                const float*, const float*, const ideq_params*,
-                                const ideq_adj_params*, float*, float*, ideq_info*) {
-  return fail(ctx, IDEQ_ERR_UNSUPPORTED, "backward not built yet");
+ideq_status ideq_solve_backward(ideq_ctx* ctx, const ideq_operator* op, ideq_shape shape,
+                                const float* y, const float* x_bar, const float* dl_dx,
+                                const ideq_params* p, const ideq_adj_params* ap, float* dl_dtheta,
+                                float* dl_dlambda, ideq_info* info) {
+  if (!ctx || !y || !x_bar || !dl_dx || !dl_dtheta || !dl_dlambda || !ap || !shape_ok(shape))
+    return fail(ctx, IDEQ_ERR_ARG, "bad arguments");
+  ideq_status s = check_params(ctx, p);
+  if (s != IDEQ_OK) return s;
+  OpDev od;
+  if ((s = check_op(ctx, op, shape, &od)) != IDEQ_OK) return s;
+  if (od.kind == IDEQ_OP_SATBLUR)
+    return fail(ctx, IDEQ_ERR_UNSUPPORTED, "backward supports linear operators (blur, mask)");
+  if (ap->mode != IDEQ_ADJ_JFB && ap->mode != IDEQ_ADJ_IMPLICIT)
+    return fail(ctx, IDEQ_ERR_ARG, "adjoint mode");
+  if (ap->mode == IDEQ_ADJ_IMPLICIT && (ap->max_iter < 1 || !(ap->tol > 0.0) ||
+                                        !(ap->beta >= 0.f && ap->beta < 1.f)))
+    return fail(ctx, IDEQ_ERR_ARG, "adjoint tol > 0, max_iter >= 1, 0 <= beta < 1");
+  if ((s = ensure_plan(ctx, shape)) != IDEQ_OK) return s;
+  if (!ctx->train) {
+    std::unique_ptr<TrainPlan> tp(new TrainPlan());
+    std::string e;
+    if (!tp->build(ctx->w.get(), shape.n, shape.h, shape.w, ctx->precision, ctx->gsum, &e))
+      return fail(ctx, IDEQ_ERR_UNSUPPORTED, "training plan: " + e);
+    ctx->train = std::move(tp);
+  }
+  TrainPlan* T = ctx->train.get();
+  cudaStream_t st = ctx->stream;
+  const int n = shape.n, per = ctx->sv_per;
+  const size_t bytes = (size_t)n * per * 4;
+  // fixed point: N(xbar), r and grad g(xbar) with every t-chain cotangent kept
+  CK(cudaMemcpyAsync(T->z, x_bar, bytes, cudaMemcpyDeviceToDevice, st));
+  CK(launch_zero_d(n, ctx->gsum, st));
+  CK(run_steps(T->fwd, ctx->d_err, st, &ctx->prof, &ctx->launches));
+  CK(run_steps(T->tchain, ctx->d_err, st, &ctx->prof, &ctx->launches));
+  // adjoint: u = J_R^T u + v with J_R = I - tau (H_f + lambda H_g) at xbar
+  if (ap->mode == IDEQ_ADJ_IMPLICIT) {
+    CK(cudaMemcpyAsync(ctx->xb[0], dl_dx, bytes, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(ctx->xb[1], dl_dx, bytes, cudaMemcpyDeviceToDevice, st));
+    CK(launch_solver_init(n, ctx->sv, 0.f, st));
+    for (int it = 0; it < ap->max_iter; ++it) {
+      const int par = it & 1;
+      float* uk = ctx->xb[par];
+      float* up = ctx->xb[1 - par];
+      CK(launch_extrapolate(n, per, uk, up, ctx->sv.beta_eff, T->zd, st));
+      CK(run_steps(T->jvp, ctx->d_err, st, &ctx->prof, &ctx->launches));
+      CK(run_steps(T->pchain, ctx->d_err, st, &ctx->prof, &ctx->launches));
+      CK(data_grad(ctx, od, shape, T->zd, nullptr, ctx->gf, ctx->tmp, ctx->sv.fsum));
+      CK(launch_red_update(n, per, ctx->sv_nblk, T->zd, ctx->gf, T->hvp, uk, up, p->lambda,
+                           p->tau, ctx->sv.status, ctx->sv.part_s, ctx->sv.part_x, st, dl_dx));
+      CK(launch_finalize(n, ctx->sv_nblk, ctx->sv, 1 - par, ap->beta, INFINITY, ap->tol,
+                         ap->max_iter, 0.f, 1, st));
+      ctx->launches += 3;
+      if ((it & 1) == 1 && it + 1 < ap->max_iter) {
+        CK(cudaMemcpyAsync(ctx->h_running, ctx->sv.n_running, 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (*ctx->h_running == 0) break;
+      }
+    }
+    CK(launch_gather_parity(n, per, ctx->sv.parity, ctx->xb[0], ctx->xb[1], ctx->ubuf, st));
+  } else {
+    CK(cudaMemcpyAsync(ctx->ubuf, dl_dx, bytes, cudaMemcpyDeviceToDevice, st));
+    CK(launch_solver_init(n, ctx->sv, 0.f, st));
+  }
+  // dl/dlambda = -tau <u, grad g(xbar)>
+  CK(launch_dot((long long)n * per, ctx->ubuf, T->grad, -p->tau, ctx->dot_part, dl_dlambda, st));
+  // dl/dtheta = -tau lambda d<u, grad g_theta(xbar)>/dtheta = +tau lambda gW(rdot, r)
+  CK(cudaMemcpyAsync(T->zd, ctx->ubuf, bytes, cudaMemcpyDeviceToDevice, st));
+  CK(run_steps(T->jvp, ctx->d_err, st, &ctx->prof, &ctx->launches));
+  CK(run_steps(T->pchain, ctx->d_err, st, &ctx->prof, &ctx->launches));
+  CK(cudaMemsetAsync(dl_dtheta, 0, ctx->w->nparams * 4, st));
+  CK(T->run_wgrad(dl_dtheta, p->tau * p->lambda, true, st, &ctx->launches));
+  ctx->launches += 2;
+  if (info) CK(launch_fill_info(n, ctx->sv, *info, st));
+  if ((s = check_timeout(ctx)) != IDEQ_OK) return s;
+  if (ap->mode == IDEQ_ADJ_IMPLICIT) {
+    std::vector<int> hs(n);
+    CK(cudaMemcpy(hs.data(), ctx->sv.status, n * 4, cudaMemcpyDeviceToHost));
+    for (int v : hs)
+      if (v != IDEQ_IMG_CONVERGED) return fail(ctx, IDEQ_ADJ_MAXITER, "adjoint solve did not converge");
+  }
+  return IDEQ_OK;
 }
 
 ideq_status ideq_warm_set(ideq_ctx* ctx, const ideq_net_desc*, const float*) {

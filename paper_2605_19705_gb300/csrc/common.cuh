@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cstdint>
 #include <cstdio>
 
@@ -10,16 +11,16 @@
 
 namespace ideq {
 
-// element storage of network activations
-enum DType { F32 = 0, BF16 = 1 };
 
 template <typename T> IDEQ_DEV float ld_f(const T* p);
 template <> IDEQ_DEV float ld_f<float>(const float* p) { return *p; }
 template <> IDEQ_DEV float ld_f<__nv_bfloat16>(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+template <> IDEQ_DEV float ld_f<__half>(const __half* p) { return __half2float(*p); }
 
 template <typename T> IDEQ_DEV T from_f(float v);
 template <> IDEQ_DEV float from_f<float>(float v) { return v; }
 template <> IDEQ_DEV __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <> IDEQ_DEV __half from_f<__half>(float v) { return __float2half_rn(v); }
 
 IDEQ_DEV double warp_sum(double v) {
 #pragma unroll

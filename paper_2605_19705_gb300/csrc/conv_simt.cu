@@ -28,8 +28,6 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
   const int HW = a.H * a.W;
   const TIn* __restrict__ in = (const TIn*)a.in;
   const float* __restrict__ inf = (const float*)a.in;
-  const TIn* __restrict__ wB = (const TIn*)a.wB;  // unused type for weights below
-  (void)wB;
   const float* __restrict__ wf = (const float*)a.wB;
 
   // rows this thread loads for A
@@ -189,12 +187,16 @@ static cudaError_t launch_typed(const ConvArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_conv_simt(const ConvArgs& a, int in_bf16, int out_bf16, cudaStream_t st) {
+cudaError_t launch_conv_simt(const ConvArgs& a, int in_dt, int out_dt, cudaStream_t st) {
   if (a.M() == 0) return cudaSuccess;
-  if (in_bf16 && out_bf16) return launch_typed<__nv_bfloat16, __nv_bfloat16>(a, st);
-  if (in_bf16) return launch_typed<__nv_bfloat16, float>(a, st);
-  if (out_bf16) return launch_typed<float, __nv_bfloat16>(a, st);
-  return launch_typed<float, float>(a, st);
+  if (in_dt == DT_BF16 && out_dt == DT_BF16) return launch_typed<__nv_bfloat16, __nv_bfloat16>(a, st);
+  if (in_dt == DT_F16 && out_dt == DT_F16) return launch_typed<__half, __half>(a, st);
+  if (in_dt == DT_BF16 && out_dt == DT_F32) return launch_typed<__nv_bfloat16, float>(a, st);
+  if (in_dt == DT_F16 && out_dt == DT_F32) return launch_typed<__half, float>(a, st);
+  if (in_dt == DT_F32 && out_dt == DT_BF16) return launch_typed<float, __nv_bfloat16>(a, st);
+  if (in_dt == DT_F32 && out_dt == DT_F16) return launch_typed<float, __half>(a, st);
+  if (in_dt == DT_F32 && out_dt == DT_F32) return launch_typed<float, float>(a, st);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace ideq

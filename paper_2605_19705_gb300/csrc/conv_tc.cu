@@ -1,15 +1,20 @@
 // tcgen05 (5th-generation tensor core) implicit-GEMM convolution for sm_103a.
 //
-// One CTA computes a 128 x BN tile of D = A * B^T (see ConvArgs):
+// Persistent kernel, one CTA per SM, looping over 128 x BN tiles of
+// D = A * B^T (see ConvArgs):
 //   warp 0      TMA producer: per K chunk of 64 channels, one box of 128 pixels
-//               x 64 channels of the NHWC bf16 activation (tap-shifted; the
-//               zero padding of the convolution is the TMA out-of-bounds fill)
-//               and one box of BN x 64 weights, into a STAGES-deep ring.
-//   warp 1      allocates TMEM and issues tcgen05.mma (M=128, N=BN, K=16,
-//               bf16 x bf16 -> f32) from one elected lane; tcgen05.commit
-//               frees ring slots and finally signals the accumulator.
-//   warps 2..5  epilogue: tcgen05.ld the f32 accumulator (one pixel row per
-//               thread), apply the fused epilogue, store bf16 NHWC.
+//               x 64 channels of the NHWC 16-bit (bf16 or f16) activation
+//               (tap-shifted; the zero padding of the convolution is the TMA
+//               out-of-bounds fill) and one box of BN x 64 weights, into a
+//               STAGES-deep ring that runs across tile boundaries.
+//   warp 1      allocates 2 x BN TMEM columns (two accumulators) and issues
+//               tcgen05.mma (M=128, N=BN, K=16, 16-bit x 16-bit -> f32) from one
+//               elected lane; tcgen05.commit frees ring slots and hands a
+//               finished accumulator to the epilogue.
+//   warps 2..9  epilogue: tcgen05.ld the f32 accumulator (one pixel row per
+//               thread, half of the columns per warp), apply the fused
+//               epilogue, store 16-bit NHWC, and release the accumulator, so
+//               that it overlaps the MMAs of the next tile.
 // Shared-memory operands use the 128-byte swizzle that TMA writes and the
 // UMMA descriptor reads (8-row atoms of 128 B, stride 1024 B).
 // Every mbarrier wait is bounded (about 2 s of %globaltimer); an expired wait
@@ -17,6 +22,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -28,20 +34,20 @@ namespace ideq {
 struct TcArgs {
   int mode, outmap, epi, act;
   int n, H, W, Cin, Cout, N;
-  int Wt, Ht, tiles_w, tiles_h, nk, cpt;
-  __nv_bfloat16* out;
-  __nv_bfloat16* out2;
-  const __nv_bfloat16* aux0;
-  const __nv_bfloat16* aux1;
-  const __nv_bfloat16* aux2;
+  int Wt, Ht, tiles_w, tiles_h, tiles_n, nk, cpt;
+  void* out;
+  void* out2;
+  const void* aux0;
+  const void* aux1;
+  const void* aux2;
   int* err;
 };
 
 struct TcPlan {
   CUtensorMap tmA;
   CUtensorMap tmB;
-  int bn = 0, stages = 0;
-  int Wt = 0, Ht = 0, tiles_w = 0, tiles_h = 0, nk = 0, cpt = 0;
+  int bn = 0, stages = 0, dt = DT_BF16;
+  int Wt = 0, Ht = 0, tiles_w = 0, tiles_h = 0, tiles_n = 0, nk = 0, cpt = 0;
   dim3 grid;
   size_t smem = 0;
 };
@@ -140,12 +146,17 @@ IDEQ_DEV uint64_t umma_desc_sw128(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor of kind::f16: D f32 (bits [4,6) = 1), A and B bf16
-// (bits [7,10) and [10,13) = 1), both K-major, N >> 3 in [17,23), M >> 4 in [24,29).
-__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+// Instruction descriptor of kind::f16: D f32 (bits [4,6) = 1), A and B of the
+// same 16-bit format (bits [7,10) and [10,13): 0 = f16, 1 = bf16), both
+// K-major, N >> 3 in [17,23), M >> 4 in [24,29).
+__host__ __device__ constexpr uint32_t umma_idesc_16(int M, int N, uint32_t fmt) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
 }
+
+template <typename T> struct Fmt;
+template <> struct Fmt<__nv_bfloat16> { static constexpr uint32_t v = 1; };
+template <> struct Fmt<__half> { static constexpr uint32_t v = 0; };
 
 IDEQ_DEV void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                         uint32_t accumulate) {
@@ -177,15 +188,29 @@ IDEQ_DEV void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-IDEQ_DEV void load_bf16x16(const __nv_bfloat16* p, float (&v)[16]) {
+IDEQ_DEV float2 to_f2(__nv_bfloat162 h) { return __bfloat1622float2(h); }
+IDEQ_DEV float2 to_f2(__half2 h) { return __half22float2(h); }
+template <typename T> struct Pair;
+template <> struct Pair<__nv_bfloat16> {
+  using t = __nv_bfloat162;
+  static IDEQ_DEV t make(float a, float b) { return __floats2bfloat162_rn(a, b); }
+};
+template <> struct Pair<__half> {
+  using t = __half2;
+  static IDEQ_DEV t make(float a, float b) { return __floats2half2_rn(a, b); }
+};
+
+template <typename T>
+IDEQ_DEV void load16x16(const T* p, float (&v)[16]) {
+  using P2 = typename Pair<T>::t;
   const uint4* q = (const uint4*)p;
   const uint4 a = q[0], b = q[1];
-  const __nv_bfloat162* h0 = (const __nv_bfloat162*)&a;
-  const __nv_bfloat162* h1 = (const __nv_bfloat162*)&b;
+  const P2* h0 = (const P2*)&a;
+  const P2* h1 = (const P2*)&b;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const float2 f0 = __bfloat1622float2(h0[i]);
-    const float2 f1 = __bfloat1622float2(h1[i]);
+    const float2 f0 = to_f2(h0[i]);
+    const float2 f1 = to_f2(h1[i]);
     v[2 * i] = f0.x;
     v[2 * i + 1] = f0.y;
     v[8 + 2 * i] = f1.x;
@@ -193,14 +218,16 @@ IDEQ_DEV void load_bf16x16(const __nv_bfloat16* p, float (&v)[16]) {
   }
 }
 
-IDEQ_DEV void store_bf16x16(__nv_bfloat16* p, const float (&v)[16]) {
+template <typename T>
+IDEQ_DEV void store16x16(T* p, const float (&v)[16]) {
+  using P2 = typename Pair<T>::t;
   uint4 a, b;
-  __nv_bfloat162* h0 = (__nv_bfloat162*)&a;
-  __nv_bfloat162* h1 = (__nv_bfloat162*)&b;
+  P2* h0 = (P2*)&a;
+  P2* h1 = (P2*)&b;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    h0[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-    h1[i] = __floats2bfloat162_rn(v[8 + 2 * i], v[8 + 2 * i + 1]);
+    h0[i] = Pair<T>::make(v[2 * i], v[2 * i + 1]);
+    h1[i] = Pair<T>::make(v[8 + 2 * i], v[8 + 2 * i + 1]);
   }
   uint4* q = (uint4*)p;
   q[0] = a;
@@ -209,10 +236,37 @@ IDEQ_DEV void store_bf16x16(__nv_bfloat16* p, const float (&v)[16]) {
 
 // ------------------------------------------------------------------ kernel
 
-constexpr int TC_THREADS = 192;
-constexpr int A_BYTES = 128 * 128;  // 128 pixel rows x 64 bf16
+constexpr int EPI_WARPS = 8;
+constexpr int TC_THREADS = 64 + 32 * EPI_WARPS;
+constexpr int A_BYTES = 128 * 128;  // 128 pixel rows x 64 16-bit channels
 
-template <int BN, int STAGES>
+IDEQ_DEV void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+struct TileCoord {
+  int img, h0, w0, n0;
+};
+
+IDEQ_DEV TileCoord tile_coord(const TcArgs& a, int t, int bn) {
+  const int per_img = a.tiles_h * a.tiles_w;
+  const int tiles_m = a.n * per_img;
+  const int nidx = t / tiles_m, m = t - nidx * tiles_m;
+  TileCoord c;
+  c.img = m / per_img;
+  const int rr = m - c.img * per_img;
+  c.h0 = (rr / a.tiles_w) * a.Ht;
+  c.w0 = (rr % a.tiles_w) * a.Wt;
+  c.n0 = nidx * bn;
+  return c;
+}
+
+// Persistent CTA (one per SM): tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...
+// The smem ring runs across tile boundaries; the TMEM accumulator is double
+// buffered (2 x BN columns) so that the epilogue of one tile overlaps the MMAs
+// of the next.  Barriers: full/empty per ring slot, tfull/tempty per TMEM
+// buffer (tempty counts one arrival per epilogue warp), drain for the error path.
+template <typename T, int BN, int STAGES>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     conv_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                    const __grid_constant__ CUtensorMap tmB, TcArgs a) {
@@ -222,35 +276,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
   uint8_t* sB = smem + STAGES * A_BYTES;
-  uint64_t* bars = (uint64_t*)(sB + STAGES * B_BYTES);  // full[S], empty[S], accum
-  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 1);
+  uint64_t* bars = (uint64_t*)(sB + STAGES * B_BYTES);
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 5);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
-  const uint32_t accb = smem_u32(bars + 2 * STAGES);
-
-  // tile coordinates
-  const int mt = blockIdx.x;
-  const int per_img = a.tiles_h * a.tiles_w;
-  const int img = mt / per_img;
-  const int rr = mt - img * per_img;
-  const int h0 = (rr / a.tiles_w) * a.Ht;
-  const int w0 = (rr % a.tiles_w) * a.Wt;
-  const int n0 = blockIdx.y * BN;
+  const uint32_t tfull0 = smem_u32(bars + 2 * STAGES);
+  const uint32_t tempty0 = smem_u32(bars + 2 * STAGES + 2);
+  const uint32_t drain = smem_u32(bars + 2 * STAGES + 4);
+  const int ntiles = a.n * a.tiles_h * a.tiles_w * a.tiles_n;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
-    mbar_init(accb, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull0 + 8 * b, 1);
+      mbar_init(tempty0 + 8 * b, EPI_WARPS);
+    }
+    mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"((uint32_t)BN)
+                 "r"((uint32_t)(2 * BN))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -263,94 +315,125 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
-      int issued = 0;
+      int g = 0;  // ring position across tiles
       bool ok = true;
-      for (int kc = 0; kc < a.nk && ok; ++kc) {
-        const int s = kc % STAGES, j = kc / STAGES;
-        if (j > 0 && !mbar_wait(empty0 + 8 * s, (j - 1) & 1, a.err, 1)) { ok = false; break; }
-        mbar_expect_tx(full0 + 8 * s, STAGE_TX);
-        const uint32_t dA = smem_u32(sA + s * A_BYTES);
-        const uint32_t dB = smem_u32(sB + s * B_BYTES);
-        if (a.mode == CM_DOWN) {
-          const int k0 = kc * 64;
-          const int di = k0 / (2 * a.Cin), rem = k0 - di * 2 * a.Cin;
-          tma_load_5d(dA, &tmA, rem, w0, di, h0, img, full0 + 8 * s);
-        } else {
-          int tap = 4, c0 = kc * 64;
-          if (a.mode == CM_CONV3) {
-            tap = kc / a.cpt;
-            c0 = (kc - tap * a.cpt) * 64;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const TileCoord tc = tile_coord(a, t, BN);
+        for (int kc = 0; kc < a.nk; ++kc) {
+          const int s = g % STAGES, j = g / STAGES;
+          if (j > 0 && !mbar_wait(empty0 + 8 * s, (j - 1) & 1, a.err, 1)) {
+            ok = false;
+            break;
           }
-          tma_load_4d(dA, &tmA, c0, w0 + tap % 3 - 1, h0 + tap / 3 - 1, img, full0 + 8 * s);
+          mbar_expect_tx(full0 + 8 * s, STAGE_TX);
+          const uint32_t dA = smem_u32(sA + s * A_BYTES);
+          const uint32_t dB = smem_u32(sB + s * B_BYTES);
+          if (a.mode == CM_DOWN) {
+            const int k0 = kc * 64;
+            const int di = k0 / (2 * a.Cin), rem = k0 - di * 2 * a.Cin;
+            tma_load_5d(dA, &tmA, rem, tc.w0, di, tc.h0, tc.img, full0 + 8 * s);
+          } else {
+            int tap = 4, c0 = kc * 64;
+            if (a.mode == CM_CONV3) {
+              tap = kc / a.cpt;
+              c0 = (kc - tap * a.cpt) * 64;
+            }
+            tma_load_4d(dA, &tmA, c0, tc.w0 + tap % 3 - 1, tc.h0 + tap / 3 - 1, tc.img,
+                        full0 + 8 * s);
+          }
+          tma_load_2d(dB, &tmB, kc * 64, tc.n0, full0 + 8 * s);
+          ++g;
         }
-        tma_load_2d(dB, &tmB, kc * 64, n0, full0 + 8 * s);
-        ++issued;
       }
       // tail: wait until the MMA warp released every slot still in use, so no
       // tcgen05.commit arrival is outstanding when the CTA exits.
-      const int first = issued > STAGES ? issued - STAGES : 0;
-      for (int kc = first; kc < issued; ++kc) {
-        const int s = kc % STAGES, j = kc / STAGES;
+      const int first = g > STAGES ? g - STAGES : 0;
+      for (int i = first; i < g; ++i) {
+        const int s = i % STAGES, j = i / STAGES;
         if (ok) ok = mbar_wait(empty0 + 8 * s, j & 1, a.err, 2);
         if (!ok) mbar_wait(full0 + 8 * s, j & 1, a.err, 2);  // our own copies in flight
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = umma_idesc_bf16(128, BN);
+      constexpr uint32_t idesc = umma_idesc_16(128, BN, Fmt<T>::v);
       bool ok = true;
-      int done = 0;
-      for (int kc = 0; kc < a.nk; ++kc) {
-        const int s = kc % STAGES, j = kc / STAGES;
-        if (!mbar_wait(full0 + 8 * s, j & 1, a.err, 3)) { ok = false; break; }
+      int g = 0, lt = 0;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++lt) {
+        const int b = lt & 1, u = lt >> 1;
+        if (u > 0 && !mbar_wait(tempty0 + 8 * b, (u - 1) & 1, a.err, 5)) {
+          ok = false;
+          break;
+        }
         tc_fence_after();
-        const uint64_t ad = umma_desc_sw128(smem_u32(sA + s * A_BYTES));
-        const uint64_t bd = umma_desc_sw128(smem_u32(sB + s * B_BYTES));
+        const uint32_t td = tmem + (uint32_t)(b * BN);
+        for (int kc = 0; kc < a.nk; ++kc) {
+          const int s = g % STAGES, j = g / STAGES;
+          if (!mbar_wait(full0 + 8 * s, j & 1, a.err, 3)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint64_t ad = umma_desc_sw128(smem_u32(sA + s * A_BYTES));
+          const uint64_t bd = umma_desc_sw128(smem_u32(sB + s * B_BYTES));
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-          umma_bf16(tmem, ad + 2 * kk, bd + 2 * kk, idesc, (kc | kk) != 0 ? 1u : 0u);
-        umma_commit(empty0 + 8 * s);
-        ++done;
+          for (int kk = 0; kk < 4; ++kk)
+            umma_bf16(td, ad + 2 * kk, bd + 2 * kk, idesc, (kc | kk) != 0 ? 1u : 0u);
+          umma_commit(empty0 + 8 * s);
+          ++g;
+        }
+        if (ok) umma_commit(tfull0 + 8 * b);
       }
-      (void)done;
-      (void)ok;
-      umma_commit(accb);  // also on the error path: arrives once issued MMAs finish
+      if (!ok) {  // let every issued MMA finish before TMEM is released
+        umma_commit(drain);
+        mbar_wait(drain, 0, a.err, 6);
+      }
     }
   } else {
-    // epilogue warps 2..5 -> TMEM lane quarter (warp % 4)
-    const int q = warp & 3;
+    // epilogue: warp -> TMEM lane quarter (warp % 4) and column half ((warp - 2) / 4)
+    const int q = warp & 3, half = (warp - 2) >> 2;
     const int row = q * 32 + lane;
-    const bool ok = mbar_wait(accb, 0, a.err, 4);
-    tc_fence_after();
-    const int ly = row / a.Wt, lx = row - ly * a.Wt;
-    const int y = h0 + ly, x = w0 + lx;
-    const bool valid = ok && (*(volatile int*)a.err == 0) && y < a.H && x < a.W;
+    constexpr int HALF = BN / 2;
+    int lt = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
+      const int b = lt & 1, u = lt >> 1;
+      const bool ok = mbar_wait(tfull0 + 8 * b, u & 1, a.err, 4);
+      tc_fence_after();
+      const TileCoord tc = tile_coord(a, t, BN);
+      const int ly = row / a.Wt, lx = row - ly * a.Wt;
+      const int y = tc.h0 + ly, x = tc.w0 + lx;
+      const bool valid = ok && y < a.H && x < a.W;
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);  // warp-collective
-      if (!valid) continue;
-      const int n = n0 + c0;
-      size_t o;
-      if (a.outmap == OM_D2S) {
-        const int qq = n / a.Cout, co = n - qq * a.Cout;
-        const int oy = 2 * y + (qq >> 1), ox = 2 * x + (qq & 1);
-        o = (((size_t)img * 2 * a.H + oy) * 2 * a.W + ox) * a.Cout + co;
-      } else {
-        o = (((size_t)img * a.H + y) * a.W + x) * (size_t)a.Cout + n;
-      }
-      float x0[16], x1[16], x2[16], r[16], r2[16];
-      if (a.aux0) load_bf16x16(a.aux0 + o, x0);
-      if (a.aux1) load_bf16x16(a.aux1 + o, x1);
-      if (a.aux2) load_bf16x16(a.aux2 + o, x2);
+      for (int c0 = half * HALF; c0 < (half + 1) * HALF; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + (uint32_t)(b * BN) + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+        if (!valid) continue;
+        const int n = tc.n0 + c0;
+        size_t o;
+        if (a.outmap == OM_D2S) {
+          const int qq = n / a.Cout, co = n - qq * a.Cout;
+          const int oy = 2 * y + (qq >> 1), ox = 2 * x + (qq & 1);
+          o = (((size_t)tc.img * 2 * a.H + oy) * 2 * a.W + ox) * a.Cout + co;
+        } else {
+          o = (((size_t)tc.img * a.H + y) * a.W + x) * (size_t)a.Cout + n;
+        }
+        float x0[16], x1[16], x2[16], r[16], r2[16];
+        if (a.aux0) load16x16((const T*)a.aux0 + o, x0);
+        if (a.aux1) load16x16((const T*)a.aux1 + o, x1);
+        if (a.aux2) load16x16((const T*)a.aux2 + o, x2);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        r2[i] = 0.f;
-        r[i] = epi_math(a.epi, a.act, v[i], a.aux0 ? x0[i] : 0.f, a.aux1 ? x1[i] : 0.f,
-                        a.aux2 ? x2[i] : 0.f, &r2[i]);
+        for (int i = 0; i < 16; ++i) {
+          r2[i] = 0.f;
+          r[i] = epi_math(a.epi, a.act, v[i], a.aux0 ? x0[i] : 0.f, a.aux1 ? x1[i] : 0.f,
+                          a.aux2 ? x2[i] : 0.f, &r2[i]);
+        }
+        store16x16((T*)a.out + o, r);
+        if (a.epi == EP_ACT || a.epi == EP_MUL_KEEP) store16x16((T*)a.out2 + o, r2);
       }
-      store_bf16x16(a.out + o, r);
-      if (a.epi == EP_ACT || a.epi == EP_MUL_KEEP) store_bf16x16(a.out2 + o, r2);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty0 + 8 * b);
+      if (!ok) break;
     }
   }
   tc_fence_before();
@@ -358,7 +441,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"((uint32_t)BN)
+                 "r"((uint32_t)(2 * BN))
                  : "memory");
   }
 }
@@ -396,12 +479,13 @@ bool tc_supported(const ConvArgs& a) {
 
 template <int BN, int ST>
 static size_t smem_bytes() {
-  return 1024 + (size_t)ST * (A_BYTES + BN * 128) + (2 * ST + 1) * 8 + 16;
+  return 1024 + (size_t)ST * (A_BYTES + BN * 128) + (2 * ST + 5) * 8 + 16;
 }
 
-static int stages_for(int bn) { return bn == 64 ? 4 : (bn == 128 ? 4 : 3); }
+// ring depth: ~192 KB of operands per CTA (one persistent CTA per SM)
+static int stages_for(int bn) { return bn == 64 ? 8 : (bn == 128 ? 6 : 4); }
 
-TcPlan* tc_plan_create(const ConvArgs& a, std::string* err) {
+TcPlan* tc_plan_create(const ConvArgs& a, int dtype, std::string* err) {
   auto enc = get_encode();
   if (!enc) {
     *err = "cuTensorMapEncodeTiled unavailable";
@@ -411,7 +495,12 @@ TcPlan* tc_plan_create(const ConvArgs& a, std::string* err) {
     *err = "layer not supported by the tensor-core kernel";
     return nullptr;
   }
+  if (dtype != DT_BF16 && dtype != DT_F16) {
+    *err = "tensor-core kernel needs bf16 or f16 operands";
+    return nullptr;
+  }
   TcPlan* p = new TcPlan();
+  p->dt = dtype;
   const int N = a.N();
   p->bn = pick_bn(N);
   p->stages = stages_for(p->bn);
@@ -424,8 +513,20 @@ TcPlan* tc_plan_create(const ConvArgs& a, std::string* err) {
   p->tiles_h = (a.H + p->Ht - 1) / p->Ht;
   p->cpt = a.Cin / 64;
   p->nk = a.K() / 64;
-  p->grid = dim3((unsigned)(a.n * p->tiles_h * p->tiles_w), (unsigned)(N / p->bn), 1);
-  const CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  p->tiles_n = N / p->bn;
+  {
+    static int sms = 0;
+    if (sms == 0) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (sms <= 0) sms = 148;
+    }
+    const long long tiles = (long long)a.n * p->tiles_h * p->tiles_w * p->tiles_n;
+    p->grid = dim3((unsigned)std::min<long long>(tiles, sms), 1, 1);
+  }
+  const CUtensorMapDataType dt =
+      dtype == DT_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
   CUresult r;
   if (a.mode == CM_DOWN) {
     const int Hi = 2 * a.H, Wi = 2 * a.W;
@@ -469,27 +570,37 @@ TcPlan* tc_plan_create(const ConvArgs& a, std::string* err) {
     }
   }
   switch (p->bn) {
-    case 64: p->smem = smem_bytes<64, 4>(); break;
-    case 128: p->smem = smem_bytes<128, 4>(); break;
-    default: p->smem = smem_bytes<256, 3>(); break;
+    case 64: p->smem = smem_bytes<64, 8>(); break;
+    case 128: p->smem = smem_bytes<128, 6>(); break;
+    default: p->smem = smem_bytes<256, 4>(); break;
   }
   return p;
 }
 
 void tc_plan_destroy(TcPlan* p) { delete p; }
 
-template <int BN, int ST>
+template <typename T, int BN, int ST>
 static cudaError_t launch_bn(const TcPlan* p, const TcArgs& ta, cudaStream_t st) {
   static bool attr_set = false;  // per instantiation; set before first launch
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<BN, ST>,
+    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<T, BN, ST>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem_bytes<BN, ST>());
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  conv_tc_kernel<BN, ST><<<p->grid, TC_THREADS, smem_bytes<BN, ST>(), st>>>(p->tmA, p->tmB, ta);
+  conv_tc_kernel<T, BN, ST><<<p->grid, TC_THREADS, smem_bytes<BN, ST>(), st>>>(p->tmA, p->tmB,
+                                                                               ta);
   return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_typed(const TcPlan* p, const TcArgs& t, cudaStream_t st) {
+  switch (p->bn) {
+    case 64: return launch_bn<T, 64, 8>(p, t, st);
+    case 128: return launch_bn<T, 128, 6>(p, t, st);
+    default: return launch_bn<T, 256, 4>(p, t, st);
+  }
 }
 
 cudaError_t launch_conv_tc(const TcPlan* p, const ConvArgs& a, int* err_flag, cudaStream_t st) {
@@ -508,19 +619,17 @@ cudaError_t launch_conv_tc(const TcPlan* p, const ConvArgs& a, int* err_flag, cu
   t.Ht = p->Ht;
   t.tiles_w = p->tiles_w;
   t.tiles_h = p->tiles_h;
+  t.tiles_n = p->tiles_n;
   t.nk = p->nk;
   t.cpt = p->cpt;
-  t.out = (__nv_bfloat16*)a.out;
-  t.out2 = (__nv_bfloat16*)a.out2;
-  t.aux0 = (const __nv_bfloat16*)a.aux0;
-  t.aux1 = (const __nv_bfloat16*)a.aux1;
-  t.aux2 = (const __nv_bfloat16*)a.aux2;
+  t.out = a.out;
+  t.out2 = a.out2;
+  t.aux0 = a.aux0;
+  t.aux1 = a.aux1;
+  t.aux2 = a.aux2;
   t.err = err_flag;
-  switch (p->bn) {
-    case 64: return launch_bn<64, 4>(p, t, st);
-    case 128: return launch_bn<128, 4>(p, t, st);
-    default: return launch_bn<256, 3>(p, t, st);
-  }
+  if (p->dt == DT_F16) return launch_typed<__half>(p, t, st);
+  return launch_typed<__nv_bfloat16>(p, t, st);
 }
 
 }  // namespace ideq

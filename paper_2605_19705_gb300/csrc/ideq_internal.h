@@ -16,6 +16,9 @@
 
 namespace ideq {
 
+// element storage of network activations
+enum DType { DT_F32 = 0, DT_BF16 = 1, DT_F16 = 2 };
+
 // ------------------------------------------------------------- conv GEMMs
 //
 // Every network layer is one implicit GEMM  D[M][N] = A[M][K] * B[N][K]^T
@@ -60,20 +63,27 @@ struct ConvArgs {
   IDEQ_HD double flops() const { return 2.0 * (double)M() * N() * K(); }
 };
 
-// dtype: 0 = f32, 1 = bf16 for activations (in/out NHWC); NCHW sides are f32.
-cudaError_t launch_conv_simt(const ConvArgs& a, int in_bf16, int out_bf16, cudaStream_t st);
+// Element types of NHWC activations: DT_F32, DT_BF16 or DT_F16 (common.cuh);
+// NCHW image-side tensors are always f32.  SIMT weights are always f32.
+cudaError_t launch_conv_simt(const ConvArgs& a, int in_dt, int out_dt, cudaStream_t st);
 
-// tcgen05 path: bf16 NHWC in/out, Cin % 64 == 0, N % 16 == 0 (see conv_tc.cu).
+// Image-side <-> feature-side 3x3 convs (head, tail, their transposes; see
+// conv_edge.cu).  feat_dt is the element type of the NHWC side.
+bool edge_supported(const ConvArgs& a);
+cudaError_t launch_conv_edge(const ConvArgs& a, int feat_dt, cudaStream_t st);
+
+// tcgen05 path: 16-bit (bf16 or f16) NHWC in/out and weights, Cin % 64 == 0,
+// N % 64 == 0 (see conv_tc.cu).
 struct TcPlan;  // tensor maps + launch geometry, built once per (layer, buffers)
 bool tc_supported(const ConvArgs& a);
-TcPlan* tc_plan_create(const ConvArgs& a, std::string* err);
+TcPlan* tc_plan_create(const ConvArgs& a, int dt, std::string* err);
 void tc_plan_destroy(TcPlan* p);
 cudaError_t launch_conv_tc(const TcPlan* p, const ConvArgs& a, int* err_flag, cudaStream_t st);
 
 // Weight forms: GEMM B matrices from the PyTorch-layout weights.
 enum WForm { WF_CONV3_FWD = 0, WF_CONV3_DGRAD, WF_DOWN_FWD, WF_DOWN_DGRAD, WF_UP_FWD, WF_UP_DGRAD };
 cudaError_t launch_weight_form(int form, int cin, int cout, const float* src, float* dst_f32,
-                               void* dst_bf16, cudaStream_t st);
+                               void* dst_bf16, void* dst_f16, cudaStream_t st);
 // Scatter a GEMM-layout weight gradient [N][K] back to PyTorch layout (+=).
 cudaError_t launch_weight_unform(int form, int cin, int cout, const float* g, float* dst,
                                  cudaStream_t st);
@@ -121,10 +131,11 @@ struct SolverDev {
 
 cudaError_t launch_extrapolate(int n, int per_img, const float* x, const float* xp,
                                const float* beta_eff, float* z, cudaStream_t st);
+// xn = z - tau (gf + lambda gg) (+ addv when non-null) for running images.
 cudaError_t launch_red_update(int n, int per_img, int nblk, const float* z, const float* gf,
                               const float* gg, const float* x, float* xn, float lam, float tau,
                               const int* status, double* part_s, double* part_x,
-                              cudaStream_t st);
+                              cudaStream_t st, const float* addv = nullptr);
 cudaError_t launch_finalize(int n, int nblk, const SolverDev& s, int parity_new, float beta,
                             float B, double tol, int max_iter, float lam, int apply_logic,
                             cudaStream_t st);
@@ -138,5 +149,8 @@ int update_blocks_per_image(int per_img);
 cudaError_t launch_axpby(long long n, float a, const float* x, float b, const float* y,
                          float* out, cudaStream_t st);
 cudaError_t launch_zero_d(long long n, double* p, cudaStream_t st);
+// *out = scale * <a, b> (n floats), FP64 accumulation; part holds >= 128 doubles.
+cudaError_t launch_dot(long long n, const float* a, const float* b, float scale, double* part,
+                       float* out, cudaStream_t st);
 
 }  // namespace ideq

@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(256) red_update_kernel(
     int per_img, const float* __restrict__ z, const float* __restrict__ gf,
     const float* __restrict__ gg, const float* __restrict__ x, float* __restrict__ xn,
     float lam, float tau, const int* __restrict__ status, double* __restrict__ part_s,
-    double* __restrict__ part_x) {
+    double* __restrict__ part_x, const float* __restrict__ addv) {
   __shared__ double red[32];
   const int b = blockIdx.y;
   const int nblk = gridDim.x;
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(256) red_update_kernel(
   double ss = 0.0, sx = 0.0;
   const size_t base = (size_t)b * per_img;
   if (run) {
-    if ((per_img & 3) == 0) {
+    if ((per_img & 3) == 0 && addv == nullptr) {
       const int n4 = per_img >> 2;
       const float4* z4 = (const float4*)(z + base);
       const float4* f4 = (const float4*)(gf + base);
@@ -256,7 +256,8 @@ __global__ void __launch_bounds__(256) red_update_kernel(
       }
     } else {
       for (int i = blockIdx.x * 256 + threadIdx.x; i < per_img; i += nblk * 256) {
-        const float o = z[base + i] - tau * (gf[base + i] + lam * gg[base + i]);
+        float o = z[base + i] - tau * (gf[base + i] + lam * gg[base + i]);
+        if (addv) o += addv[base + i];
         xn[base + i] = o;
         const double d = (double)o - x[base + i];
         ss += d * d;
@@ -275,10 +276,10 @@ __global__ void __launch_bounds__(256) red_update_kernel(
 cudaError_t launch_red_update(int n, int per_img, int nblk, const float* z, const float* gf,
                               const float* gg, const float* x, float* xn, float lam, float tau,
                               const int* status, double* part_s, double* part_x,
-                              cudaStream_t st) {
+                              cudaStream_t st, const float* addv) {
   dim3 grid(nblk, n);
   red_update_kernel<<<grid, 256, 0, st>>>(per_img, z, gf, gg, x, xn, lam, tau, status, part_s,
-                                          part_x);
+                                          part_x, addv);
   return cudaGetLastError();
 }
 
@@ -474,7 +475,7 @@ static void wform_dims(int form, int cin, int cout, int* N, int* K) {
 
 __global__ void wform_kernel(int form, int cin, int cout, int N, int K,
                              const float* __restrict__ src, float* __restrict__ d32,
-                             __nv_bfloat16* __restrict__ d16) {
+                             __nv_bfloat16* __restrict__ d16, __half* __restrict__ dh) {
   const long long tot = (long long)N * K;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
        e += (long long)gridDim.x * blockDim.x) {
@@ -482,37 +483,72 @@ __global__ void wform_kernel(int form, int cin, int cout, int N, int K,
     const float v = src[wform_src(form, cin, cout, nn, kk)];
     if (d32) d32[e] = v;
     if (d16) d16[e] = __float2bfloat16_rn(v);
+    if (dh) dh[e] = __float2half_rn(v);
   }
 }
 
 __global__ void wunform_kernel(int form, int cin, int cout, int N, int K,
-                               const float* __restrict__ g, float* __restrict__ dst) {
+                               const float* __restrict__ g, float scale, float* __restrict__ dst) {
   const long long tot = (long long)N * K;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
        e += (long long)gridDim.x * blockDim.x) {
     const int nn = (int)(e / K), kk = (int)(e % K);
-    dst[wform_src(form, cin, cout, nn, kk)] += g[e];
+    dst[wform_src(form, cin, cout, nn, kk)] += scale * g[e];
   }
 }
 
 cudaError_t launch_weight_form(int form, int cin, int cout, const float* src, float* dst_f32,
-                               void* dst_bf16, cudaStream_t st) {
+                               void* dst_bf16, void* dst_f16, cudaStream_t st) {
   int N, K;
   wform_dims(form, cin, cout, &N, &K);
   const long long tot = (long long)N * K;
   const int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
   wform_kernel<<<blocks, 256, 0, st>>>(form, cin, cout, N, K, src, dst_f32,
-                                       (__nv_bfloat16*)dst_bf16);
+                                       (__nv_bfloat16*)dst_bf16, (__half*)dst_f16);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_weight_unform_scaled(int form, int cin, int cout, const float* g, float scale,
+                                        float* dst, cudaStream_t st) {
+  int N, K;
+  wform_dims(form, cin, cout, &N, &K);
+  const long long tot = (long long)N * K;
+  const int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
+  wunform_kernel<<<blocks, 256, 0, st>>>(form, cin, cout, N, K, g, scale, dst);
   return cudaGetLastError();
 }
 
 cudaError_t launch_weight_unform(int form, int cin, int cout, const float* g, float* dst,
                                  cudaStream_t st) {
-  int N, K;
-  wform_dims(form, cin, cout, &N, &K);
-  const long long tot = (long long)N * K;
-  const int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
-  wunform_kernel<<<blocks, 256, 0, st>>>(form, cin, cout, N, K, g, dst);
+  return launch_weight_unform_scaled(form, cin, cout, g, 1.f, dst, st);
+}
+
+// out = scale * sum_i a[i] b[i] over n elements: FP64 partials of 128 blocks,
+// then one block sums them in a fixed order.
+__global__ void dot_part_kernel(long long n, const float* __restrict__ a,
+                                const float* __restrict__ b, double* __restrict__ part) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    s += (double)a[i] * (double)b[i];
+  const double t = block_sum(s, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+__global__ void dot_final_kernel(int nb, const double* __restrict__ part, float scale,
+                                 float* __restrict__ out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) s += part[i];
+  const double t = block_sum(s, red);
+  if (threadIdx.x == 0) *out = (float)((double)scale * t);
+}
+
+cudaError_t launch_dot(long long n, const float* a, const float* b, float scale, double* part,
+                       float* out, cudaStream_t st) {
+  dot_part_kernel<<<128, 256, 0, st>>>(n, a, b, part);
+  dot_final_kernel<<<1, 128, 0, st>>>(128, part, scale, out);
   return cudaGetLastError();
 }
 

@@ -114,7 +114,9 @@ bool NetWeights::build(const ideq_net_desc& d, std::string* err) {
     l.dg32 = (float*)al(l.numel * 4);
     l.fwd16 = (__nv_bfloat16*)al(l.numel * 2);
     l.dg16 = (__nv_bfloat16*)al(l.numel * 2);
-    if (!l.fwd32 || !l.dg32 || !l.fwd16 || !l.dg16) {
+    l.fwdh = (__half*)al(l.numel * 2);
+    l.dgh = (__half*)al(l.numel * 2);
+    if (!l.fwd32 || !l.dg32 || !l.fwd16 || !l.dg16 || !l.fwdh || !l.dgh) {
       *err = "cudaMalloc(weight forms) failed";
       return false;
     }
@@ -125,9 +127,9 @@ bool NetWeights::build(const ideq_net_desc& d, std::string* err) {
 cudaError_t NetWeights::reform(cudaStream_t st) {
   for (auto& l : layers) {
     cudaError_t e = launch_weight_form(l.fwd_form, l.cin, l.cout, master + l.off, l.fwd32,
-                                       l.fwd16, st);
+                                       l.fwd16, l.fwdh, st);
     if (e != cudaSuccess) return e;
-    e = launch_weight_form(l.dg_form, l.cin, l.cout, master + l.off, l.dg32, l.dg16, st);
+    e = launch_weight_form(l.dg_form, l.cin, l.cout, master + l.off, l.dg32, l.dg16, l.dgh, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -198,19 +200,23 @@ struct Builder {
     a.aux1 = aux1;
     a.aux2 = aux2;
     a.sumsq = sumsq;
-    const bool bf = P->prec != IDEQ_FP32;
-    s.in_bf16 = bf && !in_nchw;
-    s.out_bf16 = bf && !out_nchw;
-    if (bf && s.in_bf16 && s.out_bf16 && tc_supported(a)) {
-      a.wB = dgrad ? (const void*)L.dg16 : (const void*)L.fwd16;
+    const int adt = P->prec == IDEQ_FP32 ? DT_F32 : (P->prec == IDEQ_FP16 ? DT_F16 : DT_BF16);
+    s.in_dt = in_nchw ? DT_F32 : adt;
+    s.out_dt = out_nchw ? DT_F32 : adt;
+    if (adt != DT_F32 && !in_nchw && !out_nchw && tc_supported(a)) {
+      if (adt == DT_F16)
+        a.wB = dgrad ? (const void*)L.dgh : (const void*)L.fwdh;
+      else
+        a.wB = dgrad ? (const void*)L.dg16 : (const void*)L.fwd16;
       std::string e;
-      s.tc = tc_plan_create(a, &e);
+      s.tc = tc_plan_create(a, adt, &e);
       if (!s.tc) {
         *err = e;
         ok = false;
       }
     } else {
       a.wB = dgrad ? (const void*)L.dg32 : (const void*)L.fwd32;
+      s.edge = edge_supported(a);
     }
     list.push_back(s);
   }
@@ -228,7 +234,7 @@ bool NetPlan::build(NetWeights* wts, int n_, int H_, int W_, int prec_, double* 
   prec = prec_;
   gsum = gsum_;
   const ideq_net_desc& d = wts->desc;
-  Builder B{this, err, true, prec == IDEQ_FP32 ? 4 : 2};
+  Builder B{this, err, true, prec == IDEQ_FP32 ? 4 : 2};  // activation element bytes
   const size_t img_bytes = (size_t)n * c * H * W * 4;
   z = (float*)alloc(img_bytes);
   r = (float*)alloc(img_bytes);
@@ -425,8 +431,10 @@ cudaError_t run_steps(const std::vector<Step>& steps, int* err_flag, cudaStream_
         prof->flops += s.a.flops();
         prof->launches += 1;
       }
+    } else if (s.edge) {
+      e = launch_conv_edge(s.a, s.a.in_nchw ? s.out_dt : s.in_dt, st);
     } else {
-      e = launch_conv_simt(s.a, s.in_bf16, s.out_bf16, st);
+      e = launch_conv_simt(s.a, s.in_dt, s.out_dt, st);
     }
     if (launches) *launches += 1;
     if (e != cudaSuccess) return e;

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <string>
 #include <vector>
@@ -19,11 +20,13 @@ struct Layer {
   int fwd_form, dg_form;
   float* fwd32 = nullptr;
   float* dg32 = nullptr;
-  __nv_bfloat16* fwd16 = nullptr;
+  __nv_bfloat16* fwd16 = nullptr;  // bf16 forms
   __nv_bfloat16* dg16 = nullptr;
+  __half* fwdh = nullptr;          // f16 forms
+  __half* dgh = nullptr;
 };
 
-// Flat weight vector + its GEMM forms (f32 and bf16, forward and input-gradient).
+// Flat weight vector + its GEMM forms (f32, bf16, f16; forward and input-gradient).
 struct NetWeights {
   ideq_net_desc desc{};
   long long nparams = 0;
@@ -42,8 +45,9 @@ bool net_param_count(const ideq_net_desc& d, long long* count, std::vector<Layer
 // One conv launch of a plan.
 struct Step {
   ConvArgs a;
-  int in_bf16 = 0, out_bf16 = 0;
+  int in_dt = 0, out_dt = 0;  // DT_* of the NHWC/NCHW input and output
   TcPlan* tc = nullptr;
+  bool edge = false;  // image-side <-> feature-side kernel
 };
 
 // Execution plan for one (n, H, W, precision): activation buffers and the

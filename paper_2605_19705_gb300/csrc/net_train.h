@@ -1,0 +1,44 @@
+// Training plan of the regulariser network (see net_train.cu).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "net.h"
+
+namespace ideq {
+
+struct WgStep {
+  int layer;            // index into NetWeights::layers
+  ConvArgs a;           // the forward conv (geometry and primal input)
+  int in_dt, cot_dt;
+  const void* tin;      // tangent input of the conv
+  const void* pcot;     // p-chain cotangent of its output
+  const void* tcot;     // t-chain cotangent of its output
+};
+
+struct TrainPlan {
+  int n = 0, c = 0, H = 0, W = 0, prec = 0;
+  NetWeights* w = nullptr;
+  float *z = nullptr, *r = nullptr, *grad = nullptr;  // point, residual, grad g
+  float *zd = nullptr, *rd = nullptr, *hvp = nullptr; // direction, rdot, Hess g . direction
+  double* gsum = nullptr;
+  std::vector<Step> fwd, tchain, jvp, pchain;
+  std::vector<WgStep> wg;
+  float* wg_part = nullptr;
+  float* wg_acc = nullptr;
+  std::vector<void*> allocs;
+  ~TrainPlan();
+  void* alloc(size_t bytes);
+  bool build(NetWeights* w, int n, int H, int W, int prec, double* gsum, std::string* err);
+  cudaError_t run_wgrad(float* dst, float scale, bool with_tangent, cudaStream_t st,
+                        long long* launches);
+};
+
+int wgrad_splits(const ConvArgs& a);
+cudaError_t launch_wgrad(const ConvArgs& a, int in_dt, int cot_dt, const void* cot, float scale,
+                         float* part, float* dst, cudaStream_t st);
+cudaError_t launch_weight_unform_scaled(int form, int cin, int cout, const float* g, float scale,
+                                        float* dst, cudaStream_t st);
+
+}  // namespace ideq
