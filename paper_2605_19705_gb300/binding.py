@@ -273,13 +273,23 @@ def ideq_solve(ctx: Context, op: Operator, y, params: Params, x0=None, out=None,
 
 
 def ideq_solve_backward(ctx: Context, op: Operator, y, x_bar, dl_dx, params: Params,
-                        adj: AdjParams, dl_dtheta, dl_dlambda, info=None):
+                        adj: AdjParams, dl_dtheta, dl_dlambda, info=None, allow_maxiter=False):
+    """Implicit backward; returns the status (IDEQ_ADJ_MAXITER raises unless allowed)."""
     import torch
-    return ctx.check(_lib.ideq_solve_backward(
+    st = _lib.ideq_solve_backward(
         ctx.h, ctypes.byref(op), _shape(y), _ptr(y, torch.float32), _ptr(x_bar, torch.float32),
         _ptr(dl_dx, torch.float32), ctypes.byref(params), ctypes.byref(adj),
         _ptr(dl_dtheta, torch.float32), _ptr(dl_dlambda, torch.float32),
-        ctypes.byref(info.s) if info is not None else None))
+        ctypes.byref(info.s) if info is not None else None)
+    if st == IDEQ_ADJ_MAXITER and allow_maxiter:
+        return st
+    return ctx.check(st)
+
+
+def make_adj(mode=IDEQ_ADJ_IMPLICIT, tol=1e-3, max_iter=500, beta=0.0) -> AdjParams:
+    a = AdjParams()
+    a.mode, a.tol, a.max_iter, a.beta = mode, tol, max_iter, beta
+    return a
 
 
 def ideq_prof_enable(ctx: Context, on: bool):
@@ -296,3 +306,4 @@ def ideq_launch_count(ctx: Context) -> int:
     n = ctypes.c_int64(0)
     ctx.check(_lib.ideq_launch_count(ctx.h, ctypes.byref(n)))
     return int(n.value)
+

@@ -19,6 +19,13 @@ struct ideq_ctx {
   std::unique_ptr<NetWeights> w;
   std::unique_ptr<NetPlan> plan;
   std::unique_ptr<TrainPlan> train;
+  // learned warm start: weights, its plan for the current shape, Adam state
+  std::unique_ptr<NetWeights> warm_w;
+  std::unique_ptr<TrainPlan> warm_plan;
+  float* warm_m = nullptr;
+  float* warm_v = nullptr;
+  float* warm_g = nullptr;
+  int warm_t = 0;
   std::string err;
   int* d_err = nullptr;       // device error flag of bounded waits
   int* h_running = nullptr;   // pinned
@@ -91,6 +98,7 @@ ideq_status ensure_plan(ideq_ctx* ctx, const ideq_shape& s) {
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->plan.reset();
   ctx->train.reset();
+  ctx->warm_plan.reset();
   // solver workspace
   if (ctx->sv_mem) {
     cudaFree(ctx->sv_mem);
@@ -224,6 +232,34 @@ ideq_status check_params(ideq_ctx* ctx, const ideq_params* p) {
   return IDEQ_OK;
 }
 
+ideq_status ensure_warm_plan(ideq_ctx* ctx, const ideq_shape& s) {
+  if (!ctx->warm_w) return fail(ctx, IDEQ_ERR_ARG, "no warm-start network (ideq_warm_set)");
+  if (s.c != ctx->warm_w->desc.in_ch) return fail(ctx, IDEQ_ERR_ARG, "warm start channels");
+  TrainPlan* T = ctx->warm_plan.get();
+  if (T && T->n == s.n && T->H == s.h && T->W == s.w && T->prec == ctx->precision) return IDEQ_OK;
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->warm_plan.reset();
+  std::unique_ptr<TrainPlan> tp(new TrainPlan());
+  std::string e;
+  if (!tp->build(ctx->warm_w.get(), s.n, s.h, s.w, ctx->precision, nullptr, &e, true))
+    return fail(ctx, IDEQ_ERR_UNSUPPORTED, "warm-start plan: " + e);
+  ctx->warm_plan = std::move(tp);
+  return IDEQ_OK;
+}
+
+// x0 = aty + W(aty) into out (all device, f32 NCHW)
+ideq_status warm_forward(ideq_ctx* ctx, const ideq_shape& s, const float* aty, float* out) {
+  ideq_status st = ensure_warm_plan(ctx, s);
+  if (st != IDEQ_OK) return st;
+  TrainPlan* T = ctx->warm_plan.get();
+  const size_t bytes = (size_t)s.n * s.c * s.h * s.w * 4;
+  CK(cudaMemcpyAsync(T->z, aty, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(run_steps(T->fwd, ctx->d_err, ctx->stream, &ctx->prof, &ctx->launches));
+  if (out != T->out_img)
+    CK(cudaMemcpyAsync(out, T->out_img, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  return IDEQ_OK;
+}
+
 }  // namespace
 
 // =========================================================================== C ABI
@@ -265,6 +301,11 @@ ideq_status ideq_destroy(ideq_ctx* ctx) {
   if (!ctx) return IDEQ_ERR_ARG;
   cudaStreamSynchronize(ctx->stream);
   ctx->plan.reset();
+  ctx->train.reset();
+  ctx->warm_plan.reset();
+  ctx->warm_w.reset();
+  for (float* p : {ctx->warm_m, ctx->warm_v, ctx->warm_g})
+    if (p) cudaFree(p);
   ctx->w.reset();
   if (ctx->sv_mem) cudaFree(ctx->sv_mem);
   if (ctx->scratch) cudaFree(ctx->scratch);
@@ -371,14 +412,19 @@ ideq_status ideq_solve(ideq_ctx* ctx, const ideq_operator* op, ideq_shape shape,
   OpDev od;
   if ((s = check_op(ctx, op, shape, &od)) != IDEQ_OK) return s;
   if (p->init == IDEQ_INIT_X0 && !x0) return fail(ctx, IDEQ_ERR_ARG, "init X0 needs x0");
-  if (p->init == IDEQ_INIT_WARM) return fail(ctx, IDEQ_ERR_UNSUPPORTED, "warm start not set");
+  if (p->init == IDEQ_INIT_WARM && !ctx->warm_w)
+    return fail(ctx, IDEQ_ERR_ARG, "init WARM needs ideq_warm_set");
   if ((s = ensure_plan(ctx, shape)) != IDEQ_OK) return s;
   const size_t bytes = (size_t)shape.n * shape.c * shape.h * shape.w * 4;
   cudaStream_t st = ctx->stream;
-  if (p->init == IDEQ_INIT_X0)
+  if (p->init == IDEQ_INIT_X0) {
     CK(cudaMemcpyAsync(ctx->xb[0], x0, bytes, cudaMemcpyDeviceToDevice, st));
-  else
+  } else if (p->init == IDEQ_INIT_WARM) {
+    CK(back_project(ctx, od, shape, y, ctx->tmp));
+    if ((s = warm_forward(ctx, shape, ctx->tmp, ctx->xb[0])) != IDEQ_OK) return s;
+  } else {
     CK(back_project(ctx, od, shape, y, ctx->xb[0]));
+  }
   CK(cudaMemcpyAsync(ctx->xb[1], ctx->xb[0], bytes, cudaMemcpyDeviceToDevice, st));
   CK(launch_solver_init(shape.n, ctx->sv, 0.f, st));  // x^{-1} = x^0
   const int poll = p->tol > 0.0 ? 2 : 0;
@@ -490,18 +536,67 @@ ideq_status ideq_solve_backward(ideq_ctx* ctx, const ideq_operator* op, ideq_sha
   return IDEQ_OK;
 }
 
-ideq_status ideq_warm_set(ideq_ctx* ctx, const ideq_net_desc*, const float*) {
-  return fail(ctx, IDEQ_ERR_UNSUPPORTED, "warm start not built yet");
+ideq_status ideq_warm_set(ideq_ctx* ctx, const ideq_net_desc* net, const float* weights) {
+  if (!ctx || !net || !weights) return fail(ctx, IDEQ_ERR_ARG, "bad arguments");
+  if (net->kind != IDEQ_NET_CNN) return fail(ctx, IDEQ_ERR_ARG, "warm start must be a plain CNN");
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->warm_plan.reset();
+  for (float* p : {ctx->warm_m, ctx->warm_v, ctx->warm_g})
+    if (p) cudaFree(p);
+  ctx->warm_m = ctx->warm_v = ctx->warm_g = nullptr;
+  std::unique_ptr<NetWeights> w(new NetWeights());
+  std::string e;
+  if (!w->build(*net, &e)) return fail(ctx, IDEQ_ERR_ARG, "warm start: " + e);
+  CK(w->upload(weights, ctx->stream));
+  const size_t b = (size_t)w->nparams * 4;
+  CK(cudaMalloc((void**)&ctx->warm_m, b));
+  CK(cudaMalloc((void**)&ctx->warm_v, b));
+  CK(cudaMalloc((void**)&ctx->warm_g, b));
+  CK(cudaMemsetAsync(ctx->warm_m, 0, b, ctx->stream));
+  CK(cudaMemsetAsync(ctx->warm_v, 0, b, ctx->stream));
+  ctx->warm_t = 0;
+  ctx->warm_w = std::move(w);
+  return IDEQ_OK;
 }
-ideq_status ideq_warm_forward(ideq_ctx* ctx, ideq_shape, const float*, float*) {
-  return fail(ctx, IDEQ_ERR_UNSUPPORTED, "warm start not built yet");
+
+ideq_status ideq_warm_forward(ideq_ctx* ctx, ideq_shape shape, const float* aty, float* x0) {
+  if (!ctx || !aty || !x0 || !shape_ok(shape)) return fail(ctx, IDEQ_ERR_ARG, "bad arguments");
+  return warm_forward(ctx, shape, aty, x0);
 }
-ideq_status ideq_warm_train_step(ideq_ctx* ctx, ideq_shape, const float*, const float*, float,
-                                 double*) {
-  return fail(ctx, IDEQ_ERR_UNSUPPORTED, "warm start not built yet");
+
+ideq_status ideq_warm_train_step(ideq_ctx* ctx, ideq_shape shape, const float* aty,
+                                 const float* target, float lr, double* loss) {
+  if (!ctx || !aty || !target || !shape_ok(shape) || !(lr > 0.f))
+    return fail(ctx, IDEQ_ERR_ARG, "bad arguments");
+  ideq_status s = warm_forward(ctx, shape, aty, nullptr);
+  if (s != IDEQ_OK) return s;
+  TrainPlan* T = ctx->warm_plan.get();
+  NetWeights* W = ctx->warm_w.get();
+  cudaStream_t st = ctx->stream;
+  const long long numel = (long long)shape.n * shape.c * shape.h * shape.w;
+  double* part = nullptr;
+  // the loss kernel needs 128 doubles of partials: reuse the solver's if sized, else scratch
+  float* scr = ensure_scratch(ctx, 128 * 8);
+  if (!scr) return fail(ctx, IDEQ_ERR_NOMEM, "scratch");
+  part = (double*)scr;
+  CK(launch_mse_grad(numel, T->out_img, target, T->cot_img, part, loss, st));
+  CK(run_steps(T->tchain, ctx->d_err, st, &ctx->prof, &ctx->launches));
+  CK(cudaMemsetAsync(ctx->warm_g, 0, W->nparams * 4, st));
+  CK(T->run_wgrad(ctx->warm_g, 1.f, false, st, &ctx->launches));
+  ctx->warm_t += 1;
+  CK(launch_adam(W->nparams, W->master, ctx->warm_g, ctx->warm_m, ctx->warm_v, ctx->warm_t, lr,
+                 0.9f, 0.999f, 1e-8f, st));
+  CK(W->reform(st));
+  ctx->launches += 3 + 2 * (long long)W->layers.size();
+  return IDEQ_OK;
 }
-ideq_status ideq_warm_get(ideq_ctx* ctx, float*) {
-  return fail(ctx, IDEQ_ERR_UNSUPPORTED, "warm start not built yet");
+
+ideq_status ideq_warm_get(ideq_ctx* ctx, float* weights) {
+  if (!ctx || !weights) return fail(ctx, IDEQ_ERR_ARG, "bad arguments");
+  if (!ctx->warm_w) return fail(ctx, IDEQ_ERR_ARG, "no warm-start network");
+  CK(cudaMemcpyAsync(weights, ctx->warm_w->master, ctx->warm_w->nparams * 4,
+                     cudaMemcpyDeviceToDevice, ctx->stream));
+  return IDEQ_OK;
 }
 
 ideq_status ideq_prof_enable(ideq_ctx* ctx, int on) {

@@ -552,4 +552,64 @@ cudaError_t launch_dot(long long n, const float* a, const float* b, float scale,
   return cudaGetLastError();
 }
 
+// ===================================================================== warm start
+
+// cot = 2 (x - t) / numel; partial sums of (x - t)^2 for the mean squared error.
+__global__ void mse_grad_kernel(long long numel, const float* __restrict__ x,
+                                const float* __restrict__ t, float* __restrict__ cot,
+                                double* __restrict__ part) {
+  __shared__ double red[32];
+  double s = 0.0;
+  const float sc = (float)(2.0 / (double)numel);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < numel;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float d = x[i] - t[i];
+    cot[i] = sc * d;
+    s += (double)d * d;
+  }
+  const double tt = block_sum(s, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = tt;
+}
+
+__global__ void mean_final_kernel(int nb, const double* __restrict__ part, double inv,
+                                  double* __restrict__ out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) s += part[i];
+  const double t = block_sum(s, red);
+  if (threadIdx.x == 0 && out) *out = t * inv;
+}
+
+cudaError_t launch_mse_grad(long long numel, const float* x, const float* t, float* cot,
+                            double* part, double* loss, cudaStream_t st) {
+  mse_grad_kernel<<<128, 256, 0, st>>>(numel, x, t, cot, part);
+  mean_final_kernel<<<1, 128, 0, st>>>(128, part, 1.0 / (double)numel, loss);
+  return cudaGetLastError();
+}
+
+// Adam (Kingma & Ba) with bias correction; the optimiser of the paper's training
+// (App. D.1.3), PyTorch's default constants.
+__global__ void adam_kernel(long long n, float* __restrict__ p, const float* __restrict__ g,
+                            float* __restrict__ m, float* __restrict__ v, float lr, float b1,
+                            float b2, float eps, float c1, float c2) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+cudaError_t launch_adam(long long n, float* p, const float* g, float* m, float* v, int t, float lr,
+                        float b1, float b2, float eps, cudaStream_t st) {
+  const float c1 = (float)(1.0 - pow((double)b1, (double)t));
+  const float c2 = (float)(1.0 - pow((double)b2, (double)t));
+  const int blocks = (int)std::min<long long>((n + 255) / 256, 2048);
+  adam_kernel<<<blocks, 256, 0, st>>>(n, p, g, m, v, lr, b1, b2, eps, c1, c2);
+  return cudaGetLastError();
+}
+
 }  // namespace ideq

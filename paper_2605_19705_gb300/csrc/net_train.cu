@@ -115,8 +115,9 @@ struct TB {
 }  // namespace
 
 bool TrainPlan::build(NetWeights* wts, int n_, int H_, int W_, int prec_, double* gsum_,
-                      std::string* err) {
+                      std::string* err, bool warm_) {
   w = wts;
+  warm = warm_;
   n = n_;
   c = wts->desc.in_ch;
   H = H_;
@@ -136,6 +137,16 @@ bool TrainPlan::build(NetWeights* wts, int n_, int H_, int W_, int prec_, double
   if (!z || !r || !grad || !zd || !rd || !hvp) {
     *err = "cudaMalloc(train images) failed";
     return false;
+  }
+  out_img = r;
+  cot_img = r;
+  if (warm) {
+    out_img = hvp;  // x0 = z + W(z)
+    cot_img = grad; // dl/dx0, written by the loss kernel
+    if (d.kind != IDEQ_NET_CNN) {
+      *err = "the warm start is a plain conv net";
+      return false;
+    }
   }
   const auto& Ls = wts->layers;
 
@@ -166,8 +177,9 @@ bool TrainPlan::build(NetWeights* wts, int n_, int H_, int W_, int prec_, double
       const void* in = first ? (const void*)z : a[i - 1];
       const void* tin = first ? (const void*)zd : ad[i - 1];
       if (last) {
-        fsteps[i] = B.make(L, false, CM_CONV3, OM_IDENT, H, W, L.cin, L.cout, in, r, EP_AXPY_NCHW,
-                           z, nullptr, first, true, -1.f, gsum);
+        fsteps[i] = B.make(L, false, CM_CONV3, OM_IDENT, H, W, L.cin, L.cout, in, out_img,
+                           EP_AXPY_NCHW, z, nullptr, first, true, warm ? 1.f : -1.f,
+                           warm ? nullptr : gsum);
         jvp.push_back(B.make(L, false, CM_CONV3, OM_IDENT, H, W, L.cin, L.cout, tin, rd,
                              EP_AXPY_NCHW, zd, nullptr, first, true, -1.f, nullptr));
       } else {
@@ -184,9 +196,11 @@ bool TrainPlan::build(NetWeights* wts, int n_, int H_, int W_, int prec_, double
     for (int i = D - 1; i >= 0; --i) {
       const Layer& L = Ls[i];
       const bool last = i == D - 1, first = i == 0;
-      const void* tin = last ? (const void*)r : tcv[i];
+      const void* tin = last ? (const void*)cot_img : tcv[i];
       const void* pin = last ? (const void*)rd : pcv[i];
-      if (first) {
+      if (first && warm) {
+        // the warm start needs no input gradient: the chain ends at layer 1
+      } else if (first) {
         tchain.push_back(B.make(L, true, CM_CONV3, OM_IDENT, H, W, L.cout, L.cin, tin, grad,
                                 EP_AXPY_NCHW, r, nullptr, last, true, -1.f, nullptr));
         pchain.push_back(B.make(L, true, CM_CONV3, OM_IDENT, H, W, L.cout, L.cin, pin, hvp,
@@ -200,7 +214,7 @@ bool TrainPlan::build(NetWeights* wts, int n_, int H_, int W_, int prec_, double
       }
       // weight gradient of layer i: output cotangents (pchain, tchain) x inputs
       const void* pcot = last ? (const void*)rd : pcv[i];
-      const void* tcot = last ? (const void*)r : tcv[i];
+      const void* tcot = last ? (const void*)cot_img : tcv[i];
       B.wg(L, fsteps[i], first ? (const void*)zd : ad[i - 1], pcot, tcot);
     }
   } else {
@@ -374,18 +388,18 @@ bool TrainPlan::build(NetWeights* wts, int n_, int H_, int W_, int prec_, double
 }
 
 // dst (flat, PyTorch layout) += scale * gradient in the weights of
-// <pcot, out(primal)> + <tcot, out(tangent)> over every conv.  tcot terms are
-// skipped when with_tangent is false (plain reverse, e.g. the warm start).
-cudaError_t TrainPlan::run_wgrad(float* dst, float scale, bool with_tangent, cudaStream_t st,
+// <pcot, out(primal)> + <tcot, out(tangent)> over every conv (dual), or of
+// <tcot, out(primal)> alone (plain reverse chain, e.g. the warm start).
+cudaError_t TrainPlan::run_wgrad(float* dst, float scale, bool dual, cudaStream_t st,
                                  long long* launches) {
   for (const WgStep& g : wg) {
     const Layer& L = w->layers[g.layer];
     const long long nk = (long long)g.a.N() * g.a.K();
     cudaError_t e = cudaMemsetAsync(wg_acc, 0, nk * 4, st);
     if (e != cudaSuccess) return e;
-    e = launch_wgrad(g.a, g.in_dt, g.cot_dt, g.pcot, 1.f, wg_part, wg_acc, st);
+    e = launch_wgrad(g.a, g.in_dt, g.cot_dt, dual ? g.pcot : g.tcot, 1.f, wg_part, wg_acc, st);
     if (e != cudaSuccess) return e;
-    if (with_tangent) {
+    if (dual) {
       ConvArgs t = g.a;
       t.in = g.tin;
       e = launch_wgrad(t, g.in_dt, g.cot_dt, g.tcot, 1.f, wg_part, wg_acc, st);
@@ -394,7 +408,7 @@ cudaError_t TrainPlan::run_wgrad(float* dst, float scale, bool with_tangent, cud
     // accumulate the [N][K] forward-form gradient into the PyTorch layout
     e = launch_weight_unform_scaled(L.fwd_form, L.cin, L.cout, wg_acc, scale, dst + L.off, st);
     if (e != cudaSuccess) return e;
-    if (launches) *launches += with_tangent ? 5 : 3;
+    if (launches) *launches += dual ? 5 : 3;
   }
   return cudaSuccess;
 }

@@ -22,6 +22,11 @@ struct TrainPlan {
   NetWeights* w = nullptr;
   float *z = nullptr, *r = nullptr, *grad = nullptr;  // point, residual, grad g
   float *zd = nullptr, *rd = nullptr, *hvp = nullptr; // direction, rdot, Hess g . direction
+  // warm-start mode (plain CNN x0 = z + W(z)): forward output and the cotangent
+  // that starts the reverse chain
+  bool warm = false;
+  float* out_img = nullptr;
+  float* cot_img = nullptr;
   double* gsum = nullptr;
   std::vector<Step> fwd, tchain, jvp, pchain;
   std::vector<WgStep> wg;
@@ -30,9 +35,11 @@ struct TrainPlan {
   std::vector<void*> allocs;
   ~TrainPlan();
   void* alloc(size_t bytes);
-  bool build(NetWeights* w, int n, int H, int W, int prec, double* gsum, std::string* err);
-  cudaError_t run_wgrad(float* dst, float scale, bool with_tangent, cudaStream_t st,
-                        long long* launches);
+  bool build(NetWeights* w, int n, int H, int W, int prec, double* gsum, std::string* err,
+             bool warm = false);
+  // dual: dst += scale * sum_conv [pcot (x) input + tcot (x) tangent input]
+  // plain: dst += scale * sum_conv tcot (x) input (one reverse chain)
+  cudaError_t run_wgrad(float* dst, float scale, bool dual, cudaStream_t st, long long* launches);
 };
 
 int wgrad_splits(const ConvArgs& a);
@@ -40,5 +47,11 @@ cudaError_t launch_wgrad(const ConvArgs& a, int in_dt, int cot_dt, const void* c
                          float* part, float* dst, cudaStream_t st);
 cudaError_t launch_weight_unform_scaled(int form, int cin, int cout, const float* g, float scale,
                                         float* dst, cudaStream_t st);
+// cot = 2 (x - t) / numel and *loss = mean((x - t)^2) (FP64); part >= 128 doubles
+cudaError_t launch_mse_grad(long long numel, const float* x, const float* t, float* cot,
+                            double* part, double* loss, cudaStream_t st);
+// one Adam step (bias-corrected) on n parameters; t is the 1-based step count
+cudaError_t launch_adam(long long n, float* p, const float* g, float* m, float* v, int t, float lr,
+                        float b1, float b2, float eps, cudaStream_t st);
 
 }  // namespace ideq
