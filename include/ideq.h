@@ -211,6 +211,31 @@ ideq_status ideq_warm_train_step(ideq_ctx *ctx, ideq_shape shape, const float *a
 /* Copy the warm-start weights (device float32). */
 ideq_status ideq_warm_get(ideq_ctx *ctx, float *weights);
 
+/* ---- allocation-free RED update ------------------------------------------- */
+
+/* The paper has no counterpart of this call: it exists for callers that cannot
+ * allocate device memory -- code embedded in a framework that owns every device
+ * allocation, processes with a fixed memory budget, servers that must not
+ * allocate while serving.  It performs the RED update of Algorithm 1 on caller
+ * buffers, without a context:
+ *   x_new = z - tau (grad_f + lambda grad_g)
+ *   step_sq[b] = ||x_new_b - x_b||^2,  x_sq[b] = ||x_b||^2   (FP64, per image)
+ * n images of per_img floats each, contiguous (NCHW), device pointers; step_sq
+ * and x_sq are device arrays of n doubles (nullable).  It calls no cudaMalloc or
+ * cudaFree: its per-block partial sums live in one static device array of 65536
+ * doubles (512 KiB) that every GPU loading the library keeps until the process
+ * exits.  It needs 2 * n * min(64, ceil(per_img / 4096)) of them; larger requests
+ * (for instance more than 512 images of 256K floats or more) return
+ * IDEQ_ERR_ARG.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress) with the device
+ * current, so make it before any stream capture.  All calls share the array:
+ * calls that overlap on the GPU (different streams, no ordering) race; calls on
+ * one stream are safe.  Nothing in the array needs clearing between calls. */
+ideq_status ideq_red_update_noalloc(int n, int per_img, const float *z, const float *grad_f,
+                                    const float *grad_g, const float *x, float *x_new,
+                                    float lambda, float tau, double *step_sq, double *x_sq,
+                                    void *stream);
+
 /* ---- instrumentation ------------------------------------------------------ */
 
 /* When enabled, CUDA events bracket every launch of the tensor-core

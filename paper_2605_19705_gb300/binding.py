@@ -84,6 +84,8 @@ _sig = {
     "ideq_prof_enable": [c_void_p, c_int],
     "ideq_prof_read": [c_void_p, P(c_double), P(ctypes.c_int64), P(c_double)],
     "ideq_launch_count": [c_void_p, P(ctypes.c_int64)],
+    "ideq_red_update_noalloc": [c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                c_float, c_float, c_void_p, c_void_p, c_void_p],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
@@ -307,3 +309,20 @@ def ideq_launch_count(ctx: Context) -> int:
     ctx.check(_lib.ideq_launch_count(ctx.h, ctypes.byref(n)))
     return int(n.value)
 
+
+def ideq_red_update_noalloc(z, grad_f, grad_g, x, x_new, lam, tau, step_sq=None, x_sq=None):
+    """Context-free RED update for callers that cannot allocate device memory.
+
+    x_new = z - tau (grad_f + lam grad_g) with per-image FP64 ||x_new - x||^2 and
+    ||x||^2; every tensor is a caller-owned CUDA tensor (images (n, c, h, w) f32,
+    norms (n,) f64).  Runs on torch's current stream; allocates nothing."""
+    import torch
+    n = z.shape[0]
+    per = z.numel() // n
+    st = _lib.ideq_red_update_noalloc(n, per, _ptr(z, torch.float32), _ptr(grad_f, torch.float32),
+                                      _ptr(grad_g, torch.float32), _ptr(x, torch.float32),
+                                      _ptr(x_new, torch.float32), lam, tau,
+                                      _ptr(step_sq, torch.float64), _ptr(x_sq, torch.float64),
+                                      _stream())
+    if st != IDEQ_OK:
+        raise IdeqError(st, "ideq_red_update_noalloc failed")
