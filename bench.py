@@ -42,6 +42,12 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--ncu-steps", type=int, default=0,
+                    help="profiling mode: run this many inertial steps of the batch and exit "
+                         "(no timing, no JSON), for ncu captures")
+    ap.add_argument("--precision", default="fp16", choices=["fp16", "bf16", "fp32"],
+                    help="convolution arithmetic of the profiling mode")
+    ap.add_argument("--batch", type=int, default=0, help="profiling mode: batch size override")
     return ap.parse_args()
 
 
@@ -286,6 +292,28 @@ def cpu_baseline(iters_per_image):
                       f"to {iters_per_image:.1f} iterations per restoration"}
 
 
+def run_profile_steps(args):
+    """Plan set-up plus args.ncu_steps inertial steps (ideq_step) of the benchmark
+    batch; the target of the ncu captures summarised under profiles/."""
+    import torch
+    from paper_2605_19705_gb300 import build as pbuild
+    pbuild.build()
+    from paper_2605_19705_gb300 import binding as B
+    cfg, wl, _ = load_workload(args.batch or None)
+    prec = {"fp16": B.IDEQ_FP16, "bf16": B.IDEQ_BF16, "fp32": B.IDEQ_FP32}[args.precision]
+    ctx = B.Context(B.net_desc(cfg["net"], cfg["c"]), torch.tensor(wl["weights"], device="cuda"),
+                    prec)
+    op = B.make_operator(B.IDEQ_OP_BLUR, torch.tensor(wl["kern"], device="cuda"))
+    xt = torch.tensor(wl["x_true"], device="cuda")
+    y = B.ideq_apply_A(ctx, op, xt) + torch.tensor(wl["noise"], device="cuda")
+    xk = B.ideq_apply_AT(ctx, op, y)
+    xkm1 = xk.clone()
+    params = B.make_params(cfg["lam"], cfg["tau"], cfg["beta"])
+    for _ in range(args.ncu_steps):
+        B.ideq_step(ctx, op, y, xk, xkm1, params)
+    torch.cuda.synchronize()
+
+
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
@@ -330,7 +358,9 @@ def run_reference(args):
 
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.ncu_steps > 0:
+        run_profile_steps(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)

@@ -5,18 +5,25 @@
 //   warp 0      TMA producer: per K chunk of 64 channels, one box of 128 pixels
 //               x 64 channels of the NHWC 16-bit (bf16 or f16) activation
 //               (tap-shifted; the zero padding of the convolution is the TMA
-//               out-of-bounds fill) and one box of BN x 64 weights, into a
-//               STAGES-deep ring that runs across tile boundaries.
+//               out-of-bounds fill) and one box of BN x 64 weights, into a ring
+//               of shared-memory stages that runs across tile boundaries.
 //   warp 1      allocates 2 x BN TMEM columns (two accumulators) and issues
 //               tcgen05.mma (M=128, N=BN, K=16, 16-bit x 16-bit -> f32) from one
 //               elected lane; tcgen05.commit frees ring slots and hands a
 //               finished accumulator to the epilogue.
-//   warps 2..9  epilogue: tcgen05.ld the f32 accumulator (one pixel row per
-//               thread, half of the columns per warp), apply the fused
-//               epilogue, store 16-bit NHWC, and release the accumulator, so
-//               that it overlaps the MMAs of the next tile.
-// Shared-memory operands use the 128-byte swizzle that TMA writes and the
-// UMMA descriptor reads (8-row atoms of 128 B, stride 1024 B).
+//   warps 2..9  epilogue, per 64-column panel of the tile: tcgen05.ld the f32
+//               accumulator (one pixel row per thread, 32 columns per warp),
+//               read the auxiliary inputs (residual / skip / saved derivative)
+//               from shared memory, apply the fused epilogue, write the 16-bit
+//               results to shared memory, and let one thread store the panel
+//               with a TMA tensor store.  The auxiliary panels are TMA-loaded
+//               ahead (the next tile's while the MMAs run), the output staging
+//               is double-buffered, and the accumulator is released after its
+//               last read, so that the epilogue overlaps the MMAs of the next
+//               tile.
+// Every shared-memory matrix (operands, staging) uses the 128-byte swizzle:
+// 8-row atoms of 128 B, 16-byte chunk c of row r stored at chunk c ^ (r & 7),
+// which TMA writes/reads and the UMMA descriptor expects.
 // Every mbarrier wait is bounded (about 2 s of %globaltimer); an expired wait
 // sets *err_flag, all roles drain and the CTA returns after freeing TMEM.
 #include <cuda.h>
@@ -35,18 +42,15 @@ struct TcArgs {
   int mode, outmap, epi, act;
   int n, H, W, Cin, Cout, N;
   int Wt, Ht, tiles_w, tiles_h, tiles_n, nk, cpt;
-  void* out;
-  void* out2;
-  const void* aux0;
-  const void* aux1;
-  const void* aux2;
+  int stages;  // ring depth
+  int nout;    // staged outputs (1 or 2)
+  int naux;    // auxiliary inputs (0..3)
   int* err;
 };
 
 struct TcPlan {
-  CUtensorMap tmA;
-  CUtensorMap tmB;
-  int bn = 0, stages = 0, dt = DT_BF16;
+  CUtensorMap tmA, tmB, tmO[2], tmX[3];
+  int bn = 0, stages = 0, dt = DT_BF16, nout = 1, naux = 0;
   int Wt = 0, Ht = 0, tiles_w = 0, tiles_h = 0, tiles_n = 0, nk = 0, cpt = 0;
   dim3 grid;
   size_t smem = 0;
@@ -188,60 +192,91 @@ IDEQ_DEV void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-IDEQ_DEV float2 to_f2(__nv_bfloat162 h) { return __bfloat1622float2(h); }
-IDEQ_DEV float2 to_f2(__half2 h) { return __half22float2(h); }
-template <typename T> struct Pair;
-template <> struct Pair<__nv_bfloat16> {
-  using t = __nv_bfloat162;
-  static IDEQ_DEV t make(float a, float b) { return __floats2bfloat162_rn(a, b); }
-};
-template <> struct Pair<__half> {
-  using t = __half2;
-  static IDEQ_DEV t make(float a, float b) { return __floats2half2_rn(a, b); }
-};
-
-template <typename T>
-IDEQ_DEV void load16x16(const T* p, float (&v)[16]) {
-  using P2 = typename Pair<T>::t;
-  const uint4* q = (const uint4*)p;
-  const uint4 a = q[0], b = q[1];
-  const P2* h0 = (const P2*)&a;
-  const P2* h1 = (const P2*)&b;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const float2 f0 = to_f2(h0[i]);
-    const float2 f1 = to_f2(h1[i]);
-    v[2 * i] = f0.x;
-    v[2 * i + 1] = f0.y;
-    v[8 + 2 * i] = f1.x;
-    v[8 + 2 * i + 1] = f1.y;
-  }
-}
-
-template <typename T>
-IDEQ_DEV void store16x16(T* p, const float (&v)[16]) {
-  using P2 = typename Pair<T>::t;
-  uint4 a, b;
-  P2* h0 = (P2*)&a;
-  P2* h1 = (P2*)&b;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    h0[i] = Pair<T>::make(v[2 * i], v[2 * i + 1]);
-    h1[i] = Pair<T>::make(v[8 + 2 * i], v[8 + 2 * i + 1]);
-  }
-  uint4* q = (uint4*)p;
-  q[0] = a;
-  q[1] = b;
-}
-
-// ------------------------------------------------------------------ kernel
-
-constexpr int EPI_WARPS = 8;
-constexpr int TC_THREADS = 64 + 32 * EPI_WARPS;
-constexpr int A_BYTES = 128 * 128;  // 128 pixel rows x 64 16-bit channels
-
 IDEQ_DEV void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+IDEQ_DEV void tma_store_4d(const CUtensorMap* tm, uint32_t src, int c0, int c1, int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4, %5}], [%1];"
+      ::"l"(tm), "r"(src), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+      : "memory");
+}
+
+IDEQ_DEV void tma_store_5d(const CUtensorMap* tm, uint32_t src, int c0, int c1, int c2, int c3,
+                           int c4) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4, %5, %6}],"
+      " [%1];" ::"l"(tm),
+      "r"(src), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+      : "memory");
+}
+
+IDEQ_DEV void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+IDEQ_DEV void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+IDEQ_DEV void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+IDEQ_DEV void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Named barrier over the 8 epilogue warps, returning the OR of `v` over them.
+IDEQ_DEV bool epi_bar_or(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred pi, po;\n\t"
+      "setp.ne.u32 pi, %1, 0;\n\t"
+      "bar.red.or.pred po, 1, 256, pi;\n\t"
+      "selp.u32 %0, 1, 0, po;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v)
+      : "memory");
+  return r != 0;
+}
+
+// 16 consecutive 16-bit values of row `row` starting at 16-byte chunk c16 (even)
+// of a 128-byte-swizzled panel
+IDEQ_DEV uint32_t swz(uint32_t panel, int row, int c16) {
+  return panel + row * 128 + (((c16 ^ (row & 7)) & 7) << 4);
+}
+
+IDEQ_DEV void lds128(uint32_t a, uint4& v) {
+  asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "r"(a));
+}
+IDEQ_DEV void sts128(uint32_t a, const uint4& v) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z),
+               "r"(v.w)
+               : "memory");
+}
+
+template <typename T> struct H2;
+template <> struct H2<__nv_bfloat16> {
+  using t = __nv_bfloat162;
+  static IDEQ_DEV float2 f(t h) { return __bfloat1622float2(h); }
+  static IDEQ_DEV t mk(float a, float b) { return __floats2bfloat162_rn(a, b); }
+};
+template <> struct H2<__half> {
+  using t = __half2;
+  static IDEQ_DEV float2 f(t h) { return __half22float2(h); }
+  static IDEQ_DEV t mk(float a, float b) { return __floats2half2_rn(a, b); }
+};
+
+template <typename T>
+IDEQ_DEV void unpack8(const uint4& u, float* v) {
+  const typename H2<T>::t* h = (const typename H2<T>::t*)&u;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float2 f = H2<T>::f(h[i]);
+    v[2 * i] = f.x;
+    v[2 * i + 1] = f.y;
+  }
+}
+template <typename T>
+IDEQ_DEV uint4 pack8(const float* v) {
+  uint4 u;
+  typename H2<T>::t* h = (typename H2<T>::t*)&u;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) h[i] = H2<T>::mk(v[2 * i], v[2 * i + 1]);
+  return u;
 }
 
 struct TileCoord {
@@ -261,33 +296,62 @@ IDEQ_DEV TileCoord tile_coord(const TcArgs& a, int t, int bn) {
   return c;
 }
 
-// Persistent CTA (one per SM): tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...
-// The smem ring runs across tile boundaries; the TMEM accumulator is double
-// buffered (2 x BN columns) so that the epilogue of one tile overlaps the MMAs
-// of the next.  Barriers: full/empty per ring slot, tfull/tempty per TMEM
-// buffer (tempty counts one arrival per epilogue warp), drain for the error path.
-template <typename T, int BN, int STAGES>
+constexpr int EPI_WARPS = 8;
+constexpr int TC_THREADS = 64 + 32 * EPI_WARPS;
+constexpr int A_BYTES = 128 * 128;  // 128 pixel rows x 64 16-bit channels
+constexpr int PANEL = 128 * 128;    // 128 rows x 64 columns of 16-bit results
+
+// Epilogue TMA (load of auxiliary panels, store of result panels): 4-D NHWC
+// boxes (64 channels x Wt x Ht), or the 5-D depth-to-space view for OM_D2S.
+IDEQ_DEV void epi_tma(bool store, const TcArgs& a, const CUtensorMap* tm, uint32_t sm,
+                      const TileCoord& tc, int col, uint32_t bar) {
+  if (a.outmap == OM_D2S) {
+    const int q = col / a.Cout, co = col - q * a.Cout;
+    const int c0 = (q & 1) * a.Cout + co, di = q >> 1;
+    if (store)
+      tma_store_5d(tm, sm, c0, tc.w0, di, tc.h0, tc.img);
+    else
+      tma_load_5d(sm, tm, c0, tc.w0, di, tc.h0, tc.img, bar);
+  } else {
+    if (store)
+      tma_store_4d(tm, sm, col, tc.w0, tc.h0, tc.img);
+    else
+      tma_load_4d(sm, tm, col, tc.w0, tc.h0, tc.img, bar);
+  }
+}
+
+template <typename T, int BN>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     conv_tc_kernel(const __grid_constant__ CUtensorMap tmA,
-                   const __grid_constant__ CUtensorMap tmB, TcArgs a) {
+                   const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ CUtensorMap tmO0,
+                   const __grid_constant__ CUtensorMap tmO1,
+                   const __grid_constant__ CUtensorMap tmX0,
+                   const __grid_constant__ CUtensorMap tmX1,
+                   const __grid_constant__ CUtensorMap tmX2, TcArgs a) {
   constexpr int B_BYTES = BN * 128;
   constexpr uint32_t STAGE_TX = A_BYTES + B_BYTES;
+  constexpr int NPANEL = BN / 64;
+  const int ST = a.stages;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
-  uint8_t* sB = smem + STAGES * A_BYTES;
-  uint64_t* bars = (uint64_t*)(sB + STAGES * B_BYTES);
-  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 5);
+  uint8_t* sB = smem + ST * A_BYTES;
+  uint8_t* sOut = sB + ST * B_BYTES;          // [2 buffers][nout][PANEL]
+  uint8_t* sAux = sOut + 2 * a.nout * PANEL;  // [naux][PANEL]
+  uint64_t* bars = (uint64_t*)(sAux + a.naux * PANEL);
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * ST + 6);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
-  const uint32_t tfull0 = smem_u32(bars + 2 * STAGES);
-  const uint32_t tempty0 = smem_u32(bars + 2 * STAGES + 2);
-  const uint32_t drain = smem_u32(bars + 2 * STAGES + 4);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + ST);
+  const uint32_t tfull0 = smem_u32(bars + 2 * ST);
+  const uint32_t tempty0 = smem_u32(bars + 2 * ST + 2);
+  const uint32_t drain = smem_u32(bars + 2 * ST + 4);
+  const uint32_t auxbar = smem_u32(bars + 2 * ST + 5);
   const int ntiles = a.n * a.tiles_h * a.tiles_w * a.tiles_n;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < ST; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
@@ -296,6 +360,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       mbar_init(tempty0 + 8 * b, EPI_WARPS);
     }
     mbar_init(drain, 1);
+    mbar_init(auxbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -320,7 +385,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         const TileCoord tc = tile_coord(a, t, BN);
         for (int kc = 0; kc < a.nk; ++kc) {
-          const int s = g % STAGES, j = g / STAGES;
+          const int s = g % ST, j = g / ST;
           if (j > 0 && !mbar_wait(empty0 + 8 * s, (j - 1) & 1, a.err, 1)) {
             ok = false;
             break;
@@ -347,9 +412,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
       // tail: wait until the MMA warp released every slot still in use, so no
       // tcgen05.commit arrival is outstanding when the CTA exits.
-      const int first = g > STAGES ? g - STAGES : 0;
+      const int first = g > ST ? g - ST : 0;
       for (int i = first; i < g; ++i) {
-        const int s = i % STAGES, j = i / STAGES;
+        const int s = i % ST, j = i / ST;
         if (ok) ok = mbar_wait(empty0 + 8 * s, j & 1, a.err, 2);
         if (!ok) mbar_wait(full0 + 8 * s, j & 1, a.err, 2);  // our own copies in flight
       }
@@ -368,7 +433,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         tc_fence_after();
         const uint32_t td = tmem + (uint32_t)(b * BN);
         for (int kc = 0; kc < a.nk; ++kc) {
-          const int s = g % STAGES, j = g / STAGES;
+          const int s = g % ST, j = g / ST;
           if (!mbar_wait(full0 + 8 * s, j & 1, a.err, 3)) {
             ok = false;
             break;
@@ -390,50 +455,103 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
     }
   } else {
-    // epilogue: warp -> TMEM lane quarter (warp % 4) and column half ((warp - 2) / 4)
+    // ---------------- epilogue warps 2..9
     const int q = warp & 3, half = (warp - 2) >> 2;
     const int row = q * 32 + lane;
-    constexpr int HALF = BN / 2;
-    int lt = 0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
+    const bool elected = warp == 2 && lane == 0;
+    const CUtensorMap* tmO[2] = {&tmO0, &tmO1};
+    const CUtensorMap* tmX[3] = {&tmX0, &tmX1, &tmX2};
+    const uint32_t sOut0 = smem_u32(sOut), sAux0 = smem_u32(sAux);
+    // prefetch the auxiliary panel 0 of this CTA's first tile
+    if (elected && a.naux > 0 && (int)blockIdx.x < ntiles) {
+      const TileCoord tc = tile_coord(a, blockIdx.x, BN);
+      mbar_expect_tx(auxbar, (uint32_t)(a.naux * PANEL));
+      for (int i = 0; i < a.naux; ++i)
+        epi_tma(false, a, tmX[i], sAux0 + i * PANEL, tc, tc.n0, auxbar);
+    }
+    int lt = 0, pc = 0;
+    int aux_issued = (a.naux > 0 && (int)blockIdx.x < ntiles) ? 1 : 0;  // panels loaded
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++lt) {
       const int b = lt & 1, u = lt >> 1;
-      const bool ok = mbar_wait(tfull0 + 8 * b, u & 1, a.err, 4);
+      ok = mbar_wait(tfull0 + 8 * b, u & 1, a.err, 4);
       tc_fence_after();
       const TileCoord tc = tile_coord(a, t, BN);
-      const int ly = row / a.Wt, lx = row - ly * a.Wt;
-      const int y = tc.h0 + ly, x = tc.w0 + lx;
-      const bool valid = ok && y < a.H && x < a.W;
+      bool released = false;
+      for (int p = 0; p < NPANEL; ++p, ++pc) {
+        const int sb = pc & 1;
+        if (elected && pc >= 2) bulk_wait_read1();  // staging buffer sb is free again
+        if (epi_bar_or(!ok)) {                         // (A) all threads agree
+          ok = false;
+          break;
+        }
+        if (a.naux > 0) ok = mbar_wait(auxbar, pc & 1, a.err, 7);
+        const uint32_t ob = sOut0 + (sb * a.nout) * PANEL;
 #pragma unroll 1
-      for (int c0 = half * HALF; c0 < (half + 1) * HALF; c0 += 16) {
-        float v[16];
-        tmem_ld16(tmem + (uint32_t)(b * BN) + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
-        if (!valid) continue;
-        const int n = tc.n0 + c0;
-        size_t o;
-        if (a.outmap == OM_D2S) {
-          const int qq = n / a.Cout, co = n - qq * a.Cout;
-          const int oy = 2 * y + (qq >> 1), ox = 2 * x + (qq & 1);
-          o = (((size_t)tc.img * 2 * a.H + oy) * 2 * a.W + ox) * a.Cout + co;
-        } else {
-          o = (((size_t)tc.img * a.H + y) * a.W + x) * (size_t)a.Cout + n;
-        }
-        float x0[16], x1[16], x2[16], r[16], r2[16];
-        if (a.aux0) load16x16((const T*)a.aux0 + o, x0);
-        if (a.aux1) load16x16((const T*)a.aux1 + o, x1);
-        if (a.aux2) load16x16((const T*)a.aux2 + o, x2);
+        for (int jj = 0; jj < 2; ++jj) {
+          const int j = 2 * half + jj;  // 16-column chunk of the panel
+          float v[16];
+          tmem_ld16(tmem + (uint32_t)(b * BN + 64 * p + 16 * j) + ((uint32_t)(q * 32) << 16), v);
+          float x0[16], x1[16], x2[16], r[16], r2[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          r2[i] = 0.f;
-          r[i] = epi_math(a.epi, a.act, v[i], a.aux0 ? x0[i] : 0.f, a.aux1 ? x1[i] : 0.f,
-                          a.aux2 ? x2[i] : 0.f, &r2[i]);
+          for (int h = 0; h < 2; ++h) {
+            uint4 w4;
+            if (a.naux > 0) { lds128(swz(sAux0, row, 2 * j + h), w4); unpack8<T>(w4, x0 + 8 * h); }
+            if (a.naux > 1) { lds128(swz(sAux0 + PANEL, row, 2 * j + h), w4); unpack8<T>(w4, x1 + 8 * h); }
+            if (a.naux > 2) { lds128(swz(sAux0 + 2 * PANEL, row, 2 * j + h), w4); unpack8<T>(w4, x2 + 8 * h); }
+          }
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            r2[i] = 0.f;
+            r[i] = epi_math(a.epi, a.act, v[i], a.naux > 0 ? x0[i] : 0.f,
+                            a.naux > 1 ? x1[i] : 0.f, a.naux > 2 ? x2[i] : 0.f, &r2[i]);
+          }
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            sts128(swz(ob, row, 2 * j + h), pack8<T>(r + 8 * h));
+            if (a.nout > 1) sts128(swz(ob + PANEL, row, 2 * j + h), pack8<T>(r2 + 8 * h));
+          }
         }
-        store16x16((T*)a.out + o, r);
-        if (a.epi == EP_ACT || a.epi == EP_MUL_KEEP) store16x16((T*)a.out2 + o, r2);
+        if (p == NPANEL - 1) {  // last read of this accumulator: hand it back to the MMA warp
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(tempty0 + 8 * b);
+          released = true;
+        }
+        fence_async_smem();
+        if (epi_bar_or(!ok)) {  // (B) staging written, auxiliary panel consumed
+          ok = false;
+          break;
+        }
+        if (elected) {
+          for (int i = 0; i < a.nout; ++i) epi_tma(true, a, tmO[i], ob + i * PANEL, tc, tc.n0 + 64 * p, 0);
+          bulk_commit();
+          if (a.naux > 0) {  // prefetch the next auxiliary panel (this tile or the next)
+            int nt = t, np = p + 1;
+            if (np == NPANEL) {
+              nt = t + gridDim.x;
+              np = 0;
+            }
+            if (nt < ntiles) {
+              const TileCoord nc = tile_coord(a, nt, BN);
+              mbar_expect_tx(auxbar, (uint32_t)(a.naux * PANEL));
+              for (int i = 0; i < a.naux; ++i)
+                epi_tma(false, a, tmX[i], sAux0 + i * PANEL, nc, nc.n0 + 64 * np, auxbar);
+              ++aux_issued;
+            }
+          }
+        }
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(tempty0 + 8 * b);
-      if (!ok) break;
+      if (!released) {
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty0 + 8 * b);
+      }
+    }
+    if (elected) {
+      bulk_wait_all();
+      // on an early exit, let an auxiliary load that is still in flight land
+      if (a.naux > 0 && aux_issued > pc) mbar_wait(auxbar, (aux_issued - 1) & 1, a.err, 8);
     }
   }
   tc_fence_before();
@@ -468,22 +586,56 @@ static int pick_bn(int N) {
   return 64;
 }
 
+static int epi_nout(int epi) { return (epi == EP_ACT || epi == EP_MUL_KEEP) ? 2 : 1; }
+static int epi_naux(int epi) {
+  if (epi == EP_DUAL) return 3;
+  if (epi == EP_ADD || epi == EP_MUL || epi == EP_MUL_KEEP) return 1;
+  return 0;
+}
+
 bool tc_supported(const ConvArgs& a) {
   if (a.in_nchw || a.out_nchw || a.epi == EP_AXPY_NCHW) return false;
   if (a.Cin % 64 != 0) return false;
-  if (a.N() % 64 != 0) return false;
-  if (a.outmap == OM_D2S && a.Cout % 16 != 0) return false;
+  if (a.N() % 64 != 0 || a.Cout % 64 != 0) return false;
   if (a.mode == CM_DOWN && a.outmap != OM_IDENT) return false;
+  if (epi_naux(a.epi) >= 1 && !a.aux0) return false;
+  if (epi_naux(a.epi) >= 2 && (!a.aux1 || !a.aux2)) return false;
+  if (epi_nout(a.epi) == 2 && !a.out2) return false;
   return true;
 }
 
-template <int BN, int ST>
-static size_t smem_bytes() {
-  return 1024 + (size_t)ST * (A_BYTES + BN * 128) + (2 * ST + 5) * 8 + 16;
+static size_t fixed_smem(int nout, int naux, int stages) {
+  return 1024 + (size_t)(2 * nout + naux) * PANEL + (2 * stages + 6) * 8 + 16;
 }
 
-// ring depth: ~192 KB of operands per CTA (one persistent CTA per SM)
-static int stages_for(int bn) { return bn == 64 ? 8 : (bn == 128 ? 6 : 4); }
+constexpr size_t kMaxSmem = 227 * 1024;
+
+static bool encode(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap* m, CUtensorMapDataType dt,
+                   int rank, const void* base, const cuuint64_t* dims, const cuuint64_t* strides,
+                   const cuuint32_t* box) {
+  cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  return enc(m, dt, rank, const_cast<void*>(base), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// map of an epilogue tensor (output or auxiliary, both shaped like the output)
+static bool encode_epi(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap* m,
+                       CUtensorMapDataType dt, const ConvArgs& a, const TcPlan* p,
+                       const void* base) {
+  const cuuint64_t C = (cuuint64_t)a.Cout;
+  if (a.outmap == OM_D2S) {  // output image 2H x 2W viewed as [n][H][di][W][dj*C + co]
+    const cuuint64_t W2 = 2 * (cuuint64_t)a.W;
+    cuuint64_t dims[5] = {2 * C, (cuuint64_t)a.W, 2, (cuuint64_t)a.H, (cuuint64_t)a.n};
+    cuuint64_t strides[4] = {2 * C * 2, W2 * C * 2, 2 * W2 * C * 2, 2 * (cuuint64_t)a.H * 2 * W2 * C};
+    cuuint32_t box[5] = {64, (cuuint32_t)p->Wt, 1, (cuuint32_t)p->Ht, 1};
+    return encode(enc, m, dt, 5, base, dims, strides, box);
+  }
+  cuuint64_t dims[4] = {C, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.n};
+  cuuint64_t strides[3] = {C * 2, (cuuint64_t)a.W * C * 2, (cuuint64_t)a.H * a.W * C * 2};
+  cuuint32_t box[4] = {64, (cuuint32_t)p->Wt, (cuuint32_t)p->Ht, 1};
+  return encode(enc, m, dt, 4, base, dims, strides, box);
+}
 
 TcPlan* tc_plan_create(const ConvArgs& a, int dtype, std::string* err) {
   auto enc = get_encode();
@@ -503,7 +655,14 @@ TcPlan* tc_plan_create(const ConvArgs& a, int dtype, std::string* err) {
   p->dt = dtype;
   const int N = a.N();
   p->bn = pick_bn(N);
-  p->stages = stages_for(p->bn);
+  p->nout = epi_nout(a.epi);
+  p->naux = epi_naux(a.epi);
+  // ring depth: what is left of the shared memory after the epilogue staging
+  const size_t stage = (size_t)A_BYTES + (size_t)p->bn * 128;
+  int st = 8;
+  while (st > 2 && fixed_smem(p->nout, p->naux, st) + st * stage > kMaxSmem) --st;
+  p->stages = st;
+  p->smem = fixed_smem(p->nout, p->naux, st) + st * stage;
   // M tile: Ht x Wt pixels of the grid, Wt a power of two
   int wt = 1;
   while (wt < a.W && wt < 128) wt <<= 1;
@@ -527,7 +686,7 @@ TcPlan* tc_plan_create(const ConvArgs& a, int dtype, std::string* err) {
   }
   const CUtensorMapDataType dt =
       dtype == DT_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-  CUresult r;
+  bool ok;
   if (a.mode == CM_DOWN) {
     const int Hi = 2 * a.H, Wi = 2 * a.W;
     cuuint64_t dims[5] = {(cuuint64_t)(2 * a.Cin), (cuuint64_t)a.W, 2, (cuuint64_t)a.H,
@@ -535,71 +694,58 @@ TcPlan* tc_plan_create(const ConvArgs& a, int dtype, std::string* err) {
     cuuint64_t strides[4] = {(cuuint64_t)2 * a.Cin * 2, (cuuint64_t)Wi * a.Cin * 2,
                              (cuuint64_t)2 * Wi * a.Cin * 2, (cuuint64_t)Hi * Wi * a.Cin * 2};
     cuuint32_t box[5] = {64, (cuuint32_t)p->Wt, 1, (cuuint32_t)p->Ht, 1};
-    cuuint32_t es[5] = {1, 1, 1, 1, 1};
-    r = enc(&p->tmA, dt, 5, const_cast<void*>(a.in), dims, strides, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    ok = encode(enc, &p->tmA, dt, 5, a.in, dims, strides, box);
   } else {
     cuuint64_t dims[4] = {(cuuint64_t)a.Cin, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.n};
     cuuint64_t strides[3] = {(cuuint64_t)a.Cin * 2, (cuuint64_t)a.W * a.Cin * 2,
                              (cuuint64_t)a.H * a.W * a.Cin * 2};
     cuuint32_t box[4] = {64, (cuuint32_t)p->Wt, (cuuint32_t)p->Ht, 1};
-    cuuint32_t es[4] = {1, 1, 1, 1};
-    r = enc(&p->tmA, dt, 4, const_cast<void*>(a.in), dims, strides, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  }
-  if (r != CUDA_SUCCESS) {
-    *err = "cuTensorMapEncodeTiled(A) failed: " + std::to_string((int)r);
-    delete p;
-    return nullptr;
+    ok = encode(enc, &p->tmA, dt, 4, a.in, dims, strides, box);
   }
   {
     const int K = a.K();
     cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)N};
     cuuint64_t strides[1] = {(cuuint64_t)K * 2};
     cuuint32_t box[2] = {64, (cuuint32_t)p->bn};
-    cuuint32_t es[2] = {1, 1};
-    r = enc(&p->tmB, dt, 2, const_cast<void*>(a.wB), dims, strides, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) {
-      *err = "cuTensorMapEncodeTiled(B) failed: " + std::to_string((int)r);
-      delete p;
-      return nullptr;
-    }
+    ok = ok && encode(enc, &p->tmB, dt, 2, a.wB, dims, strides, box);
   }
-  switch (p->bn) {
-    case 64: p->smem = smem_bytes<64, 8>(); break;
-    case 128: p->smem = smem_bytes<128, 6>(); break;
-    default: p->smem = smem_bytes<256, 4>(); break;
+  const void* outs[2] = {a.out, a.out2};
+  const void* auxs[3] = {a.aux0, a.aux1, a.aux2};
+  for (int i = 0; i < 2; ++i)
+    ok = ok && encode_epi(enc, &p->tmO[i], dt, a, p, i < p->nout ? outs[i] : a.out);
+  for (int i = 0; i < 3; ++i)
+    ok = ok && encode_epi(enc, &p->tmX[i], dt, a, p, i < p->naux ? auxs[i] : a.out);
+  if (!ok) {
+    *err = "cuTensorMapEncodeTiled failed";
+    delete p;
+    return nullptr;
   }
   return p;
 }
 
 void tc_plan_destroy(TcPlan* p) { delete p; }
 
-template <typename T, int BN, int ST>
+template <typename T, int BN>
 static cudaError_t launch_bn(const TcPlan* p, const TcArgs& ta, cudaStream_t st) {
   static bool attr_set = false;  // per instantiation; set before first launch
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<T, BN, ST>,
+    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<T, BN>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_bytes<BN, ST>());
+                                         (int)kMaxSmem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  conv_tc_kernel<T, BN, ST><<<p->grid, TC_THREADS, smem_bytes<BN, ST>(), st>>>(p->tmA, p->tmB,
-                                                                               ta);
+  conv_tc_kernel<T, BN><<<p->grid, TC_THREADS, p->smem, st>>>(
+      p->tmA, p->tmB, p->tmO[0], p->tmO[1], p->tmX[0], p->tmX[1], p->tmX[2], ta);
   return cudaGetLastError();
 }
 
 template <typename T>
 static cudaError_t launch_typed(const TcPlan* p, const TcArgs& t, cudaStream_t st) {
   switch (p->bn) {
-    case 64: return launch_bn<T, 64, 8>(p, t, st);
-    case 128: return launch_bn<T, 128, 6>(p, t, st);
-    default: return launch_bn<T, 256, 4>(p, t, st);
+    case 64: return launch_bn<T, 64>(p, t, st);
+    case 128: return launch_bn<T, 128>(p, t, st);
+    default: return launch_bn<T, 256>(p, t, st);
   }
 }
 
@@ -622,11 +768,9 @@ cudaError_t launch_conv_tc(const TcPlan* p, const ConvArgs& a, int* err_flag, cu
   t.tiles_n = p->tiles_n;
   t.nk = p->nk;
   t.cpt = p->cpt;
-  t.out = a.out;
-  t.out2 = a.out2;
-  t.aux0 = a.aux0;
-  t.aux1 = a.aux1;
-  t.aux2 = a.aux2;
+  t.stages = p->stages;
+  t.nout = p->nout;
+  t.naux = p->naux;
   t.err = err_flag;
   if (p->dt == DT_F16) return launch_typed<__half>(p, t, st);
   return launch_typed<__nv_bfloat16>(p, t, st);

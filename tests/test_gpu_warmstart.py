@@ -1,0 +1,103 @@
+"""Learned warm start on the GPU: forward and training kernels vs the FP64 oracle,
+and what the trained network saves over the plain initialisation A^T y."""
+import numpy as np
+import pytest
+
+from gpu_common import ctx_for, op_for, rel, setup
+from oracle import nets, solver, warmstart
+from synth import generators as G
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2605_19705_gb300 import build
+    build.build()
+
+
+def _warm(cfg):
+    from paper_2605_19705_gb300 import binding as B
+    chans = cfg["warm"]["chans"]
+    desc = B.net_desc({"type": "cnn", "chans": chans, "act": "relu"}, cfg["c"])
+    return desc, chans
+
+
+def test_warm_forward_and_training_steps_match_oracle():
+    from paper_2605_19705_gb300 import binding as B
+    from paper_2605_19705_gb300 import warmstart as W
+    cfg, wl, net, ops, ys = setup("C4", n=2, h=40, w=56)
+    ctx = ctx_for(cfg, wl, B.IDEQ_FP32)
+    desc, chans = _warm(cfg)
+    w0 = wl["warm_weights"]
+    W.warm_set(ctx, desc, torch.tensor(w0, device="cuda"))
+    rng = np.random.default_rng(4)
+    aty = rng.uniform(0, 1, ys.shape).astype(np.float32)
+    target = np.clip(aty + 0.1 * rng.standard_normal(ys.shape), 0, 1).astype(np.float32)
+    ta, tt = torch.tensor(aty, device="cuda"), torch.tensor(target, device="cuda")
+    x0 = W.warm_forward(ctx, ta).double().cpu().numpy()
+    ops_, wt = nets.cnn_program(chans, "relu")
+    onet = nets.Net(ops_, wt, w0)
+    ref = np.stack([warmstart.warm_forward(onet, aty[i].astype(np.float64)) for i in range(2)])
+    assert rel(x0, ref) < 1e-5
+    # three Adam steps: losses before each step and the final weights
+    adam = warmstart.Adam(onet.nparams, lr=1e-3)
+    p = np.asarray(w0, np.float64)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for step in range(3):
+        onet = nets.Net(ops_, wt, p)
+        lo, g = warmstart.warm_loss_grad(onet, aty.astype(np.float64), target.astype(np.float64))
+        W.warm_train_step(ctx, ta, tt, 1e-3, loss)
+        assert abs(float(loss.item()) - lo) < 1e-5 * lo, (step, float(loss.item()), lo)
+        p = adam.step(p, g)
+    wg = W.warm_get(ctx, onet.nparams).double().cpu().numpy()
+    assert rel(wg - w0, p - w0) < 1e-3, rel(wg - w0, p - w0)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_trained_warm_start_saves_iterations_at_equal_residual(prec):
+    """Train W on equilibria of 48 training images (saturation after blur, 64^2 RGB),
+    then solve 8 held-out images from A^T y and from the warm start: the warm start
+    needs fewer iterations to the same stopping residual, and the two restorations
+    agree within 0.05 dB."""
+    from paper_2605_19705_gb300 import binding as B
+    from paper_2605_19705_gb300 import warmstart as W
+    P = B.IDEQ_FP32 if prec == "fp32" else B.IDEQ_FP16
+    train_cfg, train_wl, _, _, ys_tr = setup("C4", n=48, h=64, w=64,
+                                             seeds=dict(img=9000, noise=9500, weights=2001,
+                                                        kernel=0, mask=0, warm=2004))
+    test_cfg, test_wl, _, _, ys_te = setup("C4", n=8, h=64, w=64)
+    ctx = ctx_for(train_cfg, train_wl, P)
+    desc, chans = _warm(train_cfg)
+    W.warm_set(ctx, desc, torch.tensor(train_wl["warm_weights"], device="cuda"))
+    op_tr = op_for(train_cfg, train_wl)
+    params = B.make_params(train_cfg["lam"], train_cfg["tau"], train_cfg["beta"], tol=1e-4,
+                           max_iter=3000)
+    atys, xbars = [], []
+    for i in range(0, 48, 8):  # equilibria of the plain solver, 8 images at a time
+        op_i = B.make_operator(B.IDEQ_OP_SATBLUR, torch.tensor(train_wl["kern"][i:i + 8],
+                                                               device="cuda"), sat_gain=2.0)
+        a, x = W.equilibria(ctx, op_i, torch.tensor(ys_tr[i:i + 8], device="cuda"), params)
+        atys.append(a)
+        xbars.append(x)
+    atys, xbars = torch.cat(atys), torch.cat(xbars)
+    hist = W.train(ctx, atys, xbars, steps=300, lr=2e-3, batch=8)
+    assert hist[-1] < hist[0]
+    op_te = op_for(test_cfg, test_wl)
+    y = torch.tensor(ys_te, device="cuda")
+    res = {}
+    for init in (B.IDEQ_INIT_ATY, B.IDEQ_INIT_WARM):
+        p = B.make_params(test_cfg["lam"], test_cfg["tau"], test_cfg["beta"], tol=1e-4,
+                          max_iter=3000, init=init)
+        info = B.InfoBuffers(8)
+        x, st = B.ideq_solve(ctx, op_te, y, p, info=info)
+        res[init] = (x, info.iters.float().mean().item(), info.rel_res.max().item())
+    (x_p, it_p, r_p), (x_w, it_w, r_w) = res[B.IDEQ_INIT_ATY], res[B.IDEQ_INIT_WARM]
+    assert r_p < 1e-4 and r_w < 1e-4
+    assert it_w < it_p, (it_w, it_p)
+    xt = torch.tensor(test_wl["x_true"], device="cuda", dtype=torch.float64)
+    psnr = lambda x: (10 * torch.log10(1.0 / ((x.double() - xt) ** 2).mean(dim=(1, 2, 3))))
+    assert float((psnr(x_p) - psnr(x_w)).abs().max()) < 0.05
