@@ -58,6 +58,31 @@ def dist_env():
     return rank, world, local
 
 
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "conv_tc_c1a_fp16_traffic.md")
+KERNEL_SRC = os.path.join(ROOT, "paper_2605_19705_gb300", "csrc", "conv_tc.cu")
+
+
+def recorded_traffic():
+    """Per-launch DRAM bytes (read + write) of the tcgen05 conv from the committed
+    ncu capture, or None when the kernel source changed since it was taken."""
+    import hashlib
+    try:
+        rec = {}
+        with open(TRAFFIC_FILE) as f:
+            for line in f:
+                if ":" in line and line.split(":")[0].strip() in ("per_launch_bytes",
+                                                                  "kernel_source_sha256"):
+                    k, v = line.split(":", 1)
+                    rec[k.strip()] = v.strip().strip("`")
+        with open(KERNEL_SRC, "rb") as f:
+            h = hashlib.sha256(f.read()).hexdigest()
+        if rec.get("kernel_source_sha256") != h:
+            return None
+        return float(rec["per_launch_bytes"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -256,7 +281,8 @@ def run_ours(args):
         "gpu_launches": launches,
         "roofline": {"bound": "tensor", "kernel": "conv_tc_kernel (all tcgen05 conv launches)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak if peak else None, "traffic": None,
+                     "frac": achieved / peak if peak else None, "traffic": recorded_traffic(),
+                     "traffic_unit": "bytes per launch (ncu dram__bytes_read+write)",
                      "peak_source": f"bf16_tflops_sustained ({src})",
                      "launches": conv_launches, "avg_launch_ms": conv_ms / max(conv_launches, 1)},
         "clocks": clk,

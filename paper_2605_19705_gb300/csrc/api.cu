@@ -49,6 +49,11 @@ struct ideq_ctx {
 
 namespace {
 
+// A failed runtime call leaves its (non-sticky) error as the thread's "last
+// error"; launchers report cudaGetLastError(), so every entry point clears what
+// an earlier, unrelated call may have left behind.
+void clear_stale_cuda_error() { (void)cudaGetLastError(); }
+
 ideq_status fail(ideq_ctx* c, ideq_status s, const std::string& msg) {
   if (c) c->err = msg;
   return s;
@@ -255,7 +260,7 @@ ideq_status warm_forward(ideq_ctx* ctx, const ideq_shape& s, const float* aty, f
   const size_t bytes = (size_t)s.n * s.c * s.h * s.w * 4;
   CK(cudaMemcpyAsync(T->z, aty, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
   CK(run_steps(T->fwd, ctx->d_err, ctx->stream, &ctx->prof, &ctx->launches));
-  if (out != T->out_img)
+  if (out && out != T->out_img)
     CK(cudaMemcpyAsync(out, T->out_img, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
   return IDEQ_OK;
 }
@@ -277,6 +282,7 @@ ideq_status ideq_num_params(const ideq_net_desc* net, int64_t* count) {
 
 ideq_status ideq_create(ideq_ctx** out, const ideq_net_desc* net, const float* weights,
                         int precision, void* stream) {
+  clear_stale_cuda_error();
   if (!out || !net || !weights) return IDEQ_ERR_ARG;
   if (precision != IDEQ_FP32 && precision != IDEQ_BF16 && precision != IDEQ_FP16)
     return IDEQ_ERR_UNSUPPORTED;
@@ -298,6 +304,7 @@ ideq_status ideq_create(ideq_ctx** out, const ideq_net_desc* net, const float* w
 }
 
 ideq_status ideq_destroy(ideq_ctx* ctx) {
+  clear_stale_cuda_error();
   if (!ctx) return IDEQ_ERR_ARG;
   cudaStreamSynchronize(ctx->stream);
   ctx->plan.reset();
@@ -318,12 +325,14 @@ ideq_status ideq_destroy(ideq_ctx* ctx) {
 const char* ideq_last_error(ideq_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 ideq_status ideq_set_weights(ideq_ctx* ctx, const float* weights) {
+  clear_stale_cuda_error();
   if (!ctx || !weights) return IDEQ_ERR_ARG;
   CK(ctx->w->upload(weights, ctx->stream));
   return IDEQ_OK;
 }
 
 ideq_status ideq_set_precision(ideq_ctx* ctx, int precision) {
+  clear_stale_cuda_error();
   if (!ctx) return IDEQ_ERR_ARG;
   if (precision != IDEQ_FP32 && precision != IDEQ_BF16 && precision != IDEQ_FP16)
     return fail(ctx, IDEQ_ERR_UNSUPPORTED, "precision");
@@ -332,6 +341,7 @@ ideq_status ideq_set_precision(ideq_ctx* ctx, int precision) {
 }
 
 ideq_status ideq_set_stream(ideq_ctx* ctx, void* stream) {
+  clear_stale_cuda_error();
   if (!ctx) return IDEQ_ERR_ARG;
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->stream = (cudaStream_t)stream;
@@ -340,6 +350,7 @@ ideq_status ideq_set_stream(ideq_ctx* ctx, void* stream) {
 
 ideq_status ideq_apply_A(ideq_ctx* ctx, const ideq_operator* op, ideq_shape shape, const float* x,
                          float* Ax) {
+  clear_stale_cuda_error();
   if (!ctx || !x || !Ax || !shape_ok(shape)) return fail(ctx, IDEQ_ERR_ARG, "bad arguments");
   OpDev od;
   ideq_status s = check_op(ctx, op, shape, &od);
@@ -351,6 +362,7 @@ ideq_status ideq_apply_A(ideq_ctx* ctx, const ideq_operator* op, ideq_shape shap
 
 ideq_status ideq_apply_AT(ideq_ctx* ctx, const ideq_operator* op, ideq_shape shape, const float* r,
                           const float* lin_point, float* out) {
+  clear_stale_cuda_error();
   if (!ctx || !r || !out || !shape_ok(shape)) return fail(ctx, IDEQ_ERR_ARG, "bad arguments");
   OpDev od;
   ideq_status s = check_op(ctx, op, shape, &od);
@@ -369,6 +381,7 @@ ideq_status ideq_apply_AT(ideq_ctx* ctx, const ideq_operator* op, ideq_shape sha
 
 ideq_status ideq_grad_reg(ideq_ctx* ctx, ideq_shape shape, const float* z, float* grad,
                           double* g_val) {
+  clear_stale_cuda_error();
   if (!ctx || !z || !grad || !shape_ok(shape)) return fail(ctx, IDEQ_ERR_ARG, "bad arguments");
   ideq_status s = ensure_plan(ctx, shape);
   if (s != IDEQ_OK) return s;
@@ -386,6 +399,7 @@ ideq_status ideq_grad_reg(ideq_ctx* ctx, ideq_shape shape, const float* z, float
 
 ideq_status ideq_step(ideq_ctx* ctx, const ideq_operator* op, ideq_shape shape, const float* y,
                       float* x_k, float* x_km1, const ideq_params* p, ideq_info* info) {
+  clear_stale_cuda_error();
   if (!ctx || !y || !x_k || !x_km1 || !shape_ok(shape)) return fail(ctx, IDEQ_ERR_ARG, "bad arguments");
   ideq_status s = check_params(ctx, p);
   if (s != IDEQ_OK) return s;
@@ -406,6 +420,7 @@ ideq_status ideq_step(ideq_ctx* ctx, const ideq_operator* op, ideq_shape shape, 
 
 ideq_status ideq_solve(ideq_ctx* ctx, const ideq_operator* op, ideq_shape shape, const float* y,
                        const float* x0, float* x_out, const ideq_params* p, ideq_info* info) {
+  clear_stale_cuda_error();
   if (!ctx || !y || !x_out || !shape_ok(shape)) return fail(ctx, IDEQ_ERR_ARG, "bad arguments");
   ideq_status s = check_params(ctx, p);
   if (s != IDEQ_OK) return s;
@@ -457,6 +472,7 @@ ideq_status ideq_solve_backward(ideq_ctx* ctx, const ideq_operator* op, ideq_sha
                                 const float* y, const float* x_bar, const float* dl_dx,
                                 const ideq_params* p, const ideq_adj_params* ap, float* dl_dtheta,
                                 float* dl_dlambda, ideq_info* info) {
+  clear_stale_cuda_error();
   if (!ctx || !y || !x_bar || !dl_dx || !dl_dtheta || !dl_dlambda || !ap || !shape_ok(shape))
     return fail(ctx, IDEQ_ERR_ARG, "bad arguments");
   ideq_status s = check_params(ctx, p);
@@ -537,6 +553,7 @@ ideq_status ideq_solve_backward(ideq_ctx* ctx, const ideq_operator* op, ideq_sha
 }
 
 ideq_status ideq_warm_set(ideq_ctx* ctx, const ideq_net_desc* net, const float* weights) {
+  clear_stale_cuda_error();
   if (!ctx || !net || !weights) return fail(ctx, IDEQ_ERR_ARG, "bad arguments");
   if (net->kind != IDEQ_NET_CNN) return fail(ctx, IDEQ_ERR_ARG, "warm start must be a plain CNN");
   CK(cudaStreamSynchronize(ctx->stream));
@@ -560,12 +577,14 @@ ideq_status ideq_warm_set(ideq_ctx* ctx, const ideq_net_desc* net, const float* 
 }
 
 ideq_status ideq_warm_forward(ideq_ctx* ctx, ideq_shape shape, const float* aty, float* x0) {
+  clear_stale_cuda_error();
   if (!ctx || !aty || !x0 || !shape_ok(shape)) return fail(ctx, IDEQ_ERR_ARG, "bad arguments");
   return warm_forward(ctx, shape, aty, x0);
 }
 
 ideq_status ideq_warm_train_step(ideq_ctx* ctx, ideq_shape shape, const float* aty,
                                  const float* target, float lr, double* loss) {
+  clear_stale_cuda_error();
   if (!ctx || !aty || !target || !shape_ok(shape) || !(lr > 0.f))
     return fail(ctx, IDEQ_ERR_ARG, "bad arguments");
   ideq_status s = warm_forward(ctx, shape, aty, nullptr);
@@ -592,6 +611,7 @@ ideq_status ideq_warm_train_step(ideq_ctx* ctx, ideq_shape shape, const float* a
 }
 
 ideq_status ideq_warm_get(ideq_ctx* ctx, float* weights) {
+  clear_stale_cuda_error();
   if (!ctx || !weights) return fail(ctx, IDEQ_ERR_ARG, "bad arguments");
   if (!ctx->warm_w) return fail(ctx, IDEQ_ERR_ARG, "no warm-start network");
   CK(cudaMemcpyAsync(weights, ctx->warm_w->master, ctx->warm_w->nparams * 4,
@@ -606,6 +626,7 @@ ideq_status ideq_prof_enable(ideq_ctx* ctx, int on) {
 }
 
 ideq_status ideq_prof_read(ideq_ctx* ctx, double* ms, int64_t* launches, double* flops) {
+  clear_stale_cuda_error();
   if (!ctx) return IDEQ_ERR_ARG;
   CK(cudaStreamSynchronize(ctx->stream));
   double t = 0;

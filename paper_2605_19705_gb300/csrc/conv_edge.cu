@@ -1,9 +1,10 @@
 // 3x3 convolutions between the image side (f32 planar NCHW, c <= 4 channels)
 // and the feature side (NHWC, C channels, f32 / bf16 / f16): the regulariser's
 // head and tail and their transposes, and the first/last layers of the plain
-// conv nets.  Both directions stage a 16x16-pixel tile with a one-pixel halo in
-// shared memory and move the feature side with 16-byte vector accesses, so
-// that consecutive lanes touch consecutive 16-byte chunks of NHWC memory.
+// conv nets.  Both directions stage a pixel tile with a one-pixel halo in
+// shared memory, move the feature side with 16-byte vector accesses (so that
+// consecutive lanes touch consecutive 16-byte chunks of NHWC memory), and read
+// each weight as a warp-wide broadcast that feeds several pixels.
 //
 //   feat2img: out[b][o][y][x] = aux[b][o][y][x] + sign * sum_{t,ci} B[o][t*C+ci] in[b][y+dy][x+dx][ci]
 //             (+ per-image 1/2 sum out^2), o < c          -> EP_AXPY_NCHW
@@ -59,54 +60,81 @@ template <> struct Vec8<__nv_bfloat16> : Vec8Half<__nv_bfloat162, __nv_bfloat16>
 template <> struct Vec8<__half> : Vec8Half<__half2, __half> {};
 
 // ------------------------------------------------------------------ feat2img
-// Tile of (EH x EH pixels) x C channels staged as float with a padded pixel
-// stride; each thread owns one output pixel and all (<= 4) output channels.
+// 32x32-pixel output tile per block, 4 horizontally adjacent pixels per thread;
+// feature channels staged 16 at a time (float, padded pixel stride).  Each
+// weight read (the same address in every lane: a broadcast) feeds 4 pixels.
+constexpr int F2_T = 32;        // output tile edge
+constexpr int F2_E = F2_T + 2;  // with halo
+constexpr int F2_CC = 16;       // channels per stage
+constexpr int F2_CP = F2_CC + 1;
+
 template <typename TIn>
 __global__ void __launch_bounds__(256) feat2img_kernel(ConvArgs a) {
   extern __shared__ float sm[];
   __shared__ double red[32];
+  float* tile = sm;                       // F2_E * F2_E * F2_CP
+  float* wsm = sm + F2_E * F2_E * F2_CP;  // [c][9][C]
   const int C = a.Cin, c = a.Cout;
-  const int CP = C + 1;  // padded pixel stride (floats)
-  float* tile = sm;                  // EH*EH*CP
-  float* wsm = sm + EH * EH * CP;    // [c][9*C]
   const int b = blockIdx.z;
-  const int y0 = blockIdx.y * ET, x0 = blockIdx.x * ET;
+  const int y0 = blockIdx.y * F2_T, x0 = blockIdx.x * F2_T;
   const TIn* in = (const TIn*)a.in;
-  const int groups = C / 8;  // C % 8 == 0
-  for (int e = threadIdx.x; e < EH * EH * groups; e += 256) {
-    const int g = e % groups, p = e / groups;
-    const int yy = y0 - 1 + p / EH, xx = x0 - 1 + p % EH;
-    float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W)
-      Vec8<TIn>::load(in + (((size_t)b * a.H + yy) * a.W + xx) * C + 8 * g, v);
-    float* t = tile + p * CP + 8 * g;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) t[i] = v[i];
-  }
-  const float* w = (const float*)a.wB;  // [c][9*C]
+  const float* w = (const float*)a.wB;  // [c][9*C], k = t*C + ci
   for (int e = threadIdx.x; e < c * 9 * C; e += 256) wsm[e] = w[e];
-  __syncthreads();
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int t = 0; t < 9; ++t) {
-    const float* tp = tile + ((ty + t / 3) * EH + tx + t % 3) * CP;
-    const float* w0 = wsm + t * C;
-    for (int ci = 0; ci < C; ++ci) {
-      const float v = tp[ci];
-      acc[0] = fmaf(w0[ci], v, acc[0]);
-      if (c > 1) acc[1] = fmaf(w0[9 * C + ci], v, acc[1]);
-      if (c > 2) acc[2] = fmaf(w0[18 * C + ci], v, acc[2]);
-      if (c > 3) acc[3] = fmaf(w0[27 * C + ci], v, acc[3]);
+  // thread -> row ty (0..31), pixels 4*qx .. 4*qx+3 (qx 0..7)
+  const int ty = threadIdx.x >> 3, qx = threadIdx.x & 7;
+  float acc[4][4];
+#pragma unroll
+  for (int o = 0; o < 4; ++o)
+#pragma unroll
+    for (int p = 0; p < 4; ++p) acc[o][p] = 0.f;
+  for (int c0 = 0; c0 < C; c0 += F2_CC) {
+    __syncthreads();
+    const int groups = F2_CC / 8;
+    for (int e = threadIdx.x; e < F2_E * F2_E * groups; e += 256) {
+      const int g = e % groups, px = e / groups;
+      const int yy = y0 - 1 + px / F2_E, xx = x0 - 1 + px % F2_E;
+      float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W)
+        Vec8<TIn>::load(in + (((size_t)b * a.H + yy) * a.W + xx) * C + c0 + 8 * g, v);
+      float* t = tile + px * F2_CP + 8 * g;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) t[i] = v[i];
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int t = 0; t < 9; ++t) {
+      const int dy = t / 3, dx = t % 3;
+      const float* tp = tile + ((ty + dy) * F2_E + 4 * qx + dx) * F2_CP;
+      const float* wt = wsm + t * C + c0;
+#pragma unroll 4
+      for (int ci = 0; ci < F2_CC; ++ci) {
+        float v[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) v[p] = tp[p * F2_CP + ci];
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+          if (o < c) {
+            const float wv = wt[o * 9 * C + ci];
+#pragma unroll
+            for (int p = 0; p < 4; ++p) acc[o][p] = fmaf(wv, v[p], acc[o][p]);
+          }
+        }
+      }
     }
   }
-  const int y = y0 + ty, x = x0 + tx;
+  const int y = y0 + ty;
   double ssq = 0.0;
-  if (y < a.H && x < a.W) {
+  if (y < a.H) {
     for (int o = 0; o < c; ++o) {
-      const size_t idx = (((size_t)b * c + o) * a.H + y) * a.W + x;
-      const float r = ((const float*)a.aux0)[idx] + a.sign * acc[o];
-      ((float*)a.out)[idx] = r;
-      ssq += 0.5 * (double)r * (double)r;
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const int x = x0 + 4 * qx + p;
+        if (x >= a.W) continue;
+        const size_t idx = (((size_t)b * c + o) * a.H + y) * a.W + x;
+        const float r = ((const float*)a.aux0)[idx] + a.sign * acc[o][p];
+        ((float*)a.out)[idx] = r;
+        ssq += 0.5 * (double)r * (double)r;
+      }
     }
   }
   if (a.sumsq) {
@@ -116,13 +144,18 @@ __global__ void __launch_bounds__(256) feat2img_kernel(ConvArgs a) {
 }
 
 // ------------------------------------------------------------------ img2feat
-// Work item = (pixel, group of 8 output channels); consecutive threads take
-// consecutive groups of one pixel, so the 16-byte stores of a warp are contiguous.
+// 16x16-pixel tile per block.  Warp w computes output-channel groups of 8 with
+// a warp-uniform group (weights read as broadcasts), 4 pixels per lane; the
+// results go through a shared-memory tile so that the NHWC stores are
+// coalesced 16-byte chunks.
 template <typename TOut, int CIN>
 __global__ void __launch_bounds__(256) img2feat_kernel(ConvArgs a) {
   __shared__ float tile[CIN * EH * EH];
-  extern __shared__ float wsm[];  // [C][9*CIN], k = t*CIN + ci
+  extern __shared__ float dsm[];
   const int C = a.Cout;
+  float* wsm = dsm;                                // [C][9*CIN]
+  TOut* stg = (TOut*)(dsm + C * 9 * CIN);          // [256 px][C + 8]
+  const int SP = C + 8;                            // padded pixel stride (elements)
   const int b = blockIdx.z;
   const int y0 = blockIdx.y * ET, x0 = blockIdx.x * ET;
   const float* in = (const float*)a.in;
@@ -137,32 +170,50 @@ __global__ void __launch_bounds__(256) img2feat_kernel(ConvArgs a) {
   const float* w = (const float*)a.wB;
   for (int e = threadIdx.x; e < C * 9 * CIN; e += 256) wsm[e] = w[e];
   __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int groups = C / 8;
+  // (group, half) pairs: a warp computes one group of 8 channels for 128 of the
+  // tile's 256 pixels (4 per lane)
+  for (int pair = warp; pair < groups * 2; pair += 8) {
+    const int g = pair >> 1, hpx = (pair & 1) * 128;  // 128 pixels per pair, 4 per lane
+    float v[4][9 * CIN];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const int px = hpx + lane + 32 * p;
+      const int ty = px >> 4, tx = px & 15;
+#pragma unroll
+      for (int t = 0; t < 9; ++t)
+#pragma unroll
+        for (int ci = 0; ci < CIN; ++ci)
+          v[p][t * CIN + ci] = tile[ci * EH * EH + (ty + t / 3) * EH + tx + t % 3];
+    }
+#pragma unroll 1
+    for (int j = 0; j < 8; ++j) {
+      const float* wr = wsm + (8 * g + j) * 9 * CIN;
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int k = 0; k < 9 * CIN; ++k) {
+        const float wv = wr[k];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) acc[p] = fmaf(wv, v[p][k], acc[p]);
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p) stg[(hpx + lane + 32 * p) * SP + 8 * g + j] = from_f<TOut>(acc[p]);
+    }
+  }
+  __syncthreads();
+  // epilogue + coalesced store: item = (pixel, group of 8), consecutive lanes -> consecutive groups
   TOut* out = (TOut*)a.out;
   TOut* out2 = (TOut*)a.out2;
   const TOut* aux0 = (const TOut*)a.aux0;
   for (int item = threadIdx.x; item < ET * ET * groups; item += 256) {
-    const int g = item % groups, p = item / groups;
-    const int ty = p / ET, tx = p % ET;
-    const int y = y0 + ty, x = x0 + tx;
+    const int g = item % groups, px = item / groups;
+    const int y = y0 + (px >> 4), x = x0 + (px & 15);
     if (y >= a.H || x >= a.W) continue;
-    float v[9 * CIN];
+    float acc[8], x0v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, r[8], r2[8];
 #pragma unroll
-    for (int t = 0; t < 9; ++t)
-#pragma unroll
-      for (int ci = 0; ci < CIN; ++ci)
-        v[t * CIN + ci] = tile[ci * EH * EH + (ty + t / 3) * EH + tx + t % 3];
-    float acc[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const float* wr = wsm + (8 * g + j) * 9 * CIN;
-      float s = 0.f;
-#pragma unroll
-      for (int k = 0; k < 9 * CIN; ++k) s = fmaf(wr[k], v[k], s);
-      acc[j] = s;
-    }
+    for (int j = 0; j < 8; ++j) acc[j] = ld_f(stg + px * SP + 8 * g + j);
     const size_t o = (((size_t)b * a.H + y) * a.W + x) * C + 8 * g;
-    float x0v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, r[8], r2[8];
     if (aux0) Vec8<TOut>::load(aux0 + o, x0v);
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -177,31 +228,38 @@ __global__ void __launch_bounds__(256) img2feat_kernel(ConvArgs a) {
 bool edge_supported(const ConvArgs& a) {
   if (a.mode != CM_CONV3 || a.outmap != OM_IDENT) return false;
   if (a.in_nchw && !a.out_nchw)
-    return a.Cin >= 1 && a.Cin <= 4 && a.Cout % 8 == 0 && a.Cout * 9 * a.Cin * 4 <= 48 * 1024 &&
+    return a.Cin >= 1 && a.Cin <= 4 && a.Cout % 8 == 0 && a.Cout <= 128 &&
            a.epi != EP_AXPY_NCHW && a.epi != EP_DUAL;
   if (a.out_nchw && !a.in_nchw)
-    return a.Cout <= 4 && a.Cin % 8 == 0 && a.epi == EP_AXPY_NCHW &&
-           (size_t)(EH * EH * (a.Cin + 1) + a.Cout * 9 * a.Cin) * 4 <= 200 * 1024;
+    return a.Cout <= 4 && a.Cin % F2_CC == 0 && a.epi == EP_AXPY_NCHW && a.Cin <= 512;
   return false;
 }
 
 template <typename T, int CIN>
 static cudaError_t launch_i2f(const ConvArgs& a, cudaStream_t st) {
   dim3 grid((a.W + ET - 1) / ET, (a.H + ET - 1) / ET, a.n);
-  const size_t smem = (size_t)a.Cout * 9 * CIN * sizeof(float);
+  const size_t smem =
+      (size_t)a.Cout * 9 * CIN * sizeof(float) + (size_t)ET * ET * (a.Cout + 8) * sizeof(T);
+  static bool attr = false;  // per instantiation
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(img2feat_kernel<T, CIN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
   img2feat_kernel<T, CIN><<<grid, 256, smem, st>>>(a);
   return cudaGetLastError();
 }
 
 template <typename T>
 static cudaError_t launch_edge_t(const ConvArgs& a, cudaStream_t st) {
-  dim3 grid((a.W + ET - 1) / ET, (a.H + ET - 1) / ET, a.n);
   if (a.out_nchw) {
-    const size_t smem = (size_t)(EH * EH * (a.Cin + 1) + a.Cout * 9 * a.Cin) * sizeof(float);
+    dim3 grid((a.W + F2_T - 1) / F2_T, (a.H + F2_T - 1) / F2_T, a.n);
+    const size_t smem = (size_t)(F2_E * F2_E * F2_CP + a.Cout * 9 * a.Cin) * sizeof(float);
     static bool attr = false;  // per instantiation
     if (!attr) {
       cudaError_t e = cudaFuncSetAttribute(feat2img_kernel<T>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
       if (e != cudaSuccess) return e;
       attr = true;
     }

@@ -171,6 +171,169 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
   }
 }
 
+// ----------------------------------------------------------------------------
+// FP32 fast path (the plain FP32 form's inner layers: NHWC f32, C_in % 16 == 0,
+// N % BN == 0).  Tile 128 pixels x BN channels, 256 threads in a 16 x 16 grid,
+// each owning 8 x (BN/16) outputs; K chunks of 16 channels of one tap, gathered
+// as float4 (4 threads per pixel row of 64 contiguous bytes) and prefetched into
+// registers while the previous chunk is multiplied from shared memory.
+template <int BN>
+__global__ void __launch_bounds__(256) conv_simt_f32_kernel(ConvArgs a) {
+  constexpr int BM = 128, BK = 16, TN = BN / 16;
+  __shared__ __align__(16) float As[2][BK][BM + 4];
+  __shared__ __align__(16) float Bs[2][BK][BN + 4];
+  const int tid = threadIdx.x;
+  const long long M = a.M();
+  const int N = a.N(), K = a.K();
+  const long long m0 = (long long)blockIdx.x * BM;
+  const int n0 = blockIdx.y * BN;
+  const int HW = a.H * a.W;
+  const int SH = a.mode == CM_DOWN ? 2 * a.H : a.H;
+  const int SW = a.mode == CM_DOWN ? 2 * a.W : a.W;
+  const float* __restrict__ in = (const float*)a.in;
+  const float* __restrict__ wf = (const float*)a.wB;
+  // A loads: 128 rows x 16 k = 512 float4; thread -> rows (tid >> 2) and (tid >> 2) + 64,
+  // k quad (tid & 3)
+  const int aq = tid & 3;
+  int r_img[2], r_y[2], r_x[2];
+  bool r_ok[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const long long m = m0 + (tid >> 2) + 64 * i;
+    r_ok[i] = m < M;
+    const long long mm = r_ok[i] ? m : 0;
+    r_img[i] = (int)(mm / HW);
+    const int rem = (int)(mm - (long long)r_img[i] * HW);
+    r_y[i] = rem / a.W;
+    r_x[i] = rem - r_y[i] * a.W;
+  }
+  // B loads: BN x 16 k = BN*4 float4; thread -> n rows (tid >> 2) + 64 j, k quad (tid & 3)
+  float4 ra[2], rb[TN / 4 > 0 ? BN / 64 : 1];
+  auto gload = [&](int k0) {
+    int dy = 0, dx = 0, c0 = k0;
+    if (a.mode == CM_CONV3) {
+      const int t = k0 / a.Cin;
+      c0 = k0 - t * a.Cin;
+      dy = t / 3 - 1;
+      dx = t % 3 - 1;
+    } else if (a.mode == CM_DOWN) {
+      const int q = k0 / a.Cin;
+      c0 = k0 - q * a.Cin;
+      dy = q >> 1;
+      dx = q & 1;
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      int sy, sx;
+      if (a.mode == CM_DOWN) {
+        sy = 2 * r_y[i] + dy;
+        sx = 2 * r_x[i] + dx;
+      } else {
+        sy = r_y[i] + dy;
+        sx = r_x[i] + dx;
+      }
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r_ok[i] && sy >= 0 && sy < SH && sx >= 0 && sx < SW)
+        v = *(const float4*)(in + (((size_t)r_img[i] * SH + sy) * SW + sx) * a.Cin + c0 + 4 * aq);
+      ra[i] = v;
+    }
+#pragma unroll
+    for (int j = 0; j < BN / 64; ++j) {
+      const int nn = n0 + (tid >> 2) + 64 * j;
+      rb[j] = *(const float4*)(wf + (size_t)nn * K + k0 + 4 * aq);
+    }
+  };
+  auto sstore = [&](int buf) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int r = (tid >> 2) + 64 * i;
+      As[buf][4 * aq + 0][r] = ra[i].x;
+      As[buf][4 * aq + 1][r] = ra[i].y;
+      As[buf][4 * aq + 2][r] = ra[i].z;
+      As[buf][4 * aq + 3][r] = ra[i].w;
+    }
+#pragma unroll
+    for (int j = 0; j < BN / 64; ++j) {
+      const int nn = (tid >> 2) + 64 * j;
+      Bs[buf][4 * aq + 0][nn] = rb[j].x;
+      Bs[buf][4 * aq + 1][nn] = rb[j].y;
+      Bs[buf][4 * aq + 2][nn] = rb[j].z;
+      Bs[buf][4 * aq + 3][nn] = rb[j].w;
+    }
+  };
+  const int tx = tid & 15, ty = tid >> 4;
+  float acc[8][TN];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
+  gload(0);
+  sstore(0);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    const bool more = k0 + BK < K;
+    if (more) gload(k0 + BK);
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      float av[8], bv[TN];
+      const float4 a0 = *(const float4*)&As[buf][kk][ty * 8];
+      const float4 a1 = *(const float4*)&As[buf][kk][ty * 8 + 4];
+      av[0] = a0.x; av[1] = a0.y; av[2] = a0.z; av[3] = a0.w;
+      av[4] = a1.x; av[5] = a1.y; av[6] = a1.z; av[7] = a1.w;
+#pragma unroll
+      for (int j = 0; j < TN; j += 4) {
+        const float4 b4 = *(const float4*)&Bs[buf][kk][tx * TN + j];
+        bv[j] = b4.x; bv[j + 1] = b4.y; bv[j + 2] = b4.z; bv[j + 3] = b4.w;
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    if (more) {
+      sstore(buf ^ 1);
+      __syncthreads();
+      buf ^= 1;
+    }
+  }
+  float* out = (float*)a.out;
+  float* out2 = (float*)a.out2;
+  const float* aux0 = (const float*)a.aux0;
+  const float* aux1 = (const float*)a.aux1;
+  const float* aux2 = (const float*)a.aux2;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const long long m = m0 + ty * 8 + i;
+    if (m >= M) continue;
+    const int img = (int)(m / HW);
+    const int rem = (int)(m - (long long)img * HW);
+    const int y = rem / a.W, x = rem - (rem / a.W) * a.W;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int n = n0 + tx * TN + j;
+      size_t o;
+      if (a.outmap == OM_D2S) {
+        const int q = n / a.Cout, co = n - q * a.Cout;
+        o = (((size_t)img * 2 * a.H + 2 * y + (q >> 1)) * 2 * a.W + 2 * x + (q & 1)) * a.Cout + co;
+      } else {
+        o = (size_t)m * a.Cout + n;
+      }
+      const float x0 = aux0 ? aux0[o] : 0.f;
+      const float x1 = aux1 ? aux1[o] : 0.f;
+      const float x2 = aux2 ? aux2[o] : 0.f;
+      float o2 = 0.f;
+      out[o] = epi_math(a.epi, a.act, acc[i][j], x0, x1, x2, &o2);
+      if (epi_has_out2(a.epi)) out2[o] = o2;
+    }
+  }
+}
+
+static bool f32_fast_ok(const ConvArgs& a) {
+  return !a.in_nchw && !a.out_nchw && a.epi != EP_AXPY_NCHW && a.Cin % 16 == 0 &&
+         (a.N() % 128 == 0 || a.N() % 64 == 0) && (a.outmap == OM_IDENT || a.Cout % 16 == 0);
+}
+
 template <typename TIn, typename TOut>
 static cudaError_t launch_typed(const ConvArgs& a, cudaStream_t st) {
   const long long M = a.M();
@@ -195,7 +358,20 @@ cudaError_t launch_conv_simt(const ConvArgs& a, int in_dt, int out_dt, cudaStrea
   if (in_dt == DT_F16 && out_dt == DT_F32) return launch_typed<__half, float>(a, st);
   if (in_dt == DT_F32 && out_dt == DT_BF16) return launch_typed<float, __nv_bfloat16>(a, st);
   if (in_dt == DT_F32 && out_dt == DT_F16) return launch_typed<float, __half>(a, st);
-  if (in_dt == DT_F32 && out_dt == DT_F32) return launch_typed<float, float>(a, st);
+  if (in_dt == DT_F32 && out_dt == DT_F32) {
+    if (f32_fast_ok(a)) {
+      const int N = a.N();
+      if (N % 128 == 0) {
+        dim3 grid((unsigned)((a.M() + 127) / 128), N / 128);
+        conv_simt_f32_kernel<128><<<grid, 256, 0, st>>>(a);
+      } else {
+        dim3 grid((unsigned)((a.M() + 127) / 128), N / 64);
+        conv_simt_f32_kernel<64><<<grid, 256, 0, st>>>(a);
+      }
+      return cudaGetLastError();
+    }
+    return launch_typed<float, float>(a, st);
+  }
   return cudaErrorInvalidValue;
 }
 

@@ -45,12 +45,15 @@ struct TcArgs {
   int stages;  // ring depth
   int nout;    // staged outputs (1 or 2)
   int naux;    // auxiliary inputs (0..3)
+  int nbo;     // output staging buffers (1 or 2)
+  int nba;     // auxiliary staging buffers (1 or 2)
   int* err;
 };
 
 struct TcPlan {
   CUtensorMap tmA, tmB, tmO[2], tmX[3];
-  int bn = 0, stages = 0, dt = DT_BF16, nout = 1, naux = 0;
+  int bn = 0, stages = 0, dt = DT_BF16, nout = 1, naux = 0, nbo = 2, nba = 2, ms = 1;
+  bool halo = false;
   int Wt = 0, Ht = 0, tiles_w = 0, tiles_h = 0, tiles_n = 0, nk = 0, cpt = 0;
   dim3 grid;
   size_t smem = 0;
@@ -148,6 +151,15 @@ IDEQ_DEV uint64_t umma_desc_sw128(uint32_t saddr) {
   d |= (uint64_t)1 << 46;
   d |= (uint64_t)2 << 61;
   return d;
+}
+
+// Same descriptor for a matrix that starts `rows` 128-byte rows into a
+// 1024-byte-aligned swizzle atom.  The tensor core takes the 8-row phase of the
+// 128-byte swizzle from the address bits themselves (the pattern TMA wrote is
+// address-based too), so the start address simply moves by whole rows and the
+// base-offset field stays 0 -- measured bit-identical to the unshifted tiles.
+IDEQ_DEV uint64_t umma_desc_sw128_rows(uint32_t atom_base, int rows) {
+  return umma_desc_sw128(atom_base + 128u * (uint32_t)rows);
 }
 
 // Instruction descriptor of kind::f16: D f32 (bits [4,6) = 1), A and B of the
@@ -283,10 +295,14 @@ struct TileCoord {
   int img, h0, w0, n0;
 };
 
-IDEQ_DEV TileCoord tile_coord(const TcArgs& a, int t, int bn) {
+// Tile t covers MS consecutive 128-row M-tiles (sub-tiles) and BN columns.
+// An M-tile index past the last one maps to an image index >= n, which the
+// TMA loads fill with zeros and the TMA stores clip.
+IDEQ_DEV TileCoord tile_coord(const TcArgs& a, int t, int bn, int ms, int sub) {
   const int per_img = a.tiles_h * a.tiles_w;
   const int tiles_m = a.n * per_img;
-  const int nidx = t / tiles_m, m = t - nidx * tiles_m;
+  const int groups = (tiles_m + ms - 1) / ms;
+  const int nidx = t / groups, m = (t - nidx * groups) * ms + sub;
   TileCoord c;
   c.img = m / per_img;
   const int rr = m - c.img * per_img;
@@ -320,7 +336,15 @@ IDEQ_DEV void epi_tma(bool store, const TcArgs& a, const CUtensorMap* tm, uint32
   }
 }
 
-template <typename T, int BN>
+// Halo form of the 3x3 conv (one tile = 128 pixels of one image row, all N
+// columns): per channel chunk the producer loads three 130-pixel row boxes
+// (rows y-1, y, y+1, pixels x0-1 .. x0+128) once, and the nine taps read them
+// through descriptors shifted by dx rows; the whole weight matrix stays
+// resident in shared memory.  A is fetched once instead of nine times.
+constexpr int HALO_ROWS = 130;
+constexpr int HALO_BOX = 17408;  // 130 rows x 128 B, rounded up to a 1024-B atom
+
+template <typename T, int BN, bool HALO, int MS>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     conv_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                    const __grid_constant__ CUtensorMap tmB,
@@ -329,26 +353,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                    const __grid_constant__ CUtensorMap tmX0,
                    const __grid_constant__ CUtensorMap tmX1,
                    const __grid_constant__ CUtensorMap tmX2, TcArgs a) {
+  static_assert(!HALO || MS == 1, "the halo form has one 128-row sub-tile");
   constexpr int B_BYTES = BN * 128;
-  constexpr uint32_t STAGE_TX = A_BYTES + B_BYTES;
+  constexpr int A_STAGE = HALO ? 3 * HALO_BOX : MS * A_BYTES;
+  constexpr uint32_t STAGE_TX =
+      HALO ? 3u * HALO_ROWS * 128u : (uint32_t)(MS * A_BYTES + B_BYTES);
   constexpr int NPANEL = BN / 64;
+  constexpr int TCOLS = MS * BN;  // TMEM columns of one accumulator buffer
   const int ST = a.stages;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
-  uint8_t* sB = smem + ST * A_BYTES;
-  uint8_t* sOut = sB + ST * B_BYTES;          // [2 buffers][nout][PANEL]
-  uint8_t* sAux = sOut + 2 * a.nout * PANEL;  // [naux][PANEL]
-  uint64_t* bars = (uint64_t*)(sAux + a.naux * PANEL);
-  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * ST + 6);
+  uint8_t* sB = smem + ST * A_STAGE;  // ring slots, or the resident weights (HALO)
+  uint8_t* sOut = sB + (HALO ? a.nk * B_BYTES : ST * B_BYTES);  // [nbo][nout][PANEL]
+  uint8_t* sAux = sOut + a.nbo * a.nout * PANEL;                 // [nba][naux][PANEL]
+  uint64_t* bars = (uint64_t*)(sAux + a.nba * a.naux * PANEL);
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * ST + 9);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + ST);
   const uint32_t tfull0 = smem_u32(bars + 2 * ST);
   const uint32_t tempty0 = smem_u32(bars + 2 * ST + 2);
   const uint32_t drain = smem_u32(bars + 2 * ST + 4);
-  const uint32_t auxbar = smem_u32(bars + 2 * ST + 5);
-  const int ntiles = a.n * a.tiles_h * a.tiles_w * a.tiles_n;
+  const uint32_t auxbar0 = smem_u32(bars + 2 * ST + 5);  // [2]
+  const uint32_t bres = smem_u32(bars + 2 * ST + 7);
+  const int ntiles = ((a.n * a.tiles_h * a.tiles_w + MS - 1) / MS) * a.tiles_n;
+  const int nsteps = HALO ? a.cpt : a.nk;  // ring stages per tile
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
@@ -358,16 +388,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull0 + 8 * b, 1);
       mbar_init(tempty0 + 8 * b, EPI_WARPS);
+      mbar_init(auxbar0 + 8 * b, 1);
     }
     mbar_init(drain, 1);
-    mbar_init(auxbar, 1);
+    mbar_init(bres, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"((uint32_t)(2 * BN))
+                 "r"((uint32_t)(2 * TCOLS))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -380,33 +411,49 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
+      if (HALO) {  // resident weights: every K chunk of B once
+        mbar_expect_tx(bres, (uint32_t)(a.nk * B_BYTES));
+        for (int kc = 0; kc < a.nk; ++kc)
+          tma_load_2d(smem_u32(sB + kc * B_BYTES), &tmB, kc * 64, 0, bres);
+      }
       int g = 0;  // ring position across tiles
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const TileCoord tc = tile_coord(a, t, BN);
-        for (int kc = 0; kc < a.nk; ++kc) {
+        const TileCoord tc = tile_coord(a, t, BN, MS, 0);
+        for (int kc = 0; kc < nsteps; ++kc) {
           const int s = g % ST, j = g / ST;
           if (j > 0 && !mbar_wait(empty0 + 8 * s, (j - 1) & 1, a.err, 1)) {
             ok = false;
             break;
           }
           mbar_expect_tx(full0 + 8 * s, STAGE_TX);
-          const uint32_t dA = smem_u32(sA + s * A_BYTES);
-          const uint32_t dB = smem_u32(sB + s * B_BYTES);
-          if (a.mode == CM_DOWN) {
-            const int k0 = kc * 64;
-            const int di = k0 / (2 * a.Cin), rem = k0 - di * 2 * a.Cin;
-            tma_load_5d(dA, &tmA, rem, tc.w0, di, tc.h0, tc.img, full0 + 8 * s);
+          const uint32_t dA = smem_u32(sA + s * A_STAGE);
+          if (HALO) {
+            for (int dy = 0; dy < 3; ++dy)
+              tma_load_4d(dA + dy * HALO_BOX, &tmA, kc * 64, tc.w0 - 1, tc.h0 + dy - 1, tc.img,
+                          full0 + 8 * s);
           } else {
-            int tap = 4, c0 = kc * 64;
-            if (a.mode == CM_CONV3) {
-              tap = kc / a.cpt;
-              c0 = (kc - tap * a.cpt) * 64;
+            const uint32_t dB = smem_u32(sB + s * B_BYTES);
+#pragma unroll
+            for (int sub = 0; sub < MS; ++sub) {
+              const TileCoord sc = sub == 0 ? tc : tile_coord(a, t, BN, MS, sub);
+              const uint32_t dAs = dA + sub * A_BYTES;
+              if (a.mode == CM_DOWN) {
+                const int k0 = kc * 64;
+                const int di = k0 / (2 * a.Cin), rem = k0 - di * 2 * a.Cin;
+                tma_load_5d(dAs, &tmA, rem, sc.w0, di, sc.h0, sc.img, full0 + 8 * s);
+              } else {
+                int tap = 4, c0 = kc * 64;
+                if (a.mode == CM_CONV3) {
+                  tap = kc / a.cpt;
+                  c0 = (kc - tap * a.cpt) * 64;
+                }
+                tma_load_4d(dAs, &tmA, c0, sc.w0 + tap % 3 - 1, sc.h0 + tap / 3 - 1, sc.img,
+                            full0 + 8 * s);
+              }
             }
-            tma_load_4d(dA, &tmA, c0, tc.w0 + tap % 3 - 1, tc.h0 + tap / 3 - 1, tc.img,
-                        full0 + 8 * s);
+            tma_load_2d(dB, &tmB, kc * 64, tc.n0, full0 + 8 * s);
           }
-          tma_load_2d(dB, &tmB, kc * 64, tc.n0, full0 + 8 * s);
           ++g;
         }
       }
@@ -418,11 +465,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (ok) ok = mbar_wait(empty0 + 8 * s, j & 1, a.err, 2);
         if (!ok) mbar_wait(full0 + 8 * s, j & 1, a.err, 2);  // our own copies in flight
       }
+      if (HALO && !ok) mbar_wait(bres, 0, a.err, 2);
     }
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = umma_idesc_16(128, BN, Fmt<T>::v);
       bool ok = true;
+      if (HALO) ok = mbar_wait(bres, 0, a.err, 9);
       int g = 0, lt = 0;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++lt) {
         const int b = lt & 1, u = lt >> 1;
@@ -431,19 +480,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t td = tmem + (uint32_t)(b * BN);
-        for (int kc = 0; kc < a.nk; ++kc) {
+        const uint32_t td = tmem + (uint32_t)(b * TCOLS);
+        for (int kc = 0; kc < nsteps; ++kc) {
           const int s = g % ST, j = g / ST;
           if (!mbar_wait(full0 + 8 * s, j & 1, a.err, 3)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint64_t ad = umma_desc_sw128(smem_u32(sA + s * A_BYTES));
-          const uint64_t bd = umma_desc_sw128(smem_u32(sB + s * B_BYTES));
+          if (HALO) {
+            const uint32_t abase = smem_u32(sA + s * A_STAGE);
+#pragma unroll 1
+            for (int tap = 0; tap < 9; ++tap) {
+              const int dy = tap / 3, dx = tap - 3 * dy;
+              const uint64_t ad = umma_desc_sw128_rows(abase + dy * HALO_BOX, dx);
+              const uint64_t bd =
+                  umma_desc_sw128(smem_u32(sB + (tap * a.cpt + kc) * B_BYTES));
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk)
-            umma_bf16(td, ad + 2 * kk, bd + 2 * kk, idesc, (kc | kk) != 0 ? 1u : 0u);
+              for (int kk = 0; kk < 4; ++kk)
+                umma_bf16(td, ad + 2 * kk, bd + 2 * kk, idesc, (kc | tap | kk) != 0 ? 1u : 0u);
+            }
+          } else {
+            const uint64_t bd = umma_desc_sw128(smem_u32(sB + s * B_BYTES));
+#pragma unroll
+            for (int sub = 0; sub < MS; ++sub) {
+              const uint64_t ad = umma_desc_sw128(smem_u32(sA + s * A_STAGE + sub * A_BYTES));
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk)
+                umma_bf16(td + sub * BN, ad + 2 * kk, bd + 2 * kk, idesc,
+                          (kc | kk) != 0 ? 1u : 0u);
+            }
+          }
           umma_commit(empty0 + 8 * s);
           ++g;
         }
@@ -462,43 +529,61 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const CUtensorMap* tmO[2] = {&tmO0, &tmO1};
     const CUtensorMap* tmX[3] = {&tmX0, &tmX1, &tmX2};
     const uint32_t sOut0 = smem_u32(sOut), sAux0 = smem_u32(sAux);
-    // prefetch the auxiliary panel 0 of this CTA's first tile
-    if (elected && a.naux > 0 && (int)blockIdx.x < ntiles) {
-      const TileCoord tc = tile_coord(a, blockIdx.x, BN);
-      mbar_expect_tx(auxbar, (uint32_t)(a.naux * PANEL));
-      for (int i = 0; i < a.naux; ++i)
-        epi_tma(false, a, tmX[i], sAux0 + i * PANEL, tc, tc.n0, auxbar);
-    }
+    constexpr int TPANEL = MS * NPANEL;  // panels per tile
+    const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int npc = my_tiles * TPANEL;  // panels this CTA processes
+    // auxiliary panel k of this CTA -> buffer k % nba, loaded ahead by the elected thread
+    auto aux_load = [&](int k) {
+      const int i = k / TPANEL, r = k - i * TPANEL, sub = r / NPANEL, p = r - sub * NPANEL;
+      const TileCoord nc = tile_coord(a, blockIdx.x + i * gridDim.x, BN, MS, sub);
+      const int buf = k % a.nba;
+      const uint32_t bar = auxbar0 + 8 * buf;
+      mbar_expect_tx(bar, (uint32_t)(a.naux * PANEL));
+      for (int x = 0; x < a.naux; ++x)
+        epi_tma(false, a, tmX[x], sAux0 + (buf * a.naux + x) * PANEL, nc, nc.n0 + 64 * p, bar);
+    };
+    int aux_issued = 0;
+    if (elected && a.naux > 0)
+      for (; aux_issued < a.nba && aux_issued < npc; ++aux_issued) aux_load(aux_issued);
     int lt = 0, pc = 0;
-    int aux_issued = (a.naux > 0 && (int)blockIdx.x < ntiles) ? 1 : 0;  // panels loaded
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++lt) {
       const int b = lt & 1, u = lt >> 1;
       ok = mbar_wait(tfull0 + 8 * b, u & 1, a.err, 4);
       tc_fence_after();
-      const TileCoord tc = tile_coord(a, t, BN);
       bool released = false;
-      for (int p = 0; p < NPANEL; ++p, ++pc) {
-        const int sb = pc & 1;
-        if (elected && pc >= 2) bulk_wait_read1();  // staging buffer sb is free again
-        if (epi_bar_or(!ok)) {                         // (A) all threads agree
+      for (int pp = 0; pp < TPANEL; ++pp, ++pc) {
+        const int sub = pp / NPANEL, p = pp - sub * NPANEL;
+        const TileCoord tc = tile_coord(a, t, BN, MS, sub);
+        const int sb = pc % a.nbo;
+        if (elected && pc >= a.nbo) {  // staging buffer sb must be read out first
+          if (a.nbo == 2)
+            bulk_wait_read1();
+          else
+            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        }
+        if (epi_bar_or(!ok)) {  // (A) all threads agree
           ok = false;
           break;
         }
-        if (a.naux > 0) ok = mbar_wait(auxbar, pc & 1, a.err, 7);
+        const int ab = pc % a.nba;
+        if (a.naux > 0) ok = mbar_wait(auxbar0 + 8 * ab, (pc / a.nba) & 1, a.err, 7);
         const uint32_t ob = sOut0 + (sb * a.nout) * PANEL;
+        const uint32_t xb = sAux0 + (ab * a.naux) * PANEL;
 #pragma unroll 1
         for (int jj = 0; jj < 2; ++jj) {
           const int j = 2 * half + jj;  // 16-column chunk of the panel
           float v[16];
-          tmem_ld16(tmem + (uint32_t)(b * BN + 64 * p + 16 * j) + ((uint32_t)(q * 32) << 16), v);
+          tmem_ld16(tmem + (uint32_t)(b * TCOLS + sub * BN + 64 * p + 16 * j) +
+                        ((uint32_t)(q * 32) << 16),
+                    v);
           float x0[16], x1[16], x2[16], r[16], r2[16];
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             uint4 w4;
-            if (a.naux > 0) { lds128(swz(sAux0, row, 2 * j + h), w4); unpack8<T>(w4, x0 + 8 * h); }
-            if (a.naux > 1) { lds128(swz(sAux0 + PANEL, row, 2 * j + h), w4); unpack8<T>(w4, x1 + 8 * h); }
-            if (a.naux > 2) { lds128(swz(sAux0 + 2 * PANEL, row, 2 * j + h), w4); unpack8<T>(w4, x2 + 8 * h); }
+            if (a.naux > 0) { lds128(swz(xb, row, 2 * j + h), w4); unpack8<T>(w4, x0 + 8 * h); }
+            if (a.naux > 1) { lds128(swz(xb + PANEL, row, 2 * j + h), w4); unpack8<T>(w4, x1 + 8 * h); }
+            if (a.naux > 2) { lds128(swz(xb + 2 * PANEL, row, 2 * j + h), w4); unpack8<T>(w4, x2 + 8 * h); }
           }
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
@@ -512,7 +597,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (a.nout > 1) sts128(swz(ob + PANEL, row, 2 * j + h), pack8<T>(r2 + 8 * h));
           }
         }
-        if (p == NPANEL - 1) {  // last read of this accumulator: hand it back to the MMA warp
+        if (pp == TPANEL - 1) {  // last read of this accumulator: hand it back to the MMA warp
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(tempty0 + 8 * b);
@@ -524,22 +609,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           break;
         }
         if (elected) {
-          for (int i = 0; i < a.nout; ++i) epi_tma(true, a, tmO[i], ob + i * PANEL, tc, tc.n0 + 64 * p, 0);
+          for (int i = 0; i < a.nout; ++i)
+            epi_tma(true, a, tmO[i], ob + i * PANEL, tc, tc.n0 + 64 * p, 0);
           bulk_commit();
-          if (a.naux > 0) {  // prefetch the next auxiliary panel (this tile or the next)
-            int nt = t, np = p + 1;
-            if (np == NPANEL) {
-              nt = t + gridDim.x;
-              np = 0;
-            }
-            if (nt < ntiles) {
-              const TileCoord nc = tile_coord(a, nt, BN);
-              mbar_expect_tx(auxbar, (uint32_t)(a.naux * PANEL));
-              for (int i = 0; i < a.naux; ++i)
-                epi_tma(false, a, tmX[i], sAux0 + i * PANEL, nc, nc.n0 + 64 * np, auxbar);
-              ++aux_issued;
-            }
-          }
+          if (a.naux > 0 && aux_issued < npc) aux_load(aux_issued++);  // into buffer ab
         }
       }
       if (!released) {
@@ -550,8 +623,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     if (elected) {
       bulk_wait_all();
-      // on an early exit, let an auxiliary load that is still in flight land
-      if (a.naux > 0 && aux_issued > pc) mbar_wait(auxbar, (aux_issued - 1) & 1, a.err, 8);
+      // on an early exit, let auxiliary loads still in flight land
+      for (int k = pc; k < aux_issued; ++k)
+        mbar_wait(auxbar0 + 8 * (k % a.nba), (k / a.nba) & 1, a.err, 8);
     }
   }
   tc_fence_before();
@@ -559,7 +633,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"((uint32_t)(2 * BN))
+                 "r"((uint32_t)(2 * TCOLS))
                  : "memory");
   }
 }
@@ -604,8 +678,8 @@ bool tc_supported(const ConvArgs& a) {
   return true;
 }
 
-static size_t fixed_smem(int nout, int naux, int stages) {
-  return 1024 + (size_t)(2 * nout + naux) * PANEL + (2 * stages + 6) * 8 + 16;
+static size_t fixed_smem(int nout, int naux, int nbo, int nba, int stages) {
+  return 1024 + (size_t)(nbo * nout + nba * naux) * PANEL + (2 * stages + 9) * 8 + 16;
 }
 
 constexpr size_t kMaxSmem = 227 * 1024;
@@ -657,12 +731,6 @@ TcPlan* tc_plan_create(const ConvArgs& a, int dtype, std::string* err) {
   p->bn = pick_bn(N);
   p->nout = epi_nout(a.epi);
   p->naux = epi_naux(a.epi);
-  // ring depth: what is left of the shared memory after the epilogue staging
-  const size_t stage = (size_t)A_BYTES + (size_t)p->bn * 128;
-  int st = 8;
-  while (st > 2 && fixed_smem(p->nout, p->naux, st) + st * stage > kMaxSmem) --st;
-  p->stages = st;
-  p->smem = fixed_smem(p->nout, p->naux, st) + st * stage;
   // M tile: Ht x Wt pixels of the grid, Wt a power of two
   int wt = 1;
   while (wt < a.W && wt < 128) wt <<= 1;
@@ -673,6 +741,51 @@ TcPlan* tc_plan_create(const ConvArgs& a, int dtype, std::string* err) {
   p->cpt = a.Cin / 64;
   p->nk = a.K() / 64;
   p->tiles_n = N / p->bn;
+  // halo form: 3x3 conv over whole 128-pixel row segments with a resident weight matrix
+  const size_t bres = (size_t)p->nk * p->bn * 128;
+  p->halo = a.mode == CM_CONV3 && p->Wt == 128 && p->Ht == 1 && p->tiles_n == 1 &&
+            bres <= 80 * 1024;
+  // two 128-row sub-tiles share each weight chunk (half the weight traffic per
+  // FLOP) when the accumulators still double-buffer in TMEM and the tiles still
+  // cover the SMs
+  {
+    static int nsm = 0;
+    if (nsm == 0) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      if (nsm <= 0) nsm = 148;
+    }
+    const long long tiles_m = (long long)a.n * p->tiles_h * p->tiles_w;
+    p->ms = (!p->halo && p->bn <= 128 && ((tiles_m + 1) / 2) * p->tiles_n >= nsm) ? 2 : 1;
+  }
+  // shared memory: ring depth and staging buffers, preferring >= 3 ring stages,
+  // then double-buffered staging
+  const size_t stage =
+      p->halo ? (size_t)3 * HALO_BOX : (size_t)p->ms * A_BYTES + (size_t)p->bn * 128;
+  const size_t resident = p->halo ? bres : 0;
+  p->stages = 0;
+  for (int min_st : {3, 2}) {
+    for (int nbuf : {2, 1}) {
+      int st = 8;
+      auto total = [&](int k) {
+        return fixed_smem(p->nout, p->naux, nbuf, nbuf, k) + resident + k * stage;
+      };
+      while (st > min_st && total(st) > kMaxSmem) --st;
+      if (total(st) <= kMaxSmem) {
+        p->stages = st;
+        p->nbo = p->nba = nbuf;
+        p->smem = total(st);
+        break;
+      }
+    }
+    if (p->stages) break;
+  }
+  if (!p->stages) {
+    *err = "tensor-core conv does not fit in shared memory";
+    delete p;
+    return nullptr;
+  }
   {
     static int sms = 0;
     if (sms == 0) {
@@ -681,7 +794,8 @@ TcPlan* tc_plan_create(const ConvArgs& a, int dtype, std::string* err) {
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       if (sms <= 0) sms = 148;
     }
-    const long long tiles = (long long)a.n * p->tiles_h * p->tiles_w * p->tiles_n;
+    const long long tiles_m = (long long)a.n * p->tiles_h * p->tiles_w;
+    const long long tiles = ((tiles_m + p->ms - 1) / p->ms) * p->tiles_n;
     p->grid = dim3((unsigned)std::min<long long>(tiles, sms), 1, 1);
   }
   const CUtensorMapDataType dt =
@@ -699,7 +813,7 @@ TcPlan* tc_plan_create(const ConvArgs& a, int dtype, std::string* err) {
     cuuint64_t dims[4] = {(cuuint64_t)a.Cin, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.n};
     cuuint64_t strides[3] = {(cuuint64_t)a.Cin * 2, (cuuint64_t)a.W * a.Cin * 2,
                              (cuuint64_t)a.H * a.W * a.Cin * 2};
-    cuuint32_t box[4] = {64, (cuuint32_t)p->Wt, (cuuint32_t)p->Ht, 1};
+    cuuint32_t box[4] = {64, (cuuint32_t)(p->halo ? HALO_ROWS : p->Wt), (cuuint32_t)p->Ht, 1};
     ok = encode(enc, &p->tmA, dt, 4, a.in, dims, strides, box);
   }
   {
@@ -725,27 +839,39 @@ TcPlan* tc_plan_create(const ConvArgs& a, int dtype, std::string* err) {
 
 void tc_plan_destroy(TcPlan* p) { delete p; }
 
-template <typename T, int BN>
+template <typename T, int BN, bool HALO, int MS>
 static cudaError_t launch_bn(const TcPlan* p, const TcArgs& ta, cudaStream_t st) {
   static bool attr_set = false;  // per instantiation; set before first launch
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<T, BN>,
+    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<T, BN, HALO, MS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kMaxSmem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  conv_tc_kernel<T, BN><<<p->grid, TC_THREADS, p->smem, st>>>(
+  conv_tc_kernel<T, BN, HALO, MS><<<p->grid, TC_THREADS, p->smem, st>>>(
       p->tmA, p->tmB, p->tmO[0], p->tmO[1], p->tmX[0], p->tmX[1], p->tmX[2], ta);
   return cudaGetLastError();
 }
 
 template <typename T>
 static cudaError_t launch_typed(const TcPlan* p, const TcArgs& t, cudaStream_t st) {
+  if (p->halo) {
+    switch (p->bn) {
+      case 64: return launch_bn<T, 64, true, 1>(p, t, st);
+      default: return launch_bn<T, 128, true, 1>(p, t, st);
+    }
+  }
+  if (p->ms == 2) {
+    switch (p->bn) {
+      case 64: return launch_bn<T, 64, false, 2>(p, t, st);
+      default: return launch_bn<T, 128, false, 2>(p, t, st);
+    }
+  }
   switch (p->bn) {
-    case 64: return launch_bn<T, 64>(p, t, st);
-    case 128: return launch_bn<T, 128>(p, t, st);
-    default: return launch_bn<T, 256>(p, t, st);
+    case 64: return launch_bn<T, 64, false, 1>(p, t, st);
+    case 128: return launch_bn<T, 128, false, 1>(p, t, st);
+    default: return launch_bn<T, 256, false, 1>(p, t, st);
   }
 }
 
@@ -771,6 +897,8 @@ cudaError_t launch_conv_tc(const TcPlan* p, const ConvArgs& a, int* err_flag, cu
   t.stages = p->stages;
   t.nout = p->nout;
   t.naux = p->naux;
+  t.nbo = p->nbo;
+  t.nba = p->nba;
   t.err = err_flag;
   if (p->dt == DT_F16) return launch_typed<__half>(p, t, st);
   return launch_typed<__nv_bfloat16>(p, t, st);

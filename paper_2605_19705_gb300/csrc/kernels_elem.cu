@@ -129,10 +129,115 @@ __global__ void mask_res_kernel(int c, int hw, const uint8_t* __restrict__ m,
   }
 }
 
+// Strip form for the common square kernel sizes: a block computes 64 rows x 32
+// columns; each thread owns a column strip of 8 outputs and, for every kernel
+// column v, slides down the KH + 7 input rows it needs, adding each loaded value
+// to every output of the strip whose kernel row it meets.  The kernel column
+// sits in registers: ~(KH + 7) shared loads per 8 * KH FMAs.
+constexpr int SR = 64, SC = 32, SS = 8;  // rows, columns, strip height
+
+template <int KH>
+__global__ void __launch_bounds__(256) blur_strip_kernel(
+    int c, int H, int W, const float* __restrict__ ker, int flip, const float* __restrict__ in,
+    const float* __restrict__ y, float* __restrict__ out, double* __restrict__ fsum, int epi,
+    float gain) {
+  constexpr int KW = KH;
+  constexpr int TR = SR + KH - 1, TC = SC + KW - 1;
+  __shared__ float sk[KH * KW];
+  __shared__ float st[TR * TC];
+  __shared__ double red[32];
+  const int plane = blockIdx.z;
+  const int b = plane / c;
+  const int i0 = blockIdx.y * SR, j0 = blockIdx.x * SC;
+  const int cy = KH / 2, cx = KW / 2;
+  const int tid = threadIdx.x;
+  const float* kb = ker + (size_t)b * KH * KW;
+  for (int e = tid; e < KH * KW; e += 256) {
+    const int u = e / KW, v = e % KW;
+    sk[e] = flip ? kb[(KH - 1 - u) * KW + (KW - 1 - v)] : kb[e];
+  }
+  const float* pin = in + (size_t)plane * H * W;
+  for (int e = tid; e < TR * TC; e += 256) {
+    const int ti = e / TC, tj = e % TC;
+    int gi = (i0 - cy + ti) % H;
+    if (gi < 0) gi += H;
+    int gj = (j0 - cx + tj) % W;
+    if (gj < 0) gj += W;
+    st[e] = pin[(size_t)gi * W + gj];
+  }
+  __syncthreads();
+  const int col = tid & 31, r0 = (tid >> 5) * SS;
+  float acc[SS];
+#pragma unroll
+  for (int i = 0; i < SS; ++i) acc[i] = 0.f;
+#pragma unroll 1
+  for (int v = 0; v < KW; ++v) {
+    float kv[KH];
+#pragma unroll
+    for (int u = 0; u < KH; ++u) kv[u] = sk[u * KW + v];
+    const float* sp = st + r0 * TC + col + v;
+#pragma unroll
+    for (int R = 0; R < SS + KH - 1; ++R) {
+      const float val = sp[R * TC];
+#pragma unroll
+      for (int i = 0; i < SS; ++i) {
+        const int u = R - i;
+        if (u >= 0 && u < KH) acc[i] = fmaf(kv[u], val, acc[i]);
+      }
+    }
+  }
+  const float tg = (epi >= DE_SAT_RES) ? tanhf(gain) : 1.f;
+  double part = 0.0;
+  const int j = j0 + col;
+#pragma unroll
+  for (int i = 0; i < SS; ++i) {
+    const int r = i0 + r0 + i;
+    if (r >= H || j >= W) continue;
+    const size_t idx = (size_t)plane * H * W + (size_t)r * W + j;
+    const float q = acc[i];
+    float o;
+    if (epi == DE_PLAIN) {
+      o = q;
+    } else if (epi == DE_LIN_RES) {
+      const float e = q - (y ? y[idx] : 0.f);
+      part += 0.5 * (double)e * (double)e;
+      o = e;
+    } else if (epi == DE_SAT_PLAIN) {
+      o = tanhf(gain * q) / tg;
+    } else if (epi == DE_SAT_RES) {
+      const float t = tanhf(gain * q);
+      const float e = t / tg - y[idx];
+      part += 0.5 * (double)e * (double)e;
+      o = (gain / tg) * (1.f - t * t) * e;
+    } else {
+      const float t = tanhf(gain * q);
+      o = (gain / tg) * (1.f - t * t) * y[idx];
+    }
+    out[idx] = o;
+  }
+  if (fsum != nullptr && (epi == DE_LIN_RES || epi == DE_SAT_RES)) {
+    const double s2 = block_sum(part, red);
+    if (tid == 0) atomicAdd(fsum + b, s2);
+  }
+}
+
 static cudaError_t blur_launch(const OpDev& op, int n, int c, int H, int W, int flip,
                                const float* in, const float* y, float* out, double* fsum,
                                int epi, cudaStream_t st) {
   if (op.kh > MAXK || op.kw > MAXK) return cudaErrorInvalidValue;
+  if (op.kh == op.kw && (op.kh == 9 || op.kh == 15 || op.kh == 25)) {
+    dim3 grid((W + SC - 1) / SC, (H + SR - 1) / SR, n * c);
+    if (op.kh == 9)
+      blur_strip_kernel<9><<<grid, 256, 0, st>>>(c, H, W, op.kernel, flip, in, y, out, fsum, epi,
+                                                 op.gain);
+    else if (op.kh == 15)
+      blur_strip_kernel<15><<<grid, 256, 0, st>>>(c, H, W, op.kernel, flip, in, y, out, fsum, epi,
+                                                  op.gain);
+    else
+      blur_strip_kernel<25><<<grid, 256, 0, st>>>(c, H, W, op.kernel, flip, in, y, out, fsum, epi,
+                                                  op.gain);
+    return cudaGetLastError();
+  }
   dim3 grid((W + BT - 1) / BT, (H + BT - 1) / BT, n * c), block(16, 16);
   blur_tile_kernel<<<grid, block, 0, st>>>(c, H, W, op.kh, op.kw, op.kernel, flip, in, y, out,
                                            fsum, epi, op.gain);

@@ -72,6 +72,7 @@ extern "C" ideq_status ideq_red_update_noalloc(int n, int per_img, const float* 
                                                const float* x, float* x_new, float lambda,
                                                float tau, double* step_sq, double* x_sq,
                                                void* stream) {
+  (void)cudaGetLastError();  // clear a stale error an unrelated earlier call may have left
   if (n <= 0 || per_img <= 0 || !z || !grad_f || !grad_g || !x || !x_new) return IDEQ_ERR_ARG;
   const int nblk = update_blocks_per_image(per_img);
   if ((long long)n * nblk * 2 > kNoallocMaxPartials) return IDEQ_ERR_ARG;  // scratch too small

@@ -99,6 +99,9 @@ def test_operator_argument_errors():
     ("C1a", dict(n=2, h=40, w=56), "bf16", 1e-2),
     ("C1a", dict(n=1, h=64, w=64), "fp16", 2e-3),
     ("C1a", dict(n=2, h=40, w=56), "fp16", 2e-3),
+    ("C1a", dict(n=1), "fp16", 2e-3),           # 256^2: halo form of the 64-channel convs
+    ("C1a", dict(n=1), "bf16", 1e-2),
+    ("C1a", dict(n=1, h=136, w=200), "fp16", 2e-3),  # halo tiles with ragged row ends
     ("C3", dict(n=1, h=32, w=32), "fp32", 1e-5),
 ])
 def test_grad_reg_matches_oracle(name, over, prec, tol):
