@@ -30,6 +30,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -190,18 +191,26 @@ IDEQ_DEV void umma_commit(uint32_t bar) {
       : "memory");
 }
 
-IDEQ_DEV void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
+// 32 consecutive f32 accumulator columns of this warp's 32 TMEM lanes (one
+// lane = one row per thread); the wait is in the same statement so that no
+// use of the registers can be scheduled before the data has arrived.
+IDEQ_DEV void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-      "%11, %12, %13, %14, %15}, [%16];"
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31}, [%32];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
 #pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 IDEQ_DEV void mbar_arrive(uint32_t bar) {
@@ -229,24 +238,22 @@ IDEQ_DEV void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;
 IDEQ_DEV void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 IDEQ_DEV void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// Named barrier over the 8 epilogue warps, returning the OR of `v` over them.
-IDEQ_DEV bool epi_bar_or(bool v) {
-  uint32_t r;
-  asm volatile(
-      "{\n\t.reg .pred pi, po;\n\t"
-      "setp.ne.u32 pi, %1, 0;\n\t"
-      "bar.red.or.pred po, 1, 256, pi;\n\t"
-      "selp.u32 %0, 1, 0, po;\n\t}"
-      : "=r"(r)
-      : "r"((uint32_t)v)
-      : "memory");
-  return r != 0;
+// Wait until at most `keep` (0 or 1) of this thread's bulk store groups still
+// read shared memory.
+IDEQ_DEV void bulk_wait_read(int keep) {
+  if (keep > 0)
+    asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+  else
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
-// 16 consecutive 16-bit values of row `row` starting at 16-byte chunk c16 (even)
-// of a 128-byte-swizzled panel
-IDEQ_DEV uint32_t swz(uint32_t panel, int row, int c16) {
-  return panel + row * 128 + (((c16 ^ (row & 7)) & 7) << 4);
+// Byte offset of 16-byte chunk c (0..3) of row `row` in one warp's epilogue
+// box: 32 rows of 64 B under the 64-byte swizzle, i.e. chunk c of row r sits
+// at chunk c ^ ((r >> 1) & 3) (address bits [4,6) XOR bits [7,9)), the layout
+// TMA reads and writes for CU_TENSOR_MAP_SWIZZLE_64B.  The eight rows that one
+// 128-byte shared-memory wavefront serves land in eight distinct bank groups.
+IDEQ_DEV uint32_t wswz(int row, int c) {
+  return (uint32_t)(row * 64 + ((c ^ ((row >> 1) & 3)) << 4));
 }
 
 IDEQ_DEV void lds128(uint32_t a, uint4& v) {
@@ -291,6 +298,80 @@ IDEQ_DEV uint4 pack8(const float* v) {
   return u;
 }
 
+constexpr int WBOX = 32 * 64;  // one warp's epilogue box: 32 rows x 32 16-bit columns
+
+template <int EPI> struct EpiTraits {
+  static constexpr int naux =
+      EPI == EP_DUAL ? 3 : (EPI == EP_ADD || EPI == EP_MUL || EPI == EP_MUL_KEEP) ? 1 : 0;
+  static constexpr bool out2 = EPI == EP_ACT || EPI == EP_MUL_KEEP;
+};
+
+// One value of the fused epilogue, the kind fixed at compile time (see Epi).
+// softplus and its derivative share one exponential:
+//   e = exp(-|v|), softplus(v) = max(v, 0) + log(1 + e),
+//   logistic(v) = 1 / (1 + e) for v >= 0 and e / (1 + e) for v < 0.
+template <int EPI, int ACT>
+IDEQ_DEV float epi_one(float v, float x0, float x1, float x2, float& o2) {
+  if (EPI == EP_ACT) {
+    if (ACT == 0) {
+      const float e = __expf(-fabsf(v));
+      const float d = 1.f + e;
+      const float rd = __fdividef(1.f, d);
+      o2 = v >= 0.f ? rd : e * rd;
+      return fmaxf(v, 0.f) + __logf(d);
+    }
+    o2 = v > 0.f ? 1.f : 0.f;
+    return fmaxf(v, 0.f);
+  }
+  if (EPI == EP_ADD) return v + x0;
+  if (EPI == EP_MUL) return v * x0;
+  if (EPI == EP_MUL_KEEP) {
+    o2 = v;
+    return v * x0;
+  }
+  if (EPI == EP_DUAL) return x0 * v + x0 * (1.f - x0) * x1 * x2;
+  return v;
+}
+
+// Epilogue of one warp's 32 columns of one row per thread: auxiliary values
+// from the warp's staged boxes at xb (one box per input), results into the
+// staging boxes at ob (the second output one box further).
+template <typename T, int EPI, int ACT>
+IDEQ_DEV void epi_chunk(const float (&v)[32], uint32_t xb, uint32_t ob, int row) {
+  using Tr = EpiTraits<EPI>;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const uint32_t off = wswz(row, c);
+    float x0[8] = {}, x1[8] = {}, x2[8] = {}, r[8], r2[8] = {};
+    uint4 w4;
+    if (Tr::naux > 0) { lds128(xb + off, w4); unpack8<T>(w4, x0); }
+    if (Tr::naux > 1) { lds128(xb + WBOX + off, w4); unpack8<T>(w4, x1); }
+    if (Tr::naux > 2) { lds128(xb + 2 * WBOX + off, w4); unpack8<T>(w4, x2); }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) r[i] = epi_one<EPI, ACT>(v[8 * c + i], x0[i], x1[i], x2[i], r2[i]);
+    sts128(ob + off, pack8<T>(r));
+    if (Tr::out2) sts128(ob + WBOX + off, pack8<T>(r2));
+  }
+}
+
+template <typename T>
+IDEQ_DEV void epi_apply(int epi, int act, const float (&v)[32], uint32_t xb, uint32_t ob,
+                        int row) {
+  switch (epi) {
+    case EP_ACT:
+      if (act == 0)
+        epi_chunk<T, EP_ACT, 0>(v, xb, ob, row);
+      else
+        epi_chunk<T, EP_ACT, 1>(v, xb, ob, row);
+      break;
+    case EP_ADD: epi_chunk<T, EP_ADD, 0>(v, xb, ob, row); break;
+    case EP_MUL: epi_chunk<T, EP_MUL, 0>(v, xb, ob, row); break;
+    case EP_MUL_KEEP: epi_chunk<T, EP_MUL_KEEP, 0>(v, xb, ob, row); break;
+    case EP_DUAL: epi_chunk<T, EP_DUAL, 0>(v, xb, ob, row); break;
+    default: epi_chunk<T, EP_STORE, 0>(v, xb, ob, row); break;
+  }
+}
+
 struct TileCoord {
   int img, h0, w0, n0;
 };
@@ -315,24 +396,28 @@ IDEQ_DEV TileCoord tile_coord(const TcArgs& a, int t, int bn, int ms, int sub) {
 constexpr int EPI_WARPS = 8;
 constexpr int TC_THREADS = 64 + 32 * EPI_WARPS;
 constexpr int A_BYTES = 128 * 128;  // 128 pixel rows x 64 16-bit channels
-constexpr int PANEL = 128 * 128;    // 128 rows x 64 columns of 16-bit results
+constexpr int PANEL = EPI_WARPS * WBOX;  // one staging buffer of one tensor, all 8 warps
 
-// Epilogue TMA (load of auxiliary panels, store of result panels): 4-D NHWC
-// boxes (64 channels x Wt x Ht), or the 5-D depth-to-space view for OM_D2S.
+// Epilogue TMA of one warp's box (load of auxiliary values, store of results):
+// the 32 tile rows 32q .. 32q+31 (q = the warp's TMEM lane quadrant) and the 32
+// columns starting at `col`, as a 4-D NHWC box (32 channels x min(Wt, 32) x
+// 32 / min(Wt, 32) pixels), or through the 5-D depth-to-space view for OM_D2S.
 IDEQ_DEV void epi_tma(bool store, const TcArgs& a, const CUtensorMap* tm, uint32_t sm,
-                      const TileCoord& tc, int col, uint32_t bar) {
+                      const TileCoord& tc, int q, int col, uint32_t bar) {
+  const int m0 = 32 * q;
+  const int w = tc.w0 + m0 % a.Wt, h = tc.h0 + m0 / a.Wt;
   if (a.outmap == OM_D2S) {
-    const int q = col / a.Cout, co = col - q * a.Cout;
-    const int c0 = (q & 1) * a.Cout + co, di = q >> 1;
+    const int sp = col / a.Cout, co = col - sp * a.Cout;
+    const int c0 = (sp & 1) * a.Cout + co, di = sp >> 1;
     if (store)
-      tma_store_5d(tm, sm, c0, tc.w0, di, tc.h0, tc.img);
+      tma_store_5d(tm, sm, c0, w, di, h, tc.img);
     else
-      tma_load_5d(sm, tm, c0, tc.w0, di, tc.h0, tc.img, bar);
+      tma_load_5d(sm, tm, c0, w, di, h, tc.img, bar);
   } else {
     if (store)
-      tma_store_4d(tm, sm, col, tc.w0, tc.h0, tc.img);
+      tma_store_4d(tm, sm, col, w, h, tc.img);
     else
-      tma_load_4d(sm, tm, col, tc.w0, tc.h0, tc.img, bar);
+      tma_load_4d(sm, tm, col, w, h, tc.img, bar);
   }
 }
 
@@ -365,18 +450,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
   uint8_t* sB = smem + ST * A_STAGE;  // ring slots, or the resident weights (HALO)
-  uint8_t* sOut = sB + (HALO ? a.nk * B_BYTES : ST * B_BYTES);  // [nbo][nout][PANEL]
-  uint8_t* sAux = sOut + a.nbo * a.nout * PANEL;                 // [nba][naux][PANEL]
+  uint8_t* sOut = sB + (HALO ? a.nk * B_BYTES : ST * B_BYTES);  // [warp][nbo][nout][WBOX]
+  uint8_t* sAux = sOut + a.nbo * a.nout * PANEL;                 // [warp][nba][naux][WBOX]
   uint64_t* bars = (uint64_t*)(sAux + a.nba * a.naux * PANEL);
-  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * ST + 9);
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * ST + 6 + 2 * EPI_WARPS);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + ST);
   const uint32_t tfull0 = smem_u32(bars + 2 * ST);
   const uint32_t tempty0 = smem_u32(bars + 2 * ST + 2);
   const uint32_t drain = smem_u32(bars + 2 * ST + 4);
-  const uint32_t auxbar0 = smem_u32(bars + 2 * ST + 5);  // [2]
-  const uint32_t bres = smem_u32(bars + 2 * ST + 7);
+  const uint32_t bres = smem_u32(bars + 2 * ST + 5);
+  const uint32_t auxbar0 = smem_u32(bars + 2 * ST + 6);  // [warp][2]
   const int ntiles = ((a.n * a.tiles_h * a.tiles_w + MS - 1) / MS) * a.tiles_n;
   const int nsteps = HALO ? a.cpt : a.nk;  // ring stages per tile
 
@@ -388,8 +473,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull0 + 8 * b, 1);
       mbar_init(tempty0 + 8 * b, EPI_WARPS);
-      mbar_init(auxbar0 + 8 * b, 1);
     }
+    for (int b = 0; b < 2 * EPI_WARPS; ++b) mbar_init(auxbar0 + 8 * b, 1);
     mbar_init(drain, 1);
     mbar_init(bres, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -522,111 +607,78 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
     }
   } else {
-    // ---------------- epilogue warps 2..9
-    const int q = warp & 3, half = (warp - 2) >> 2;
-    const int row = q * 32 + lane;
-    const bool elected = warp == 2 && lane == 0;
+    // ---------------- epilogue warps 2..9, each on its own: warp e owns TMEM
+    // lanes (rows) 32q .. 32q+31 (q = warp % 4, the quadrant it may read) and
+    // columns 32h .. 32h+31 (h = e / 4) of every 64-column panel, with its own
+    // staging boxes, auxiliary barriers and bulk store groups.
+    const int e = warp - 2, q = warp & 3, half = e >> 2;
     const CUtensorMap* tmO[2] = {&tmO0, &tmO1};
     const CUtensorMap* tmX[3] = {&tmX0, &tmX1, &tmX2};
-    const uint32_t sOut0 = smem_u32(sOut), sAux0 = smem_u32(sAux);
+    const uint32_t sO = smem_u32(sOut) + (uint32_t)(e * a.nbo * a.nout * WBOX);
+    const uint32_t sX = smem_u32(sAux) + (uint32_t)(e * a.nba * a.naux * WBOX);
+    const uint32_t xbar = auxbar0 + 16 * e;
     constexpr int TPANEL = MS * NPANEL;  // panels per tile
     const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const int npc = my_tiles * TPANEL;  // panels this CTA processes
-    // auxiliary panel k of this CTA -> buffer k % nba, loaded ahead by the elected thread
+    // auxiliary box of panel k -> buffer k % nba, loaded ahead by lane 0
     auto aux_load = [&](int k) {
       const int i = k / TPANEL, r = k - i * TPANEL, sub = r / NPANEL, p = r - sub * NPANEL;
       const TileCoord nc = tile_coord(a, blockIdx.x + i * gridDim.x, BN, MS, sub);
       const int buf = k % a.nba;
-      const uint32_t bar = auxbar0 + 8 * buf;
-      mbar_expect_tx(bar, (uint32_t)(a.naux * PANEL));
+      const uint32_t bar = xbar + 8 * buf;
+      mbar_expect_tx(bar, (uint32_t)(a.naux * WBOX));
       for (int x = 0; x < a.naux; ++x)
-        epi_tma(false, a, tmX[x], sAux0 + (buf * a.naux + x) * PANEL, nc, nc.n0 + 64 * p, bar);
+        epi_tma(false, a, tmX[x], sX + (uint32_t)((buf * a.naux + x) * WBOX), nc, q,
+                nc.n0 + 64 * p + 32 * half, bar);
     };
     int aux_issued = 0;
-    if (elected && a.naux > 0)
+    if (lane == 0 && a.naux > 0)
       for (; aux_issued < a.nba && aux_issued < npc; ++aux_issued) aux_load(aux_issued);
     int lt = 0, pc = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++lt) {
       const int b = lt & 1, u = lt >> 1;
-      ok = mbar_wait(tfull0 + 8 * b, u & 1, a.err, 4);
+      ok = __all_sync(0xffffffffu, mbar_wait(tfull0 + 8 * b, u & 1, a.err, 4));
       tc_fence_after();
-      bool released = false;
-      for (int pp = 0; pp < TPANEL; ++pp, ++pc) {
+      for (int pp = 0; pp < TPANEL && ok; ++pp, ++pc) {
         const int sub = pp / NPANEL, p = pp - sub * NPANEL;
-        const TileCoord tc = tile_coord(a, t, BN, MS, sub);
-        const int sb = pc % a.nbo;
-        if (elected && pc >= a.nbo) {  // staging buffer sb must be read out first
-          if (a.nbo == 2)
-            bulk_wait_read1();
-          else
-            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        const int sb = pc % a.nbo, ab = pc % a.nba;
+        if (lane == 0 && pc >= a.nbo) bulk_wait_read(a.nbo - 1);  // staging box sb read out
+        __syncwarp();
+        if (a.naux > 0) {
+          ok = __all_sync(0xffffffffu, mbar_wait(xbar + 8 * ab, (pc / a.nba) & 1, a.err, 7));
+          if (!ok) break;
         }
-        if (epi_bar_or(!ok)) {  // (A) all threads agree
-          ok = false;
-          break;
-        }
-        const int ab = pc % a.nba;
-        if (a.naux > 0) ok = mbar_wait(auxbar0 + 8 * ab, (pc / a.nba) & 1, a.err, 7);
-        const uint32_t ob = sOut0 + (sb * a.nout) * PANEL;
-        const uint32_t xb = sAux0 + (ab * a.naux) * PANEL;
-#pragma unroll 1
-        for (int jj = 0; jj < 2; ++jj) {
-          const int j = 2 * half + jj;  // 16-column chunk of the panel
-          float v[16];
-          tmem_ld16(tmem + (uint32_t)(b * TCOLS + sub * BN + 64 * p + 16 * j) +
-                        ((uint32_t)(q * 32) << 16),
-                    v);
-          float x0[16], x1[16], x2[16], r[16], r2[16];
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            uint4 w4;
-            if (a.naux > 0) { lds128(swz(xb, row, 2 * j + h), w4); unpack8<T>(w4, x0 + 8 * h); }
-            if (a.naux > 1) { lds128(swz(xb + PANEL, row, 2 * j + h), w4); unpack8<T>(w4, x1 + 8 * h); }
-            if (a.naux > 2) { lds128(swz(xb + 2 * PANEL, row, 2 * j + h), w4); unpack8<T>(w4, x2 + 8 * h); }
-          }
-#pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            r2[i] = 0.f;
-            r[i] = epi_math(a.epi, a.act, v[i], a.naux > 0 ? x0[i] : 0.f,
-                            a.naux > 1 ? x1[i] : 0.f, a.naux > 2 ? x2[i] : 0.f, &r2[i]);
-          }
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            sts128(swz(ob, row, 2 * j + h), pack8<T>(r + 8 * h));
-            if (a.nout > 1) sts128(swz(ob + PANEL, row, 2 * j + h), pack8<T>(r2 + 8 * h));
-          }
-        }
-        if (pp == TPANEL - 1) {  // last read of this accumulator: hand it back to the MMA warp
+        float v[32];
+        tmem_ld32(tmem + (uint32_t)(b * TCOLS + sub * BN + 64 * p + 32 * half) +
+                      ((uint32_t)(q * 32) << 16),
+                  v);
+        if (pp == TPANEL - 1) {  // last read of this accumulator: hand it back
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(tempty0 + 8 * b);
-          released = true;
         }
+        const uint32_t ob = sO + (uint32_t)(sb * a.nout * WBOX);
+        epi_apply<T>(a.epi, a.act, v, sX + (uint32_t)(ab * a.naux * WBOX), ob, lane);
         fence_async_smem();
-        if (epi_bar_or(!ok)) {  // (B) staging written, auxiliary panel consumed
-          ok = false;
-          break;
-        }
-        if (elected) {
+        __syncwarp();
+        if (lane == 0) {
+          const TileCoord tc = tile_coord(a, t, BN, MS, sub);
           for (int i = 0; i < a.nout; ++i)
-            epi_tma(true, a, tmO[i], ob + i * PANEL, tc, tc.n0 + 64 * p, 0);
+            epi_tma(true, a, tmO[i], ob + (uint32_t)(i * WBOX), tc, q,
+                    tc.n0 + 64 * p + 32 * half, 0);
           bulk_commit();
           if (a.naux > 0 && aux_issued < npc) aux_load(aux_issued++);  // into buffer ab
         }
       }
-      if (!released) {
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(tempty0 + 8 * b);
-      }
     }
-    if (elected) {
+    if (lane == 0) {
       bulk_wait_all();
       // on an early exit, let auxiliary loads still in flight land
       for (int k = pc; k < aux_issued; ++k)
-        mbar_wait(auxbar0 + 8 * (k % a.nba), (k / a.nba) & 1, a.err, 8);
+        mbar_wait(xbar + 8 * (k % a.nba), (k / a.nba) & 1, a.err, 8);
     }
+    __syncwarp();
   }
   tc_fence_before();
   __syncthreads();
@@ -654,8 +706,11 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   return fn;
 }
 
+static int tiling_override(const char* name, int dflt);
+
 static int pick_bn(int N) {
-  if (N % 256 == 0 && N >= 512) return 256;
+  const int n256 = tiling_override("IDEQ_TC_BN256_MIN", 512);  // smallest N tiled 256 wide
+  if (N % 256 == 0 && N >= n256) return 256;
   if (N % 128 == 0) return 128;
   return 64;
 }
@@ -679,36 +734,46 @@ bool tc_supported(const ConvArgs& a) {
 }
 
 static size_t fixed_smem(int nout, int naux, int nbo, int nba, int stages) {
-  return 1024 + (size_t)(nbo * nout + nba * naux) * PANEL + (2 * stages + 9) * 8 + 16;
+  return 1024 + (size_t)(nbo * nout + nba * naux) * PANEL + (2 * stages + 6 + 2 * EPI_WARPS) * 8 + 16;
 }
 
 constexpr size_t kMaxSmem = 227 * 1024;
 
 static bool encode(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap* m, CUtensorMapDataType dt,
                    int rank, const void* base, const cuuint64_t* dims, const cuuint64_t* strides,
-                   const cuuint32_t* box) {
+                   const cuuint32_t* box,
+                   CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B) {
   cuuint32_t es[5] = {1, 1, 1, 1, 1};
   return enc(m, dt, rank, const_cast<void*>(base), dims, strides, box, es,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// map of an epilogue tensor (output or auxiliary, both shaped like the output)
+// map of an epilogue tensor (output or auxiliary, both shaped like the output),
+// boxed as one epilogue warp's 32 rows x 32 channels, 64-byte swizzle
 static bool encode_epi(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap* m,
                        CUtensorMapDataType dt, const ConvArgs& a, const TcPlan* p,
                        const void* base) {
   const cuuint64_t C = (cuuint64_t)a.Cout;
+  const cuuint32_t bw = (cuuint32_t)std::min(p->Wt, 32), bh = 32 / bw;
   if (a.outmap == OM_D2S) {  // output image 2H x 2W viewed as [n][H][di][W][dj*C + co]
     const cuuint64_t W2 = 2 * (cuuint64_t)a.W;
     cuuint64_t dims[5] = {2 * C, (cuuint64_t)a.W, 2, (cuuint64_t)a.H, (cuuint64_t)a.n};
     cuuint64_t strides[4] = {2 * C * 2, W2 * C * 2, 2 * W2 * C * 2, 2 * (cuuint64_t)a.H * 2 * W2 * C};
-    cuuint32_t box[5] = {64, (cuuint32_t)p->Wt, 1, (cuuint32_t)p->Ht, 1};
-    return encode(enc, m, dt, 5, base, dims, strides, box);
+    cuuint32_t box[5] = {32, bw, 1, bh, 1};
+    return encode(enc, m, dt, 5, base, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_64B);
   }
   cuuint64_t dims[4] = {C, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.n};
   cuuint64_t strides[3] = {C * 2, (cuuint64_t)a.W * C * 2, (cuuint64_t)a.H * a.W * C * 2};
-  cuuint32_t box[4] = {64, (cuuint32_t)p->Wt, (cuuint32_t)p->Ht, 1};
-  return encode(enc, m, dt, 4, base, dims, strides, box);
+  cuuint32_t box[4] = {32, bw, bh, 1};
+  return encode(enc, m, dt, 4, base, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_64B);
+}
+
+// Integer tuning override from the environment (read at plan creation), used to
+// compare tilings on a given GPU without rebuilding; `dflt` when unset.
+static int tiling_override(const char* name, int dflt) {
+  const char* v = std::getenv(name);
+  return (v && *v) ? std::atoi(v) : dflt;
 }
 
 TcPlan* tc_plan_create(const ConvArgs& a, int dtype, std::string* err) {
@@ -744,20 +809,14 @@ TcPlan* tc_plan_create(const ConvArgs& a, int dtype, std::string* err) {
   // halo form: 3x3 conv over whole 128-pixel row segments with a resident weight matrix
   const size_t bres = (size_t)p->nk * p->bn * 128;
   p->halo = a.mode == CM_CONV3 && p->Wt == 128 && p->Ht == 1 && p->tiles_n == 1 &&
-            bres <= 80 * 1024;
-  // two 128-row sub-tiles share each weight chunk (half the weight traffic per
-  // FLOP) when the accumulators still double-buffer in TMEM and the tiles still
-  // cover the SMs
+            bres <= 80 * 1024 && tiling_override("IDEQ_TC_HALO", 1) != 0;
+  // Two 128-row sub-tiles can share each weight chunk (half the weight traffic
+  // per FLOP), but measured on the U-Net layers the coarser tiles balance worse
+  // over the SMs than they save, so M = 256 is used only when forced.
+  p->ms = 1;
   {
-    static int nsm = 0;
-    if (nsm == 0) {
-      int dev = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-      if (nsm <= 0) nsm = 148;
-    }
-    const long long tiles_m = (long long)a.n * p->tiles_h * p->tiles_w;
-    p->ms = (!p->halo && p->bn <= 128 && ((tiles_m + 1) / 2) * p->tiles_n >= nsm) ? 2 : 1;
+    const int force_ms = tiling_override("IDEQ_TC_MS", 0);  // 2 forces two sub-tiles
+    if (!p->halo && p->bn <= 128 && force_ms == 2) p->ms = 2;
   }
   // shared memory: ring depth and staging buffers, preferring >= 3 ring stages,
   // then double-buffered staging
