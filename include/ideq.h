@@ -53,10 +53,13 @@ enum { IDEQ_ACT_SOFTPLUS = 0, IDEQ_ACT_RELU = 1 };
 enum { IDEQ_OP_BLUR = 0, IDEQ_OP_MASK = 1, IDEQ_OP_SATBLUR = 2 };
 /* Arithmetic of the regulariser network's convolutions: operands in FP32
  * (SIMT), BF16 or FP16 (tensor cores, FP32 accumulation), activations stored in
- * the operand type.  The iterate, the momentum state and the data step are
- * always float32, the step-norm and energy reductions float64.  IDEQ_BF16_FP8
- * is reserved. */
-enum { IDEQ_FP32 = 0, IDEQ_BF16 = 1, IDEQ_BF16_FP8 = 2, IDEQ_FP16 = 3 };
+ * the operand type.  The _FP8 forms run the tensor-core convolutions whose
+ * input has >= 256 channels with FP8 e4m3 operands instead (per-output-channel
+ * weight scales, a per-tensor activation scale taken from the input's max |x|
+ * at every call, FP32 accumulation, 16-bit output); the implicit backward and
+ * the warm start use the 16-bit form.  The iterate, the momentum state and the
+ * data step are always float32, the step-norm and energy reductions float64. */
+enum { IDEQ_FP32 = 0, IDEQ_BF16 = 1, IDEQ_BF16_FP8 = 2, IDEQ_FP16 = 3, IDEQ_FP16_FP8 = 4 };
 enum { IDEQ_INIT_ATY = 0, IDEQ_INIT_X0 = 1, IDEQ_INIT_WARM = 2 };
 enum { IDEQ_ADJ_JFB = 0, IDEQ_ADJ_IMPLICIT = 1 };
 
@@ -103,12 +106,18 @@ typedef struct {
  * Eq. Momentum).  restart_B <= 0 or non-finite disables the restart test of
  * Eq. restart.  tol > 0 stops an image once ||x^{k+1}-x^k|| < tol ||x^k||
  * (App. D.1.3); tol = 0 runs exactly max_iter updates.  The output is the
- * last iterate (Remark 1). */
+ * last iterate (Remark 1), or, with average = 1, the averaging step of
+ * Algorithm 1: x_hat = (1/(K0+1)) sum_{k=0}^{K0} z^k, where K0 is the first
+ * minimiser of ||x^{k+1}-x^k|| over floor(K/2) < k < K-1 and K = max_iter.
+ * Averaging needs a fixed run -- tol = 0, no restart, max_iter >= 5 -- and is
+ * otherwise an argument error; ideq_step ignores it.  An image that diverged
+ * returns its last iterate. */
 typedef struct {
   float lambda, tau, beta, restart_B;
   double tol;
   int max_iter;
   int init;               /* IDEQ_INIT_ATY, IDEQ_INIT_X0 (x0 given) or IDEQ_INIT_WARM */
+  int average;            /* 0: last iterate; 1: averaging step (ideq_solve)         */
 } ideq_params;
 
 /* Per-image results, device arrays of length n; any member may be NULL. */
@@ -118,6 +127,7 @@ typedef struct {
   int *status;      /* IDEQ_IMG_*                                            */
   double *rel_res;  /* last ||x^{k+1}-x^k|| / ||x^k||                          */
   double *energy;   /* F(z) = f(z) + lambda g(z) at the last extrapolated point */
+  int *k0;          /* K0 of the averaging step; -1 when no averaging was applied */
 } ideq_info;
 
 /* Adjoint (backward) solve parameters (App. D.1.2).  IDEQ_ADJ_JFB uses the

@@ -15,7 +15,10 @@ with beta = 1 - alpha.  Readings where the paper is silent or loose:
   * stopping (App. D.1.3): ||x^{k+1} - x^k|| / ||x^k|| < tol after an update;
     the image is then frozen at x^{k+1}; tol = 0 runs exactly max_iter updates;
   * the output is the last iterate, x_hat = x^K (Remark 1 allows dropping the
-    averaging step);
+    averaging step); with average=True it is the averaging step of Algorithm 1,
+    x_hat = (1 / (K0 + 1)) sum_{k=0}^{K0} z^k with K0 the first minimiser of
+    ||x^{k+1} - x^k|| over floor(K/2) < k < K - 1, for a run of exactly K =
+    max_iter updates without restarts (tol = 0, B = inf), K >= 5;
   * a non-finite step norm marks the image diverged and freezes it.
 Alpha = 1 (beta = 0) is RED, i.e. gradient descent on F = f + lambda g (Sec. 2.1).
 """
@@ -38,9 +41,23 @@ def red_step(net, op, y, z, lam, tau):
     return z - tau * (gf + lam * gg), fval, gval
 
 
+def averaging_step(zs, steps):
+    """Averaging step of Algorithm 1 for a run of K = len(steps) updates:
+    K0 = argmin_{floor(K/2) < k < K-1} ||x^{k+1} - x^k|| (first minimiser) and
+    x_hat = (1 / (K0 + 1)) sum_{k=0}^{K0} z^k.  zs[k] = z^k, steps[k] = ||x^{k+1} - x^k||."""
+    K = len(steps)
+    window = range(K // 2 + 1, K - 1)
+    if len(window) == 0:
+        raise ValueError("the averaging window floor(K/2) < k < K-1 is empty (K < 5)")
+    K0 = min(window, key=lambda k: steps[k])
+    return np.mean(np.stack(zs[:K0 + 1]), axis=0), K0
+
+
 def solve_image(net, op, y, x0, lam, tau, beta, B=math.inf, tol=0.0, max_iter=50,
-                keep_history=False):
+                keep_history=False, average=False):
     """Run the iteration on one image.  Returns (x_hat, info dict)."""
+    if average and (tol > 0.0 or B < math.inf):
+        raise ValueError("the averaging step needs a fixed run: tol = 0 and no restart")
     x = np.asarray(x0, dtype=np.float64).copy()
     x_prev = x.copy()
     k, S, total, restarts = 0, 0.0, 0, 0
@@ -48,10 +65,14 @@ def solve_image(net, op, y, x0, lam, tau, beta, B=math.inf, tol=0.0, max_iter=50
     info = {"steps": [], "rel": [], "energy_hist": []}
     fval = gval = float("nan")
     rel = float("nan")
+    zs, norms = [], []
     while total < max_iter:
         z = x + beta * (x - x_prev)
         x_new, fval, gval = red_step(net, op, y, z, lam, tau)
         s = float(np.sum((x_new - x) ** 2))
+        if average:
+            zs.append(z)
+            norms.append(math.sqrt(s))
         nx = float(np.sum(x * x))
         x_prev, x = x, x_new
         k += 1
@@ -74,16 +95,20 @@ def solve_image(net, op, y, x0, lam, tau, beta, B=math.inf, tol=0.0, max_iter=50
             restarts += 1
     info.update(iters=total, restarts=restarts, status=status, rel_res=rel,
                 f=fval, g=gval, energy=fval + lam * gval, x_prev=x_prev)
+    if average and status == MAXITER:
+        x, info["K0"] = averaging_step(zs, norms)
+        if keep_history:
+            info["z_hist"], info["step_hist"] = zs, norms
     return x, info
 
 
 def solve_batch(net, ops, ys, x0s, lam, tau, beta, B=math.inf, tol=0.0, max_iter=50,
-                keep_history=False):
+                keep_history=False, average=False):
     """Independent solves of a batch (images never interact)."""
     xs, infos = [], []
     for i in range(len(ops)):
         x, inf = solve_image(net, ops[i], ys[i], x0s[i], lam, tau, beta, B, tol, max_iter,
-                             keep_history)
+                             keep_history, average)
         xs.append(x)
         infos.append(inf)
     return np.stack(xs), infos

@@ -28,7 +28,7 @@ IDEQ_IMG_RUNNING, IDEQ_IMG_CONVERGED, IDEQ_IMG_MAXITER, IDEQ_IMG_DIVERGED = 0, 1
 IDEQ_NET_CNN, IDEQ_NET_UNET = 0, 1
 IDEQ_ACT_SOFTPLUS, IDEQ_ACT_RELU = 0, 1
 IDEQ_OP_BLUR, IDEQ_OP_MASK, IDEQ_OP_SATBLUR = 0, 1, 2
-IDEQ_FP32, IDEQ_BF16, IDEQ_BF16_FP8, IDEQ_FP16 = 0, 1, 2, 3
+IDEQ_FP32, IDEQ_BF16, IDEQ_BF16_FP8, IDEQ_FP16, IDEQ_FP16_FP8 = 0, 1, 2, 3, 4
 IDEQ_INIT_ATY, IDEQ_INIT_X0, IDEQ_INIT_WARM = 0, 1, 2
 IDEQ_ADJ_JFB, IDEQ_ADJ_IMPLICIT = 0, 1
 
@@ -49,12 +49,12 @@ class Operator(ctypes.Structure):
 
 class Params(ctypes.Structure):
     _fields_ = [("lam", c_float), ("tau", c_float), ("beta", c_float), ("restart_B", c_float),
-                ("tol", c_double), ("max_iter", c_int), ("init", c_int)]
+                ("tol", c_double), ("max_iter", c_int), ("init", c_int), ("average", c_int)]
 
 
 class Info(ctypes.Structure):
     _fields_ = [("iters", c_void_p), ("restarts", c_void_p), ("status", c_void_p),
-                ("rel_res", c_void_p), ("energy", c_void_p)]
+                ("rel_res", c_void_p), ("energy", c_void_p), ("k0", c_void_p)]
 
 
 class AdjParams(ctypes.Structure):
@@ -231,10 +231,11 @@ def ideq_grad_reg(ctx: Context, z, grad=None, g_val=None):
     return grad
 
 
-def make_params(lam, tau, beta, B=float("inf"), tol=0.0, max_iter=50, init=IDEQ_INIT_ATY):
+def make_params(lam, tau, beta, B=float("inf"), tol=0.0, max_iter=50, init=IDEQ_INIT_ATY,
+                average=False):
     p = Params()
     p.lam, p.tau, p.beta, p.restart_B = lam, tau, beta, (B if B != float("inf") else 0.0)
-    p.tol, p.max_iter, p.init = tol, max_iter, init
+    p.tol, p.max_iter, p.init, p.average = tol, max_iter, init, 1 if average else 0
     return p
 
 
@@ -248,8 +249,9 @@ class InfoBuffers:
         self.status = torch.zeros(n, dtype=torch.int32, device=device)
         self.rel_res = torch.zeros(n, dtype=torch.float64, device=device)
         self.energy = torch.zeros(n, dtype=torch.float64, device=device)
+        self.k0 = torch.zeros(n, dtype=torch.int32, device=device)
         self.s = Info(self.iters.data_ptr(), self.restarts.data_ptr(), self.status.data_ptr(),
-                      self.rel_res.data_ptr(), self.energy.data_ptr())
+                      self.rel_res.data_ptr(), self.energy.data_ptr(), self.k0.data_ptr())
 
 
 def ideq_step(ctx: Context, op: Operator, y, x_k, x_km1, params: Params, info=None):

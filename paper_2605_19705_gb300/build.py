@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libideq.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "net.cu", "kernels_elem.cu", "conv_simt.cu", "conv_tc.cu", "conv_edge.cu", "wgrad.cu",
+SOURCES = ["api.cu", "net.cu", "kernels_elem.cu", "conv_simt.cu", "conv_tc.cu", "conv_edge.cu",
+           "conv_edge_rb.cu", "wgrad.cu",
            "net_train.cu", "noalloc.cu"]
 
 

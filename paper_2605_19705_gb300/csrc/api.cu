@@ -119,7 +119,8 @@ ideq_status ensure_plan(ideq_ctx* ctx, const ideq_shape& s) {
     return o;
   };
   const size_t o_x0 = take(img), o_x1 = take(img), o_gf = take(img), o_tmp = take(img);
-  const size_t o_i = take((size_t)n * 4 * 6), o_f = take((size_t)n * 4), o_d = take((size_t)n * 8 * 6);
+  const size_t o_i = take((size_t)n * 4 * 8), o_f = take((size_t)n * 4), o_d = take((size_t)n * 8 * 6);
+  const size_t o_zs = take(2 * img), o_zn = take(2 * img);  // FP64 sums of the averaging step
   const size_t o_p = take((size_t)n * nblk * 8 * 2), o_r = take(16), o_dp = take(128 * 8);
   const size_t o_u = take(img);
   char* m = nullptr;
@@ -143,6 +144,11 @@ ideq_status ensure_plan(ideq_ctx* ctx, const ideq_shape& s) {
   v.fsum = dp + 2 * n;
   v.gsum = dp + 3 * n;
   v.energy = dp + 4 * n;
+  v.best = dp + 5 * n;
+  v.k0 = ip + 5 * n;
+  v.snap = ip + 6 * n;
+  v.zsum = (double*)(m + o_zs);
+  v.zsnap = (double*)(m + o_zn);
   v.part_s = (double*)(m + o_p);
   v.part_x = v.part_s + (size_t)n * nblk;
   v.n_running = (int*)(m + o_r);
@@ -198,13 +204,17 @@ cudaError_t back_project(ideq_ctx* ctx, const OpDev& od, const ideq_shape& s, co
 // One iteration of Algorithm 1 on the plan buffers: x in xb[p], x_prev in
 // xb[1-p]; the update is written into xb[1-p].
 ideq_status iterate(ideq_ctx* ctx, const OpDev& od, const ideq_shape& s, const float* y,
-                    const ideq_params* p, int par, int logic) {
+                    const ideq_params* p, int par, int logic, bool average = false) {
   NetPlan* P = ctx->plan.get();
   cudaStream_t st = ctx->stream;
   const int n = s.n, per = ctx->sv_per;
   float* x = ctx->xb[par];
   float* xp = ctx->xb[1 - par];
-  CK(launch_extrapolate(n, per, x, xp, ctx->sv.beta_eff, P->z, st));
+  const int avg_K = (logic && average) ? p->max_iter : 0;
+  if (avg_K > 0)
+    CK(launch_extrapolate_avg(n, per, x, xp, ctx->sv, P->z, st));
+  else
+    CK(launch_extrapolate(n, per, x, xp, ctx->sv.beta_eff, P->z, st));
   CK(run_steps(P->fwd, ctx->d_err, st, &ctx->prof, &ctx->launches));
   CK(run_steps(P->vjp, ctx->d_err, st, &ctx->prof, &ctx->launches));
   CK(data_grad(ctx, od, s, P->z, y, ctx->gf, ctx->tmp, ctx->sv.fsum));
@@ -212,7 +222,7 @@ ideq_status iterate(ideq_ctx* ctx, const OpDev& od, const ideq_shape& s, const f
                        ctx->sv.status, ctx->sv.part_s, ctx->sv.part_x, st));
   const float B = (std::isfinite(p->restart_B) && p->restart_B > 0.f) ? p->restart_B : INFINITY;
   CK(launch_finalize(n, ctx->sv_nblk, ctx->sv, 1 - par, p->beta, B, p->tol, p->max_iter,
-                     p->lambda, logic, st));
+                     p->lambda, logic, avg_K, st));
   ctx->launches += 3;
   return IDEQ_OK;
 }
@@ -226,6 +236,11 @@ ideq_status check_timeout(ideq_ctx* ctx) {
     return fail(ctx, IDEQ_ERR_TIMEOUT, "tensor-core kernel wait expired (code " + std::to_string(h) + ")");
   }
   return IDEQ_OK;
+}
+
+bool valid_precision(int p) {
+  return p == IDEQ_FP32 || p == IDEQ_BF16 || p == IDEQ_FP16 || p == IDEQ_BF16_FP8 ||
+         p == IDEQ_FP16_FP8;
 }
 
 ideq_status check_params(ideq_ctx* ctx, const ideq_params* p) {
@@ -284,7 +299,7 @@ ideq_status ideq_create(ideq_ctx** out, const ideq_net_desc* net, const float* w
                         int precision, void* stream) {
   clear_stale_cuda_error();
   if (!out || !net || !weights) return IDEQ_ERR_ARG;
-  if (precision != IDEQ_FP32 && precision != IDEQ_BF16 && precision != IDEQ_FP16)
+  if (!valid_precision(precision))
     return IDEQ_ERR_UNSUPPORTED;
   std::unique_ptr<ideq_ctx> c(new ideq_ctx());
   ideq_ctx* ctx = c.get();
@@ -334,7 +349,7 @@ ideq_status ideq_set_weights(ideq_ctx* ctx, const float* weights) {
 ideq_status ideq_set_precision(ideq_ctx* ctx, int precision) {
   clear_stale_cuda_error();
   if (!ctx) return IDEQ_ERR_ARG;
-  if (precision != IDEQ_FP32 && precision != IDEQ_BF16 && precision != IDEQ_FP16)
+  if (!valid_precision(precision))
     return fail(ctx, IDEQ_ERR_UNSUPPORTED, "precision");
   ctx->precision = precision;
   return IDEQ_OK;
@@ -429,6 +444,9 @@ ideq_status ideq_solve(ideq_ctx* ctx, const ideq_operator* op, ideq_shape shape,
   if (p->init == IDEQ_INIT_X0 && !x0) return fail(ctx, IDEQ_ERR_ARG, "init X0 needs x0");
   if (p->init == IDEQ_INIT_WARM && !ctx->warm_w)
     return fail(ctx, IDEQ_ERR_ARG, "init WARM needs ideq_warm_set");
+  const bool restart_on = std::isfinite(p->restart_B) && p->restart_B > 0.f;
+  if (p->average && (p->tol > 0.0 || restart_on || p->max_iter < 5))
+    return fail(ctx, IDEQ_ERR_ARG, "averaging needs tol = 0, no restart and max_iter >= 5");
   if ((s = ensure_plan(ctx, shape)) != IDEQ_OK) return s;
   const size_t bytes = (size_t)shape.n * shape.c * shape.h * shape.w * 4;
   cudaStream_t st = ctx->stream;
@@ -442,9 +460,10 @@ ideq_status ideq_solve(ideq_ctx* ctx, const ideq_operator* op, ideq_shape shape,
   }
   CK(cudaMemcpyAsync(ctx->xb[1], ctx->xb[0], bytes, cudaMemcpyDeviceToDevice, st));
   CK(launch_solver_init(shape.n, ctx->sv, 0.f, st));  // x^{-1} = x^0
+  if (p->average) CK(cudaMemsetAsync(ctx->sv.zsum, 0, 2 * bytes, st));
   const int poll = p->tol > 0.0 ? 2 : 0;
   for (int it = 0; it < p->max_iter; ++it) {
-    if ((s = iterate(ctx, od, shape, y, p, it & 1, 1)) != IDEQ_OK) return s;
+    if ((s = iterate(ctx, od, shape, y, p, it & 1, 1, p->average != 0)) != IDEQ_OK) return s;
     if (poll && ((it + 1) % poll == 0) && it + 1 < p->max_iter) {
       CK(cudaMemcpyAsync(ctx->h_running, ctx->sv.n_running, 4, cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
@@ -453,6 +472,10 @@ ideq_status ideq_solve(ideq_ctx* ctx, const ideq_operator* op, ideq_shape shape,
   }
   CK(launch_gather_parity(shape.n, ctx->sv_per, ctx->sv.parity, ctx->xb[0], ctx->xb[1], x_out, st));
   ctx->launches += 1;
+  if (p->average) {
+    CK(launch_average_out(shape.n, ctx->sv_per, ctx->sv, x_out, st));
+    ctx->launches += 1;
+  }
   if (info) CK(launch_fill_info(shape.n, ctx->sv, *info, st));
   if ((s = check_timeout(ctx)) != IDEQ_OK) return s;
   // overall status (stream already synchronised by check_timeout)
@@ -519,7 +542,7 @@ ideq_status ideq_solve_backward(ideq_ctx* ctx, const ideq_operator* op, ideq_sha
       CK(launch_red_update(n, per, ctx->sv_nblk, T->zd, ctx->gf, T->hvp, uk, up, p->lambda,
                            p->tau, ctx->sv.status, ctx->sv.part_s, ctx->sv.part_x, st, dl_dx));
       CK(launch_finalize(n, ctx->sv_nblk, ctx->sv, 1 - par, ap->beta, INFINITY, ap->tol,
-                         ap->max_iter, 0.f, 1, st));
+                         ap->max_iter, 0.f, 1, 0, st));
       ctx->launches += 3;
       if ((it & 1) == 1 && it + 1 < ap->max_iter) {
         CK(cudaMemcpyAsync(ctx->h_running, ctx->sv.n_running, 4, cudaMemcpyDeviceToHost, st));

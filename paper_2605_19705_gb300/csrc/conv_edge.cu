@@ -276,6 +276,7 @@ static cudaError_t launch_edge_t(const ConvArgs& a, cudaStream_t st) {
 
 cudaError_t launch_conv_edge(const ConvArgs& a, int feat_dt, cudaStream_t st) {
   if (a.M() == 0) return cudaSuccess;
+  if (edge_rb_supported(a)) return launch_conv_edge_rb(a, feat_dt, st);
   if (feat_dt == DT_BF16) return launch_edge_t<__nv_bfloat16>(a, st);
   if (feat_dt == DT_F16) return launch_edge_t<__half>(a, st);
   return launch_edge_t<float>(a, st);

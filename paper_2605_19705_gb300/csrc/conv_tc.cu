@@ -28,6 +28,7 @@
 // sets *err_flag, all roles drain and the CTA returns after freeing TMEM.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 #include <cstdlib>
@@ -48,13 +49,17 @@ struct TcArgs {
   int naux;    // auxiliary inputs (0..3)
   int nbo;     // output staging buffers (1 or 2)
   int nba;     // auxiliary staging buffers (1 or 2)
+  const float* a_scale;  // FP8 operands: activation scale (device scalar)
+  const float* w_scale;  // FP8 operands: weight scale per GEMM column
+  int slide;             // halo form: contiguous row runs per CTA reusing row boxes
   int* err;
 };
 
 struct TcPlan {
   CUtensorMap tmA, tmB, tmO[2], tmX[3];
-  int bn = 0, stages = 0, dt = DT_BF16, nout = 1, naux = 0, nbo = 2, nba = 2, ms = 1;
-  bool halo = false;
+  int bn = 0, stages = 0, op_dt = DT_BF16, epi_dt = DT_BF16, nout = 1, naux = 0, nbo = 2,
+      nba = 2, ms = 1;
+  bool halo = false, slide = false;
   int Wt = 0, Ht = 0, tiles_w = 0, tiles_h = 0, tiles_n = 0, nk = 0, cpt = 0;
   dim3 grid;
   size_t smem = 0;
@@ -137,6 +142,13 @@ IDEQ_DEV void tma_load_5d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, i
       : "memory");
 }
 
+// Pull a tensor box into L2 ahead of its load (no shared memory, no barrier).
+IDEQ_DEV void tma_prefetch_4d(const CUtensorMap* tm, int c0, int c1, int c2, int c3) {
+  asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];" ::"l"(tm),
+               "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+               : "memory");
+}
+
 IDEQ_DEV void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 IDEQ_DEV void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -171,18 +183,34 @@ __host__ __device__ constexpr uint32_t umma_idesc_16(int M, int N, uint32_t fmt)
          ((uint32_t)(M >> 4) << 24);
 }
 
+// Operand format codes of the instruction descriptor: kind::f16 takes 0 = f16,
+// 1 = bf16; kind::f8f6f4 takes 0 = e4m3 (the same bit fields).
 template <typename T> struct Fmt;
 template <> struct Fmt<__nv_bfloat16> { static constexpr uint32_t v = 1; };
 template <> struct Fmt<__half> { static constexpr uint32_t v = 0; };
+template <> struct Fmt<__nv_fp8_e4m3> { static constexpr uint32_t v = 0; };
 
-IDEQ_DEV void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                        uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
+// One MMA, D (+)= A * B^T, 128 x N x (32 bytes of K): K = 16 16-bit elements
+// (kind::f16) or 32 e4m3 elements (kind::f8f6f4).  Both operands of one MMA
+// have the same element type.
+template <typename TA>
+IDEQ_DEV void umma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                   uint32_t accumulate) {
+  if constexpr (sizeof(TA) == 1) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  }
 }
 
 IDEQ_DEV void umma_commit(uint32_t bar) {
@@ -428,8 +456,26 @@ IDEQ_DEV void epi_tma(bool store, const TcArgs& a, const CUtensorMap* tm, uint32
 // resident in shared memory.  A is fetched once instead of nine times.
 constexpr int HALO_ROWS = 130;
 constexpr int HALO_BOX = 17408;  // 130 rows x 128 B, rounded up to a 1024-B atom
+constexpr int HALO_PF = 4;       // rows prefetched into L2 ahead of the row being loaded
 
-template <typename T, int BN, bool HALO, int MS>
+// Halo form: tile t -> row t % tiles_h of 128-pixel column strip t / tiles_h
+// (strips in (image, strip) order); the ring holds single row boxes and a tile
+// reads three of them.  Tiles stride the grid (neighbouring CTAs work on
+// neighbouring rows, so most row boxes are still in L2 when the second and third
+// CTA need them), or, in the sliding form, each CTA runs a contiguous range of
+// rows and a tile that continues its run loads only row y+1, reusing y-1 and y
+// (measured slower on the U-Net's 64-channel layers: 90 vs 60 us).
+IDEQ_DEV TileCoord halo_coord(const TcArgs& a, int t) {
+  const int strip = t / a.tiles_h;
+  TileCoord c;
+  c.h0 = t - strip * a.tiles_h;
+  c.w0 = (strip % a.tiles_w) * 128;
+  c.img = strip / a.tiles_w;
+  c.n0 = 0;
+  return c;
+}
+
+template <typename TA, typename T, int BN, bool HALO, int MS>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     conv_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                    const __grid_constant__ CUtensorMap tmB,
@@ -440,10 +486,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                    const __grid_constant__ CUtensorMap tmX2, TcArgs a) {
   static_assert(!HALO || MS == 1, "the halo form has one 128-row sub-tile");
   constexpr int B_BYTES = BN * 128;
-  constexpr int A_STAGE = HALO ? 3 * HALO_BOX : MS * A_BYTES;
-  constexpr uint32_t STAGE_TX =
-      HALO ? 3u * HALO_ROWS * 128u : (uint32_t)(MS * A_BYTES + B_BYTES);
+  constexpr int A_STAGE = HALO ? HALO_BOX : MS * A_BYTES;  // ring slot: one row box (HALO)
+  constexpr uint32_t STAGE_TX = HALO ? HALO_ROWS * 128u : (uint32_t)(MS * A_BYTES + B_BYTES);
   constexpr int NPANEL = BN / 64;
+  constexpr int KCH = 128 / (int)sizeof(TA);  // K elements per 128-byte ring row
+  static_assert(!HALO || sizeof(TA) == 2, "the halo form has 16-bit operands");
   constexpr int TCOLS = MS * BN;  // TMEM columns of one accumulator buffer
   const int ST = a.stages;
   extern __shared__ uint8_t smem_raw[];
@@ -463,7 +510,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t bres = smem_u32(bars + 2 * ST + 5);
   const uint32_t auxbar0 = smem_u32(bars + 2 * ST + 6);  // [warp][2]
   const int ntiles = ((a.n * a.tiles_h * a.tiles_w + MS - 1) / MS) * a.tiles_n;
-  const int nsteps = HALO ? a.cpt : a.nk;  // ring stages per tile
+  // this CTA's tiles: t_first + i * t_step, i < my_tiles (a contiguous range in
+  // the halo form, a grid-strided sequence otherwise)
+  int t_first, t_step, my_tiles;
+  if (HALO && a.slide) {
+    t_first = (int)(((long long)blockIdx.x * ntiles) / gridDim.x);
+    my_tiles = (int)(((long long)(blockIdx.x + 1) * ntiles) / gridDim.x) - t_first;
+    t_step = 1;
+  } else {
+    t_first = blockIdx.x;
+    t_step = gridDim.x;
+    my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  }
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
@@ -499,13 +557,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (HALO) {  // resident weights: every K chunk of B once
         mbar_expect_tx(bres, (uint32_t)(a.nk * B_BYTES));
         for (int kc = 0; kc < a.nk; ++kc)
-          tma_load_2d(smem_u32(sB + kc * B_BYTES), &tmB, kc * 64, 0, bres);
+          tma_load_2d(smem_u32(sB + kc * B_BYTES), &tmB, kc * KCH, 0, bres);
       }
-      int g = 0;  // ring position across tiles
+      int g = 0;  // ring position across tiles (row boxes in the halo form)
       bool ok = true;
-      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      if constexpr (HALO) {
+        for (int i = 0; i < my_tiles && ok; ++i) {
+          const int t = t_first + i * t_step;
+          const TileCoord tc = halo_coord(a, t);
+          const bool fresh = !a.slide || i == 0 || t % a.tiles_h == 0;  // three new boxes
+          // rows loaded a few tiles from now are pulled into L2 first: each row is
+          // read by this CTA alone, so its load would otherwise wait on DRAM
+          if (a.slide)
+            for (int r = fresh ? 2 : HALO_PF + 1; r <= HALO_PF + 1; ++r)
+              if (tc.h0 + r < a.H) tma_prefetch_4d(&tmA, 0, tc.w0 - 1, tc.h0 + r, tc.img);
+          for (int dy = fresh ? -1 : 1; dy <= 1; ++dy) {
+            const int s = g % ST, j = g / ST;
+            if (j > 0 && !mbar_wait(empty0 + 8 * s, (j - 1) & 1, a.err, 1)) {
+              ok = false;
+              break;
+            }
+            mbar_expect_tx(full0 + 8 * s, STAGE_TX);
+            tma_load_4d(smem_u32(sA + s * A_STAGE), &tmA, 0, tc.w0 - 1, tc.h0 + dy, tc.img,
+                        full0 + 8 * s);
+            ++g;
+          }
+        }
+      }
+      for (int i = 0; i < my_tiles && ok && !HALO; ++i) {
+        const int t = t_first + i * t_step;
         const TileCoord tc = tile_coord(a, t, BN, MS, 0);
-        for (int kc = 0; kc < nsteps; ++kc) {
+        for (int kc = 0; kc < a.nk; ++kc) {
           const int s = g % ST, j = g / ST;
           if (j > 0 && !mbar_wait(empty0 + 8 * s, (j - 1) & 1, a.err, 1)) {
             ok = false;
@@ -513,31 +595,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
           mbar_expect_tx(full0 + 8 * s, STAGE_TX);
           const uint32_t dA = smem_u32(sA + s * A_STAGE);
-          if (HALO) {
-            for (int dy = 0; dy < 3; ++dy)
-              tma_load_4d(dA + dy * HALO_BOX, &tmA, kc * 64, tc.w0 - 1, tc.h0 + dy - 1, tc.img,
-                          full0 + 8 * s);
-          } else {
+          {
             const uint32_t dB = smem_u32(sB + s * B_BYTES);
 #pragma unroll
             for (int sub = 0; sub < MS; ++sub) {
               const TileCoord sc = sub == 0 ? tc : tile_coord(a, t, BN, MS, sub);
               const uint32_t dAs = dA + sub * A_BYTES;
               if (a.mode == CM_DOWN) {
-                const int k0 = kc * 64;
+                const int k0 = kc * KCH;
                 const int di = k0 / (2 * a.Cin), rem = k0 - di * 2 * a.Cin;
                 tma_load_5d(dAs, &tmA, rem, sc.w0, di, sc.h0, sc.img, full0 + 8 * s);
               } else {
-                int tap = 4, c0 = kc * 64;
+                int tap = 4, c0 = kc * KCH;
                 if (a.mode == CM_CONV3) {
                   tap = kc / a.cpt;
-                  c0 = (kc - tap * a.cpt) * 64;
+                  c0 = (kc - tap * a.cpt) * KCH;
                 }
                 tma_load_4d(dAs, &tmA, c0, sc.w0 + tap % 3 - 1, sc.h0 + tap / 3 - 1, sc.img,
                             full0 + 8 * s);
               }
             }
-            tma_load_2d(dB, &tmB, kc * 64, tc.n0, full0 + 8 * s);
+            tma_load_2d(dB, &tmB, kc * KCH, tc.n0, full0 + 8 * s);
           }
           ++g;
         }
@@ -554,11 +632,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = umma_idesc_16(128, BN, Fmt<T>::v);
+      constexpr uint32_t idesc = umma_idesc_16(128, BN, Fmt<TA>::v);
       bool ok = true;
       if (HALO) ok = mbar_wait(bres, 0, a.err, 9);
-      int g = 0, lt = 0;
-      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++lt) {
+      int g = 0, base = 0;  // base: ring position of the tile's row y-1 box (HALO)
+      for (int lt = 0; lt < my_tiles && ok; ++lt) {
+        const int t = t_first + lt * t_step;
         const int b = lt & 1, u = lt >> 1;
         if (u > 0 && !mbar_wait(tempty0 + 8 * b, (u - 1) & 1, a.err, 5)) {
           ok = false;
@@ -566,40 +645,59 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         tc_fence_after();
         const uint32_t td = tmem + (uint32_t)(b * TCOLS);
-        for (int kc = 0; kc < nsteps; ++kc) {
-          const int s = g % ST, j = g / ST;
-          if (!mbar_wait(full0 + 8 * s, j & 1, a.err, 3)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          if (HALO) {
-            const uint32_t abase = smem_u32(sA + s * A_STAGE);
-#pragma unroll 1
-            for (int tap = 0; tap < 9; ++tap) {
-              const int dy = tap / 3, dx = tap - 3 * dy;
-              const uint64_t ad = umma_desc_sw128_rows(abase + dy * HALO_BOX, dx);
-              const uint64_t bd =
-                  umma_desc_sw128(smem_u32(sB + (tap * a.cpt + kc) * B_BYTES));
-#pragma unroll
-              for (int kk = 0; kk < 4; ++kk)
-                umma_bf16(td, ad + 2 * kk, bd + 2 * kk, idesc, (kc | tap | kk) != 0 ? 1u : 0u);
-            }
+        if constexpr (HALO) {
+          const bool fresh = !a.slide || lt == 0 || t % a.tiles_h == 0;
+          if (fresh) {
+            base = g;
+            g += 3;
           } else {
+            base += 1;
+            g += 1;
+          }
+          for (int dy = 0; dy < 3 && ok; ++dy) {
+            const int box = base + dy;
+            ok = mbar_wait(full0 + 8 * (box % ST), (box / ST) & 1, a.err, 3);
+          }
+          if (!ok) break;
+          tc_fence_after();
+#pragma unroll 1
+          for (int tap = 0; tap < 9; ++tap) {
+            const int dy = tap / 3, dx = tap - 3 * dy;
+            const uint64_t ad =
+                umma_desc_sw128_rows(smem_u32(sA + ((base + dy) % ST) * A_STAGE), dx);
+            const uint64_t bd = umma_desc_sw128(smem_u32(sB + tap * B_BYTES));
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+              umma<TA>(td, ad + 2 * kk, bd + 2 * kk, idesc, (tap | kk) != 0 ? 1u : 0u);
+          }
+          umma_commit(tfull0 + 8 * b);
+          // release the boxes the next tile does not read: row y-1, or all three
+          // when the next tile starts a new strip run (or there is none)
+          const bool next_fresh = !a.slide || lt + 1 == my_tiles || (t + 1) % a.tiles_h == 0;
+          for (int dy = 0; dy < (next_fresh ? 3 : 1); ++dy)
+            umma_commit(empty0 + 8 * ((base + dy) % ST));
+        } else {
+          for (int kc = 0; kc < a.nk; ++kc) {
+            const int s = g % ST, j = g / ST;
+            if (!mbar_wait(full0 + 8 * s, j & 1, a.err, 3)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
             const uint64_t bd = umma_desc_sw128(smem_u32(sB + s * B_BYTES));
 #pragma unroll
             for (int sub = 0; sub < MS; ++sub) {
               const uint64_t ad = umma_desc_sw128(smem_u32(sA + s * A_STAGE + sub * A_BYTES));
 #pragma unroll
               for (int kk = 0; kk < 4; ++kk)
-                umma_bf16(td + sub * BN, ad + 2 * kk, bd + 2 * kk, idesc,
+                umma<TA>(td + sub * BN, ad + 2 * kk, bd + 2 * kk, idesc,
                           (kc | kk) != 0 ? 1u : 0u);
             }
+            umma_commit(empty0 + 8 * s);
+            ++g;
           }
-          umma_commit(empty0 + 8 * s);
-          ++g;
+          if (ok) umma_commit(tfull0 + 8 * b);
         }
-        if (ok) umma_commit(tfull0 + 8 * b);
       }
       if (!ok) {  // let every issued MMA finish before TMEM is released
         umma_commit(drain);
@@ -618,12 +716,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t sX = smem_u32(sAux) + (uint32_t)(e * a.nba * a.naux * WBOX);
     const uint32_t xbar = auxbar0 + 16 * e;
     constexpr int TPANEL = MS * NPANEL;  // panels per tile
-    const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const int npc = my_tiles * TPANEL;  // panels this CTA processes
     // auxiliary box of panel k -> buffer k % nba, loaded ahead by lane 0
     auto aux_load = [&](int k) {
       const int i = k / TPANEL, r = k - i * TPANEL, sub = r / NPANEL, p = r - sub * NPANEL;
-      const TileCoord nc = tile_coord(a, blockIdx.x + i * gridDim.x, BN, MS, sub);
+      const int t = t_first + i * t_step;
+      const TileCoord nc = HALO ? halo_coord(a, t) : tile_coord(a, t, BN, MS, sub);
       const int buf = k % a.nba;
       const uint32_t bar = xbar + 8 * buf;
       mbar_expect_tx(bar, (uint32_t)(a.naux * WBOX));
@@ -636,7 +734,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (; aux_issued < a.nba && aux_issued < npc; ++aux_issued) aux_load(aux_issued);
     int lt = 0, pc = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++lt) {
+    for (; lt < my_tiles && ok; ++lt) {
+      const int t = t_first + lt * t_step;
       const int b = lt & 1, u = lt >> 1;
       ok = __all_sync(0xffffffffu, mbar_wait(tfull0 + 8 * b, u & 1, a.err, 4));
       tc_fence_after();
@@ -658,12 +757,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           __syncwarp();
           if (lane == 0) mbar_arrive(tempty0 + 8 * b);
         }
+        if constexpr (sizeof(TA) == 1) {  // FP8 operands: undo the two scales
+          const float sa = *a.a_scale;
+          const float* ws = a.w_scale + tile_coord(a, t, BN, MS, sub).n0 + 64 * p + 32 * half;
+#pragma unroll
+          for (int i = 0; i < 32; ++i) v[i] *= sa * __ldg(ws + i);
+        }
         const uint32_t ob = sO + (uint32_t)(sb * a.nout * WBOX);
         epi_apply<T>(a.epi, a.act, v, sX + (uint32_t)(ab * a.naux * WBOX), ob, lane);
         fence_async_smem();
         __syncwarp();
         if (lane == 0) {
-          const TileCoord tc = tile_coord(a, t, BN, MS, sub);
+          const TileCoord tc = HALO ? halo_coord(a, t) : tile_coord(a, t, BN, MS, sub);
           for (int i = 0; i < a.nout; ++i)
             epi_tma(true, a, tmO[i], ob + (uint32_t)(i * WBOX), tc, q,
                     tc.n0 + 64 * p + 32 * half, 0);
@@ -709,7 +814,8 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 static int tiling_override(const char* name, int dflt);
 
 static int pick_bn(int N) {
-  const int n256 = tiling_override("IDEQ_TC_BN256_MIN", 512);  // smallest N tiled 256 wide
+  // smallest N tiled 256 wide (measured: 256-wide tiles win from N = 256 up)
+  const int n256 = tiling_override("IDEQ_TC_BN256_MIN", 256);
   if (N % 256 == 0 && N >= n256) return 256;
   if (N % 128 == 0) return 128;
   return 64;
@@ -722,9 +828,12 @@ static int epi_naux(int epi) {
   return 0;
 }
 
-bool tc_supported(const ConvArgs& a) {
+static int k_chunk(int op_dt) { return op_dt == DT_FP8 ? 128 : 64; }  // K per 128-B row
+
+bool tc_supported(const ConvArgs& a, int op_dt) {
   if (a.in_nchw || a.out_nchw || a.epi == EP_AXPY_NCHW) return false;
-  if (a.Cin % 64 != 0) return false;
+  if (a.Cin % k_chunk(op_dt) != 0) return false;
+  if (op_dt == DT_FP8 && (!a.a_scale || !a.w_scale)) return false;
   if (a.N() % 64 != 0 || a.Cout % 64 != 0) return false;
   if (a.mode == CM_DOWN && a.outmap != OM_IDENT) return false;
   if (epi_naux(a.epi) >= 1 && !a.aux0) return false;
@@ -776,22 +885,25 @@ static int tiling_override(const char* name, int dflt) {
   return (v && *v) ? std::atoi(v) : dflt;
 }
 
-TcPlan* tc_plan_create(const ConvArgs& a, int dtype, std::string* err) {
+TcPlan* tc_plan_create(const ConvArgs& a, int op_dt, int epi_dt, std::string* err) {
   auto enc = get_encode();
   if (!enc) {
     *err = "cuTensorMapEncodeTiled unavailable";
     return nullptr;
   }
-  if (!tc_supported(a)) {
+  if ((op_dt != DT_BF16 && op_dt != DT_F16 && op_dt != DT_FP8) ||
+      (epi_dt != DT_BF16 && epi_dt != DT_F16) || (op_dt != DT_FP8 && op_dt != epi_dt)) {
+    *err = "tensor-core kernel needs bf16, f16 or e4m3 operands and a 16-bit output";
+    return nullptr;
+  }
+  if (!tc_supported(a, op_dt)) {
     *err = "layer not supported by the tensor-core kernel";
     return nullptr;
   }
-  if (dtype != DT_BF16 && dtype != DT_F16) {
-    *err = "tensor-core kernel needs bf16 or f16 operands";
-    return nullptr;
-  }
   TcPlan* p = new TcPlan();
-  p->dt = dtype;
+  p->op_dt = op_dt;
+  p->epi_dt = epi_dt;
+  const int KCH = k_chunk(op_dt);
   const int N = a.N();
   p->bn = pick_bn(N);
   p->nout = epi_nout(a.epi);
@@ -803,13 +915,15 @@ TcPlan* tc_plan_create(const ConvArgs& a, int dtype, std::string* err) {
   p->Ht = 128 / wt;
   p->tiles_w = (a.W + p->Wt - 1) / p->Wt;
   p->tiles_h = (a.H + p->Ht - 1) / p->Ht;
-  p->cpt = a.Cin / 64;
-  p->nk = a.K() / 64;
+  p->cpt = a.Cin / KCH;
+  p->nk = a.K() / KCH;
   p->tiles_n = N / p->bn;
-  // halo form: 3x3 conv over whole 128-pixel row segments with a resident weight matrix
+  // halo form: 3x3 conv of 64 channels over whole 128-pixel row segments, with
+  // the nine 64 x 64 weight taps resident in shared memory
   const size_t bres = (size_t)p->nk * p->bn * 128;
-  p->halo = a.mode == CM_CONV3 && p->Wt == 128 && p->Ht == 1 && p->tiles_n == 1 &&
-            bres <= 80 * 1024 && tiling_override("IDEQ_TC_HALO", 1) != 0;
+  p->halo = op_dt != DT_FP8 && a.mode == CM_CONV3 && p->Wt == 128 && p->Ht == 1 && p->tiles_n == 1 &&
+            p->cpt == 1 && bres <= 80 * 1024 && tiling_override("IDEQ_TC_HALO", 1) != 0;
+  p->slide = p->halo && tiling_override("IDEQ_TC_SLIDE", 0) != 0;
   // Two 128-row sub-tiles can share each weight chunk (half the weight traffic
   // per FLOP), but measured on the U-Net layers the coarser tiles balance worse
   // over the SMs than they save, so M = 256 is used only when forced.
@@ -818,13 +932,14 @@ TcPlan* tc_plan_create(const ConvArgs& a, int dtype, std::string* err) {
     const int force_ms = tiling_override("IDEQ_TC_MS", 0);  // 2 forces two sub-tiles
     if (!p->halo && p->bn <= 128 && force_ms == 2) p->ms = 2;
   }
-  // shared memory: ring depth and staging buffers, preferring >= 3 ring stages,
+  // shared memory: ring depth and staging buffers, preferring a deep ring
+  // (halo: >= 5 row boxes, three in use and two in flight; else >= 3 stages),
   // then double-buffered staging
-  const size_t stage =
-      p->halo ? (size_t)3 * HALO_BOX : (size_t)p->ms * A_BYTES + (size_t)p->bn * 128;
+  const size_t stage = p->halo ? (size_t)HALO_BOX : (size_t)p->ms * A_BYTES + (size_t)p->bn * 128;
   const size_t resident = p->halo ? bres : 0;
   p->stages = 0;
-  for (int min_st : {3, 2}) {
+  const int min_stages[2] = {p->halo ? 5 : 3, p->halo ? 4 : 2};
+  for (int min_st : min_stages) {
     for (int nbuf : {2, 1}) {
       int st = 8;
       auto total = [&](int k) {
@@ -857,37 +972,43 @@ TcPlan* tc_plan_create(const ConvArgs& a, int dtype, std::string* err) {
     const long long tiles = ((tiles_m + p->ms - 1) / p->ms) * p->tiles_n;
     p->grid = dim3((unsigned)std::min<long long>(tiles, sms), 1, 1);
   }
-  const CUtensorMapDataType dt =
-      dtype == DT_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  auto map_type = [](int d) {
+    return d == DT_FP8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                       : (d == DT_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                       : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
+  };
+  const CUtensorMapDataType dt = map_type(op_dt), edt = map_type(epi_dt);
+  const cuuint64_t es = op_dt == DT_FP8 ? 1 : 2;  // operand element bytes
   bool ok;
   if (a.mode == CM_DOWN) {
     const int Hi = 2 * a.H, Wi = 2 * a.W;
     cuuint64_t dims[5] = {(cuuint64_t)(2 * a.Cin), (cuuint64_t)a.W, 2, (cuuint64_t)a.H,
                           (cuuint64_t)a.n};
-    cuuint64_t strides[4] = {(cuuint64_t)2 * a.Cin * 2, (cuuint64_t)Wi * a.Cin * 2,
-                             (cuuint64_t)2 * Wi * a.Cin * 2, (cuuint64_t)Hi * Wi * a.Cin * 2};
-    cuuint32_t box[5] = {64, (cuuint32_t)p->Wt, 1, (cuuint32_t)p->Ht, 1};
+    cuuint64_t strides[4] = {(cuuint64_t)2 * a.Cin * es, (cuuint64_t)Wi * a.Cin * es,
+                             (cuuint64_t)2 * Wi * a.Cin * es, (cuuint64_t)Hi * Wi * a.Cin * es};
+    cuuint32_t box[5] = {(cuuint32_t)KCH, (cuuint32_t)p->Wt, 1, (cuuint32_t)p->Ht, 1};
     ok = encode(enc, &p->tmA, dt, 5, a.in, dims, strides, box);
   } else {
     cuuint64_t dims[4] = {(cuuint64_t)a.Cin, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.n};
-    cuuint64_t strides[3] = {(cuuint64_t)a.Cin * 2, (cuuint64_t)a.W * a.Cin * 2,
-                             (cuuint64_t)a.H * a.W * a.Cin * 2};
-    cuuint32_t box[4] = {64, (cuuint32_t)(p->halo ? HALO_ROWS : p->Wt), (cuuint32_t)p->Ht, 1};
+    cuuint64_t strides[3] = {(cuuint64_t)a.Cin * es, (cuuint64_t)a.W * a.Cin * es,
+                             (cuuint64_t)a.H * a.W * a.Cin * es};
+    cuuint32_t box[4] = {(cuuint32_t)KCH, (cuuint32_t)(p->halo ? HALO_ROWS : p->Wt),
+                         (cuuint32_t)p->Ht, 1};
     ok = encode(enc, &p->tmA, dt, 4, a.in, dims, strides, box);
   }
   {
     const int K = a.K();
     cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)N};
-    cuuint64_t strides[1] = {(cuuint64_t)K * 2};
-    cuuint32_t box[2] = {64, (cuuint32_t)p->bn};
+    cuuint64_t strides[1] = {(cuuint64_t)K * es};
+    cuuint32_t box[2] = {(cuuint32_t)KCH, (cuuint32_t)p->bn};
     ok = ok && encode(enc, &p->tmB, dt, 2, a.wB, dims, strides, box);
   }
   const void* outs[2] = {a.out, a.out2};
   const void* auxs[3] = {a.aux0, a.aux1, a.aux2};
   for (int i = 0; i < 2; ++i)
-    ok = ok && encode_epi(enc, &p->tmO[i], dt, a, p, i < p->nout ? outs[i] : a.out);
+    ok = ok && encode_epi(enc, &p->tmO[i], edt, a, p, i < p->nout ? outs[i] : a.out);
   for (int i = 0; i < 3; ++i)
-    ok = ok && encode_epi(enc, &p->tmX[i], dt, a, p, i < p->naux ? auxs[i] : a.out);
+    ok = ok && encode_epi(enc, &p->tmX[i], edt, a, p, i < p->naux ? auxs[i] : a.out);
   if (!ok) {
     *err = "cuTensorMapEncodeTiled failed";
     delete p;
@@ -898,39 +1019,46 @@ TcPlan* tc_plan_create(const ConvArgs& a, int dtype, std::string* err) {
 
 void tc_plan_destroy(TcPlan* p) { delete p; }
 
-template <typename T, int BN, bool HALO, int MS>
+template <typename TA, typename T, int BN, bool HALO, int MS>
 static cudaError_t launch_bn(const TcPlan* p, const TcArgs& ta, cudaStream_t st) {
   static bool attr_set = false;  // per instantiation; set before first launch
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<T, BN, HALO, MS>,
+    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<TA, T, BN, HALO, MS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kMaxSmem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  conv_tc_kernel<T, BN, HALO, MS><<<p->grid, TC_THREADS, p->smem, st>>>(
+  conv_tc_kernel<TA, T, BN, HALO, MS><<<p->grid, TC_THREADS, p->smem, st>>>(
       p->tmA, p->tmB, p->tmO[0], p->tmO[1], p->tmX[0], p->tmX[1], p->tmX[2], ta);
   return cudaGetLastError();
 }
 
 template <typename T>
 static cudaError_t launch_typed(const TcPlan* p, const TcArgs& t, cudaStream_t st) {
+  if (p->op_dt == DT_FP8) {  // e4m3 operands: plain tiles only
+    switch (p->bn) {
+      case 64: return launch_bn<__nv_fp8_e4m3, T, 64, false, 1>(p, t, st);
+      case 128: return launch_bn<__nv_fp8_e4m3, T, 128, false, 1>(p, t, st);
+      default: return launch_bn<__nv_fp8_e4m3, T, 256, false, 1>(p, t, st);
+    }
+  }
   if (p->halo) {
     switch (p->bn) {
-      case 64: return launch_bn<T, 64, true, 1>(p, t, st);
-      default: return launch_bn<T, 128, true, 1>(p, t, st);
+      case 64: return launch_bn<T, T, 64, true, 1>(p, t, st);
+      default: return launch_bn<T, T, 128, true, 1>(p, t, st);
     }
   }
   if (p->ms == 2) {
     switch (p->bn) {
-      case 64: return launch_bn<T, 64, false, 2>(p, t, st);
-      default: return launch_bn<T, 128, false, 2>(p, t, st);
+      case 64: return launch_bn<T, T, 64, false, 2>(p, t, st);
+      default: return launch_bn<T, T, 128, false, 2>(p, t, st);
     }
   }
   switch (p->bn) {
-    case 64: return launch_bn<T, 64, false, 1>(p, t, st);
-    case 128: return launch_bn<T, 128, false, 1>(p, t, st);
-    default: return launch_bn<T, 256, false, 1>(p, t, st);
+    case 64: return launch_bn<T, T, 64, false, 1>(p, t, st);
+    case 128: return launch_bn<T, T, 128, false, 1>(p, t, st);
+    default: return launch_bn<T, T, 256, false, 1>(p, t, st);
   }
 }
 
@@ -958,8 +1086,11 @@ cudaError_t launch_conv_tc(const TcPlan* p, const ConvArgs& a, int* err_flag, cu
   t.naux = p->naux;
   t.nbo = p->nbo;
   t.nba = p->nba;
+  t.slide = p->slide ? 1 : 0;
+  t.a_scale = a.a_scale;
+  t.w_scale = a.w_scale;
   t.err = err_flag;
-  if (p->dt == DT_F16) return launch_typed<__half>(p, t, st);
+  if (p->epi_dt == DT_F16) return launch_typed<__half>(p, t, st);
   return launch_typed<__nv_bfloat16>(p, t, st);
 }
 

@@ -17,7 +17,7 @@
 namespace ideq {
 
 // element storage of network activations
-enum DType { DT_F32 = 0, DT_BF16 = 1, DT_F16 = 2 };
+enum DType { DT_F32 = 0, DT_BF16 = 1, DT_F16 = 2, DT_FP8 = 3 };  // DT_FP8: e4m3 operands only
 
 // ------------------------------------------------------------- conv GEMMs
 //
@@ -57,6 +57,8 @@ struct ConvArgs {
   const void* aux1 = nullptr;
   const void* aux2 = nullptr;
   double* sumsq = nullptr;     // per-image accumulator of 1/2 sum(out^2), or null
+  const float* a_scale = nullptr;  // FP8 operands: activation scale (device scalar)
+  const float* w_scale = nullptr;  // FP8 operands: weight scale per output column [N]
   IDEQ_HD int N() const { return outmap == OM_D2S ? 4 * Cout : Cout; }
   IDEQ_HD int K() const { return mode == CM_CONV3 ? 9 * Cin : (mode == CM_DOWN ? 4 * Cin : Cin); }
   IDEQ_HD long long M() const { return (long long)n * H * W; }
@@ -71,12 +73,17 @@ cudaError_t launch_conv_simt(const ConvArgs& a, int in_dt, int out_dt, cudaStrea
 // conv_edge.cu).  feat_dt is the element type of the NHWC side.
 bool edge_supported(const ConvArgs& a);
 cudaError_t launch_conv_edge(const ConvArgs& a, int feat_dt, cudaStream_t st);
+// register-blocked forms of the common edge shapes (c in {1, 3}, C in {32, 64})
+bool edge_rb_supported(const ConvArgs& a);
+cudaError_t launch_conv_edge_rb(const ConvArgs& a, int feat_dt, cudaStream_t st);
 
-// tcgen05 path: 16-bit (bf16 or f16) NHWC in/out and weights, Cin % 64 == 0,
-// N % 64 == 0 (see conv_tc.cu).
+// tcgen05 path: 16-bit (bf16 or f16) or FP8 e4m3 NHWC input and weights, 16-bit
+// NHWC output; Cin a multiple of 64 (16-bit) or 128 (FP8) channels, N % 64 == 0
+// (see conv_tc.cu).  op_dt: operand type (DT_BF16, DT_F16, DT_FP8); epi_dt:
+// type of the outputs and auxiliary inputs (DT_BF16 or DT_F16).
 struct TcPlan;  // tensor maps + launch geometry, built once per (layer, buffers)
-bool tc_supported(const ConvArgs& a);
-TcPlan* tc_plan_create(const ConvArgs& a, int dt, std::string* err);
+bool tc_supported(const ConvArgs& a, int op_dt = DT_F16);
+TcPlan* tc_plan_create(const ConvArgs& a, int op_dt, int epi_dt, std::string* err);
 void tc_plan_destroy(TcPlan* p);
 cudaError_t launch_conv_tc(const TcPlan* p, const ConvArgs& a, int* err_flag, cudaStream_t st);
 
@@ -84,6 +91,15 @@ cudaError_t launch_conv_tc(const TcPlan* p, const ConvArgs& a, int* err_flag, cu
 enum WForm { WF_CONV3_FWD = 0, WF_CONV3_DGRAD, WF_DOWN_FWD, WF_DOWN_DGRAD, WF_UP_FWD, WF_UP_DGRAD };
 cudaError_t launch_weight_form(int form, int cin, int cout, const float* src, float* dst_f32,
                                void* dst_bf16, void* dst_f16, cudaStream_t st);
+void weight_form_dims(int form, int cin, int cout, int* N, int* K);  // the form's [N][K]
+// FP8 e4m3 weight form: w8[n][k] = e4m3(w32[n][k] / s[n]), s[n] = max_k |w32[n][k]| / 448.
+cudaError_t launch_weight_fp8(const float* w32, int N, int K, uint8_t* w8, float* scale,
+                              cudaStream_t st);
+// FP8 e4m3 activation: *amax = max |x| over n 16-bit values (dt; *amax zeroed by the
+// caller), then x8 = e4m3(x / s), *scale = s = *amax / 448 (1 when x == 0).
+cudaError_t launch_act_amax(const void* x, int dt, long long n, float* amax, cudaStream_t st);
+cudaError_t launch_act_fp8(const void* x, int dt, long long n, const float* amax, uint8_t* x8,
+                           float* scale, cudaStream_t st);
 // Scatter a GEMM-layout weight gradient [N][K] back to PyTorch layout (+=).
 cudaError_t launch_weight_unform(int form, int cin, int cout, const float* g, float* dst,
                                  cudaStream_t st);
@@ -127,10 +143,22 @@ struct SolverDev {
   double* part_s;  // [n][nblk] partial sums of ||x_new - x||^2
   double* part_x;  // [n][nblk] partial sums of ||x||^2
   int* n_running;
+  // averaging step of Algorithm 1 (used when the solve asks for it)
+  double* best;    // smallest step norm inside the averaging window so far
+  int* k0;         // its index K0 (-1: none)
+  int* snap;       // 1: the running sum after this update is the new snapshot
+  double* zsum;    // [n][per] running sum of the extrapolated points z^k
+  double* zsnap;   // [n][per] snapshot sum_{k <= K0} z^k
 };
 
 cudaError_t launch_extrapolate(int n, int per_img, const float* x, const float* xp,
                                const float* beta_eff, float* z, cudaStream_t st);
+// extrapolation that also keeps the averaging step's running sum of z and its snapshot
+cudaError_t launch_extrapolate_avg(int n, int per_img, const float* x, const float* xp,
+                                   const SolverDev& s, float* z, cudaStream_t st);
+// x_hat = snapshot / (K0 + 1) for the images the averaging step applies to
+cudaError_t launch_average_out(int n, int per_img, const SolverDev& s, float* out,
+                               cudaStream_t st);
 // xn = z - tau (gf + lambda gg) (+ addv when non-null) for running images.
 cudaError_t launch_red_update(int n, int per_img, int nblk, const float* z, const float* gf,
                               const float* gg, const float* x, float* xn, float lam, float tau,
@@ -138,7 +166,7 @@ cudaError_t launch_red_update(int n, int per_img, int nblk, const float* z, cons
                               cudaStream_t st, const float* addv = nullptr);
 cudaError_t launch_finalize(int n, int nblk, const SolverDev& s, int parity_new, float beta,
                             float B, double tol, int max_iter, float lam, int apply_logic,
-                            cudaStream_t st);
+                            int avg_K, cudaStream_t st);
 cudaError_t launch_gather_parity(int n, int per_img, const int* parity, const float* b0,
                                  const float* b1, float* out, cudaStream_t st);
 cudaError_t launch_solver_init(int n, const SolverDev& s, float beta, cudaStream_t st);

@@ -318,6 +318,52 @@ cudaError_t launch_extrapolate(int n, int per_img, const float* x, const float* 
   return cudaGetLastError();
 }
 
+// z = x + beta (x - xp), and the averaging step's bookkeeping: the running sum
+// (FP64) of the z's gains this z, after its previous value became the snapshot
+// if the last update set a new minimum inside the window.
+__global__ void extrapolate_avg_kernel(int per, long long total, const float* __restrict__ x,
+                                       const float* __restrict__ xp, SolverDev s,
+                                       float* __restrict__ z) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(i / per);
+    const float a = x[i];
+    const float zz = fmaf(s.beta_eff[b], a - xp[i], a);
+    z[i] = zz;
+    const double s0 = s.zsum[i];
+    if (s.snap[b]) s.zsnap[i] = s0;
+    s.zsum[i] = s0 + (double)zz;
+  }
+}
+
+cudaError_t launch_extrapolate_avg(int n, int per_img, const float* x, const float* xp,
+                                   const SolverDev& s, float* z, cudaStream_t st) {
+  const long long total = (long long)n * per_img;
+  const int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 8);
+  extrapolate_avg_kernel<<<blocks, 256, 0, st>>>(per_img, total, x, xp, s, z);
+  return cudaGetLastError();
+}
+
+// Averaging step output: x_hat = (sum_{k <= K0} z^k) / (K0 + 1) for the images
+// that ran all K updates and have a K0; the others keep their last iterate.
+__global__ void average_out_kernel(int per, long long total, SolverDev s, float* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(i / per);
+    if (s.status[b] != IDEQ_IMG_MAXITER || s.k0[b] < 0) continue;
+    const double sum = s.snap[b] ? s.zsum[i] : s.zsnap[i];
+    out[i] = (float)(sum / (double)(s.k0[b] + 1));
+  }
+}
+
+cudaError_t launch_average_out(int n, int per_img, const SolverDev& s, float* out,
+                               cudaStream_t st) {
+  const long long total = (long long)n * per_img;
+  const int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 8);
+  average_out_kernel<<<blocks, 256, 0, st>>>(per_img, total, s, out);
+  return cudaGetLastError();
+}
+
 int update_blocks_per_image(int per_img) {
   const int b = (per_img + 256 * 16 - 1) / (256 * 16);
   return std::max(1, std::min(b, 64));
@@ -395,8 +441,13 @@ cudaError_t launch_red_update(int n, int per_img, int nblk, const float* z, cons
 //   ||dx|| < tol ||x^k||       -> CONVERGED (frozen)
 //   total == max_iter          -> MAXITER (frozen)
 //   k S > B^2                  -> restart: k = 0, S = 0, next beta 0.
+// avg_K > 0: track the averaging step of Algorithm 1 for a run of avg_K
+// updates -- the update with index k (x^{k+1} from z^k) competes for K0 when
+// floor(K/2) < k < K-1, the first strict minimum of ||x^{k+1} - x^k|| wins, and
+// snap marks that the running sum of z up to z^k must be kept.
 __global__ void finalize_kernel(int n, int nblk, SolverDev s, int parity_new, float beta,
-                                float B, double tol, int max_iter, float lam, int logic) {
+                                float B, double tol, int max_iter, float lam, int logic,
+                                int avg_K) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   __shared__ int run_cnt[32];
   int my_run = 0;
@@ -410,7 +461,15 @@ __global__ void finalize_kernel(int n, int nblk, SolverDev s, int parity_new, fl
     sx = warp_sum(sx);
     if (lane == 0) {
       const bool running = s.status[b] == IDEQ_IMG_RUNNING;
+      if (avg_K > 0) s.snap[b] = 0;
       if (running) {
+        const int kk = s.total[b];  // index k of this update
+        if (avg_K > 0 && isfinite(ss) && kk > avg_K / 2 && kk < avg_K - 1 &&
+            sqrt(ss) < s.best[b]) {
+          s.best[b] = sqrt(ss);
+          s.k0[b] = kk;
+          s.snap[b] = 1;
+        }
         const double rel = sx > 0.0 ? sqrt(ss / sx) : INFINITY;
         s.rel[b] = rel;
         s.energy[b] = s.fsum[b] + (double)lam * s.gsum[b];
@@ -453,10 +512,10 @@ __global__ void finalize_kernel(int n, int nblk, SolverDev s, int parity_new, fl
 
 cudaError_t launch_finalize(int n, int nblk, const SolverDev& s, int parity_new, float beta,
                             float B, double tol, int max_iter, float lam, int apply_logic,
-                            cudaStream_t st) {
+                            int avg_K, cudaStream_t st) {
   const int warps = std::min(n, 32);
   finalize_kernel<<<1, 32 * warps, 0, st>>>(n, nblk, s, parity_new, beta, B, tol, max_iter, lam,
-                                           apply_logic);
+                                           apply_logic, avg_K);
   return cudaGetLastError();
 }
 
@@ -474,6 +533,9 @@ __global__ void solver_init_kernel(int n, SolverDev s, float beta) {
     s.fsum[b] = 0.0;
     s.gsum[b] = 0.0;
     s.energy[b] = 0.0;
+    s.best[b] = INFINITY;
+    s.k0[b] = -1;
+    s.snap[b] = 0;
   }
   if (b == 0) *s.n_running = n;
 }
@@ -491,6 +553,7 @@ __global__ void fill_info_kernel(int n, SolverDev s, ideq_info info) {
   if (info.status) info.status[b] = s.status[b];
   if (info.rel_res) info.rel_res[b] = s.rel[b];
   if (info.energy) info.energy[b] = s.energy[b];
+  if (info.k0) info.k0[b] = s.k0[b];
 }
 
 cudaError_t launch_fill_info(int n, const SolverDev& s, ideq_info info, cudaStream_t st) {
@@ -567,7 +630,7 @@ __device__ __forceinline__ long long wform_src(int form, int cin, int cout, int 
   }
 }
 
-static void wform_dims(int form, int cin, int cout, int* N, int* K) {
+void weight_form_dims(int form, int cin, int cout, int* N, int* K) {
   switch (form) {
     case WF_CONV3_FWD: *N = cout; *K = 9 * cin; break;
     case WF_CONV3_DGRAD: *N = cin; *K = 9 * cout; break;
@@ -605,7 +668,7 @@ __global__ void wunform_kernel(int form, int cin, int cout, int N, int K,
 cudaError_t launch_weight_form(int form, int cin, int cout, const float* src, float* dst_f32,
                                void* dst_bf16, void* dst_f16, cudaStream_t st) {
   int N, K;
-  wform_dims(form, cin, cout, &N, &K);
+  weight_form_dims(form, cin, cout, &N, &K);
   const long long tot = (long long)N * K;
   const int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
   wform_kernel<<<blocks, 256, 0, st>>>(form, cin, cout, N, K, src, dst_f32,
@@ -616,7 +679,7 @@ cudaError_t launch_weight_form(int form, int cin, int cout, const float* src, fl
 cudaError_t launch_weight_unform_scaled(int form, int cin, int cout, const float* g, float scale,
                                         float* dst, cudaStream_t st) {
   int N, K;
-  wform_dims(form, cin, cout, &N, &K);
+  weight_form_dims(form, cin, cout, &N, &K);
   const long long tot = (long long)N * K;
   const int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
   wunform_kernel<<<blocks, 256, 0, st>>>(form, cin, cout, N, K, g, scale, dst);
@@ -714,6 +777,97 @@ cudaError_t launch_adam(long long n, float* p, const float* g, float* m, float* 
   const float c2 = (float)(1.0 - pow((double)b2, (double)t));
   const int blocks = (int)std::min<long long>((n + 255) / 256, 2048);
   adam_kernel<<<blocks, 256, 0, st>>>(n, p, g, m, v, lr, b1, b2, eps, c1, c2);
+  return cudaGetLastError();
+}
+
+}  // namespace ideq
+
+// ===================================================================== FP8 forms
+
+#include <cuda_fp8.h>
+
+namespace ideq {
+
+constexpr float kE4M3Max = 448.f;  // largest finite e4m3 value
+
+IDEQ_DEV uint8_t to_e4m3(float v) {
+  return (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+}
+
+// One block per output column n: s[n] = max_k |w[n][k]| / 448 and the row in e4m3
+// (round to nearest even, saturating).  An all-zero row gets s = 1.
+__global__ void __launch_bounds__(256) weight_fp8_kernel(const float* __restrict__ w, int K,
+                                                         uint8_t* __restrict__ w8,
+                                                         float* __restrict__ scale) {
+  __shared__ float red[32];
+  const int n = blockIdx.x;
+  const float* row = w + (size_t)n * K;
+  float m = 0.f;
+  for (int k = threadIdx.x; k < K; k += 256) m = fmaxf(m, fabsf(row[k]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float t = threadIdx.x < 8 ? red[threadIdx.x] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t = fmaxf(t, __shfl_xor_sync(0xffffffffu, t, o));
+    if (threadIdx.x == 0) red[0] = t;
+  }
+  __syncthreads();
+  const float s = red[0] > 0.f ? red[0] / kE4M3Max : 1.f;
+  for (int k = threadIdx.x; k < K; k += 256) w8[(size_t)n * K + k] = to_e4m3(row[k] / s);
+  if (threadIdx.x == 0) scale[n] = s;
+}
+
+cudaError_t launch_weight_fp8(const float* w32, int N, int K, uint8_t* w8, float* scale,
+                              cudaStream_t st) {
+  weight_fp8_kernel<<<N, 256, 0, st>>>(w32, K, w8, scale);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) act_amax_kernel(const T* __restrict__ x, long long n,
+                                                       float* __restrict__ amax) {
+  float m = 0.f;
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256)
+    m = fmaxf(m, fabsf(ld_f(x + i)));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  // non-negative floats order like their bit patterns read as ints
+  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax((int*)amax, __float_as_int(m));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) act_fp8_kernel(const T* __restrict__ x, long long n,
+                                                      const float* __restrict__ amax,
+                                                      uint8_t* __restrict__ x8,
+                                                      float* __restrict__ scale) {
+  const float a = *amax;
+  const float s = a > 0.f ? a / kE4M3Max : 1.f;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *scale = s;
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256)
+    x8[i] = to_e4m3(ld_f(x + i) / s);
+}
+
+static int elem_blocks(long long n) {
+  return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152 * 8));
+}
+
+cudaError_t launch_act_amax(const void* x, int dt, long long n, float* amax, cudaStream_t st) {
+  if (dt == DT_BF16)
+    act_amax_kernel<<<elem_blocks(n), 256, 0, st>>>((const __nv_bfloat16*)x, n, amax);
+  else
+    act_amax_kernel<<<elem_blocks(n), 256, 0, st>>>((const __half*)x, n, amax);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_act_fp8(const void* x, int dt, long long n, const float* amax, uint8_t* x8,
+                           float* scale, cudaStream_t st) {
+  if (dt == DT_BF16)
+    act_fp8_kernel<<<elem_blocks(n), 256, 0, st>>>((const __nv_bfloat16*)x, n, amax, x8, scale);
+  else
+    act_fp8_kernel<<<elem_blocks(n), 256, 0, st>>>((const __half*)x, n, amax, x8, scale);
   return cudaGetLastError();
 }
 

@@ -120,6 +120,25 @@ bool NetWeights::build(const ideq_net_desc& d, std::string* err) {
       *err = "cudaMalloc(weight forms) failed";
       return false;
     }
+    int N, K;
+    if (l.cin >= kFp8MinChannels) {
+      weight_form_dims(l.fwd_form, l.cin, l.cout, &N, &K);
+      l.fwd8 = (uint8_t*)al(l.numel);
+      l.fwd8s = (float*)al((size_t)N * 4);
+      if (!l.fwd8 || !l.fwd8s) {
+        *err = "cudaMalloc(weight forms) failed";
+        return false;
+      }
+    }
+    if (l.cout >= kFp8MinChannels) {
+      weight_form_dims(l.dg_form, l.cin, l.cout, &N, &K);
+      l.dg8 = (uint8_t*)al(l.numel);
+      l.dg8s = (float*)al((size_t)N * 4);
+      if (!l.dg8 || !l.dg8s) {
+        *err = "cudaMalloc(weight forms) failed";
+        return false;
+      }
+    }
   }
   return true;
 }
@@ -131,6 +150,15 @@ cudaError_t NetWeights::reform(cudaStream_t st) {
     if (e != cudaSuccess) return e;
     e = launch_weight_form(l.dg_form, l.cin, l.cout, master + l.off, l.dg32, l.dg16, l.dgh, st);
     if (e != cudaSuccess) return e;
+    int N, K;
+    if (l.fwd8) {
+      weight_form_dims(l.fwd_form, l.cin, l.cout, &N, &K);
+      if ((e = launch_weight_fp8(l.fwd32, N, K, l.fwd8, l.fwd8s, st)) != cudaSuccess) return e;
+    }
+    if (l.dg8) {
+      weight_form_dims(l.dg_form, l.cin, l.cout, &N, &K);
+      if ((e = launch_weight_fp8(l.dg32, N, K, l.dg8, l.dg8s, st)) != cudaSuccess) return e;
+    }
   }
   return cudaSuccess;
 }
@@ -200,16 +228,53 @@ struct Builder {
     a.aux1 = aux1;
     a.aux2 = aux2;
     a.sumsq = sumsq;
-    const int adt = P->prec == IDEQ_FP32 ? DT_F32 : (P->prec == IDEQ_FP16 ? DT_F16 : DT_BF16);
+    const int prec = P->prec;
+    const int adt = prec == IDEQ_FP32
+                        ? DT_F32
+                        : ((prec == IDEQ_FP16 || prec == IDEQ_FP16_FP8) ? DT_F16 : DT_BF16);
+    const bool fp8_form = prec == IDEQ_BF16_FP8 || prec == IDEQ_FP16_FP8;
     s.in_dt = in_nchw ? DT_F32 : adt;
     s.out_dt = out_nchw ? DT_F32 : adt;
-    if (adt != DT_F32 && !in_nchw && !out_nchw && tc_supported(a)) {
+    const uint8_t* w8 = dgrad ? L.dg8 : L.fwd8;
+    const float* w8s = dgrad ? L.dg8s : L.fwd8s;
+    bool use8 = fp8_form && !in_nchw && !out_nchw && w8 && cin >= kFp8MinChannels;
+    if (use8) {  // e4m3 operands: quantise the 16-bit input first
+      const long long in_px = mode == CM_DOWN ? 4LL * P->n * gh * gw : (long long)P->n * gh * gw;
+      s.quant_n = in_px * cin;
+      s.q_src = in;
+      s.q_dst = (uint8_t*)P->alloc((size_t)s.quant_n);
+      float* sc = (float*)P->alloc(8);
+      if (!s.q_dst || !sc) {
+        ok = false;
+        return;
+      }
+      s.q_amax = sc;
+      s.q_scale = sc + 1;
+      a.in = s.q_dst;
+      a.wB = w8;
+      a.a_scale = s.q_scale;
+      a.w_scale = w8s;
+      use8 = tc_supported(a, DT_FP8);
+      if (!use8) {
+        s.quant_n = 0;
+        a.in = in;
+        a.a_scale = a.w_scale = nullptr;
+      }
+    }
+    if (use8) {
+      std::string e;
+      s.tc = tc_plan_create(a, DT_FP8, adt, &e);
+      if (!s.tc) {
+        *err = e;
+        ok = false;
+      }
+    } else if (adt != DT_F32 && !in_nchw && !out_nchw && tc_supported(a)) {
       if (adt == DT_F16)
         a.wB = dgrad ? (const void*)L.dgh : (const void*)L.fwdh;
       else
         a.wB = dgrad ? (const void*)L.dg16 : (const void*)L.fwd16;
       std::string e;
-      s.tc = tc_plan_create(a, adt, &e);
+      s.tc = tc_plan_create(a, adt, adt, &e);
       if (!s.tc) {
         *err = e;
         ok = false;
@@ -422,6 +487,15 @@ cudaError_t run_steps(const std::vector<Step>& steps, int* err_flag, cudaStream_
                       Profiler* prof, long long* launches) {
   for (const Step& s : steps) {
     cudaError_t e;
+    if (s.quant_n > 0) {
+      if ((e = cudaMemsetAsync(s.q_amax, 0, sizeof(float), st)) != cudaSuccess) return e;
+      if ((e = launch_act_amax(s.q_src, s.in_dt, s.quant_n, s.q_amax, st)) != cudaSuccess)
+        return e;
+      if ((e = launch_act_fp8(s.q_src, s.in_dt, s.quant_n, s.q_amax, s.q_dst, s.q_scale, st)) !=
+          cudaSuccess)
+        return e;
+      if (launches) *launches += 2;
+    }
     if (s.tc) {
       const bool p = prof && prof->on;
       if (p) cudaEventRecord(prof->next(), st);

@@ -24,7 +24,15 @@ struct Layer {
   __nv_bfloat16* dg16 = nullptr;
   __half* fwdh = nullptr;          // f16 forms
   __half* dgh = nullptr;
+  // e4m3 forms with per-row (output column) scales, for the directions whose
+  // input has >= 256 channels (forward: cin, input gradient: cout)
+  uint8_t* fwd8 = nullptr;
+  float* fwd8s = nullptr;
+  uint8_t* dg8 = nullptr;
+  float* dg8s = nullptr;
 };
+
+constexpr int kFp8MinChannels = 256;  // convs with at least this many input channels
 
 // Flat weight vector + its GEMM forms (f32, bf16, f16; forward and input-gradient).
 struct NetWeights {
@@ -48,6 +56,14 @@ struct Step {
   int in_dt = 0, out_dt = 0;  // DT_* of the NHWC/NCHW input and output
   TcPlan* tc = nullptr;
   bool edge = false;  // image-side <-> feature-side kernel
+  // FP8 convs (quant_n > 0): the 16-bit input q_src is first reduced to its
+  // max |x| (q_amax) and quantised to e4m3 codes (q_dst, the conv's input) with
+  // the scale q_scale that the conv's epilogue multiplies back
+  long long quant_n = 0;
+  const void* q_src = nullptr;
+  uint8_t* q_dst = nullptr;
+  float* q_amax = nullptr;
+  float* q_scale = nullptr;
 };
 
 // Execution plan for one (n, H, W, precision): activation buffers and the

@@ -85,7 +85,7 @@ struct TB {
       else
         a.wB = dgrad ? (const void*)L.dg16 : (const void*)L.fwd16;
       std::string e;
-      s.tc = tc_plan_create(a, adt, &e);
+      s.tc = tc_plan_create(a, adt, adt, &e);
       if (!s.tc) {
         *err = e;
         ok = false;
@@ -125,7 +125,10 @@ bool TrainPlan::build(NetWeights* wts, int n_, int H_, int W_, int prec_, double
   prec = prec_;
   gsum = gsum_;
   const ideq_net_desc& d = wts->desc;
-  const int adt = prec == IDEQ_FP32 ? DT_F32 : (prec == IDEQ_FP16 ? DT_F16 : DT_BF16);
+  // training runs the 16-bit form of the FP8 precisions
+  const int adt = prec == IDEQ_FP32
+                      ? DT_F32
+                      : ((prec == IDEQ_FP16 || prec == IDEQ_FP16_FP8) ? DT_F16 : DT_BF16);
   TB B{this, err, true, adt == DT_F32 ? 4 : 2, adt};
   const size_t img = (size_t)n * c * H * W * 4;
   z = (float*)alloc(img);

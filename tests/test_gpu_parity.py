@@ -181,6 +181,50 @@ def test_solve_unet_fp32(name):
     assert abs(infos2[0]["iters"] - it) <= 1
 
 
+@pytest.mark.parametrize("name,n,h,w", [("C0", 1, 64, 64), ("C0", 3, 40, 56)])
+def test_solve_averaging_step_fp32(name, n, h, w):
+    """Averaging step of Algorithm 1 over a fixed run of 50 updates: the same K0
+    as the oracle (or, where FP32 iterates reorder two step norms closer than
+    1e-4 relative, a K0 the oracle ranks as tied) and x_hat within 1e-5 of the
+    oracle's average of z^0 .. z^K0 for that K0."""
+    cfg, wl, net, ops, ys = setup(name, n=n, h=h, w=w)
+    b = B()
+    x0 = np.stack([ops[i].AT(ys[i].astype(np.float64)) for i in range(n)])
+    outs = [solver.solve_image(net, ops[i], ys[i].astype(np.float64), x0[i], cfg["lam"],
+                               cfg["tau"], cfg["beta"], math.inf, 0.0, 50, keep_history=True,
+                               average=True) for i in range(n)]
+    ctx = ctx_for(cfg, wl, b.IDEQ_FP32)
+    params = b.make_params(cfg["lam"], cfg["tau"], cfg["beta"], max_iter=50, average=True)
+    info = b.InfoBuffers(n)
+    x, st = b.ideq_solve(ctx, op_for(cfg, wl), torch.tensor(ys, device="cuda"), params,
+                         info=info, allow_maxiter=True)
+    xg = to_np(x)
+    for i in range(n):
+        xo, inf = outs[i]
+        k0 = int(info.k0[i])
+        assert 25 < k0 < 49
+        if k0 != inf["K0"]:
+            s = inf["step_hist"]
+            assert abs(s[k0] - s[inf["K0"]]) < 1e-4 * s[inf["K0"]]
+            xo = np.mean(np.stack(inf["z_hist"][:k0 + 1]), axis=0)
+        assert rel(xg[i], xo) < 1e-5
+
+
+def test_solve_averaging_rejects_runs_it_does_not_define():
+    cfg, wl, net, ops, ys = setup("C0")
+    b = B()
+    ctx = ctx_for(cfg, wl, b.IDEQ_FP32)
+    y = torch.tensor(ys, device="cuda")
+    for kw in (dict(tol=1e-4), dict(B=0.5), dict(max_iter=4)):
+        p = dict(B=math.inf, tol=0.0, max_iter=50)
+        p.update(kw)
+        params = b.make_params(cfg["lam"], cfg["tau"], cfg["beta"], p["B"], p["tol"],
+                               p["max_iter"], average=True)
+        with pytest.raises(b.IdeqError) as e:
+            b.ideq_solve(ctx, op_for(cfg, wl), y, params, allow_maxiter=True)
+        assert e.value.status == b.IDEQ_ERR_ARG
+
+
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
 def test_solve_unet_half_precision_matches_fp64_within_stated_error(prec):
     """FP16 convolutions reach the stopping residual 1e-4; BF16 convolutions stall

@@ -501,3 +501,60 @@ def test_workload_is_deterministic_and_shaped():
     assert a["kern"].shape == (2, 25, 25)
     assert abs(float(a["kern"][0].sum()) - 1.0) < 1e-5
     assert a["x_true"].min() >= 0 and a["x_true"].max() <= 1
+
+
+def fourier_heavy_ball_average(Kf, Yf, X0f, lam, tau, beta, K, hw):
+    """Averaging step of Algorithm 1 in the Fourier domain (N == 0, circular blur,
+    no restart): run K updates keeping Z_k and the step norms, K0 = first
+    minimiser of the step over floor(K/2) < k < K-1, x_hat = mean(Z_0..Z_K0)."""
+    q = 1.0 - tau * (np.abs(Kf) ** 2 + lam)
+    b = tau * np.conj(Kf) * Yf
+    X, Xp = X0f.copy(), X0f.copy()
+    Zs, steps = [], []
+    for _ in range(K):
+        Z = X + beta * (X - Xp)
+        Xn = q * Z + b
+        Zs.append(Z)
+        steps.append(math.sqrt(float(np.sum(np.abs(Xn - X) ** 2)) / hw))
+        Xp, X = X, Xn
+    best = None
+    for k in range(K // 2 + 1, K - 1):
+        if best is None or steps[k] < steps[best]:
+            best = k
+    return sum(Zs[:best + 1]) / (best + 1), best
+
+
+@pytest.mark.parametrize("K,beta", [(5, 0.8), (12, 0.8), (40, 0.5), (41, 0.95)])
+def test_averaging_step_matches_fourier_closed_form(K, beta):
+    """x_hat of the averaging step (Algorithm 1) against an independent per-frequency
+    run: same K0 and the same average of the extrapolated points z^k."""
+    net = zero_tail_unet()
+    h = w = 16
+    k = G.motion_kernel(21, 7).astype(np.float64)
+    op = operators.Operator("blur", kern=k)
+    x_true = G.synth_image(5, 1, h, w).astype(np.float64)
+    y = op.A(x_true) + 0.02 * rnd(1, h, w)
+    x0 = op.AT(y)
+    lam, tau = 0.1, 0.75
+    x, info = solver.solve_image(net, op, y, x0, lam, tau, beta, math.inf, 0.0, K, average=True)
+    kp = np.zeros((h, w))
+    kp[:7, :7] = k
+    kp = np.roll(kp, (-3, -3), axis=(0, 1))
+    Kf = np.fft.fft2(kp)
+    Xa, K0 = fourier_heavy_ball_average(Kf, np.fft.fft2(y[0]), np.fft.fft2(x0[0]), lam, tau,
+                                        beta, K, h * w)
+    assert info["K0"] == K0 and K // 2 < K0 < K - 1
+    np.testing.assert_allclose(x[0], np.real(np.fft.ifft2(Xa)), atol=1e-11)
+
+
+def test_averaging_step_of_a_constant_sequence_is_that_point():
+    """At a fixed point every z^k is that point, so is their average; K0 is the
+    first minimiser inside floor(K/2) < k < K-1; the window is empty below K = 5."""
+    zs = [np.full((2, 3), 0.25)] * 7
+    x, K0 = solver.averaging_step(zs, [1.0, 0.5, 0.4, 0.3, 0.3, 0.2, 0.1])
+    assert K0 == 5  # window {4, 5}; k = 6 (the last step, 0.1) is outside it
+    np.testing.assert_array_equal(x, zs[0])
+    _, K0 = solver.averaging_step(zs, [1.0, 0.5, 0.4, 0.3, 0.2, 0.2, 0.1])
+    assert K0 == 4  # tie: the first minimiser
+    with pytest.raises(ValueError):
+        solver.averaging_step(zs[:4], [1.0, 0.5, 0.4, 0.3])
