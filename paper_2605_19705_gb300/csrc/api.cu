@@ -2,7 +2,9 @@
 // single step and full inertial solve (Algorithm 1).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -45,6 +47,26 @@ struct ideq_ctx {
   // scratch for the stand-alone operator calls
   float* scratch = nullptr;
   size_t scratch_bytes = 0;
+  // Device-driven solve loop: one CUDA graph whose while node repeats two
+  // iterations (body captured once) for as long as an image is running, so the
+  // solve needs no host round trip per iteration.  Rebuilt when the plan, the
+  // operator, y or the parameters change; a graph that cannot be built falls back
+  // to the host-driven loop.
+  struct SolveGraph {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const void* plan = nullptr;
+    OpDev od{};
+    const float* y = nullptr;
+    ideq_params p{};
+    long long body_launches = 0;
+  } sg;
+  bool graph_ok = true;  // false once building a graph failed in this context
+  void drop_graph() {
+    if (sg.exec) cudaGraphExecDestroy(sg.exec);
+    if (sg.g) cudaGraphDestroy(sg.g);
+    sg = SolveGraph{};
+  }
 };
 
 namespace {
@@ -101,6 +123,7 @@ ideq_status ensure_plan(ideq_ctx* ctx, const ideq_shape& s) {
   NetPlan* p = ctx->plan.get();
   if (p && p->n == s.n && p->H == s.h && p->W == s.w && p->prec == ctx->precision) return IDEQ_OK;
   CK(cudaStreamSynchronize(ctx->stream));
+  ctx->drop_graph();
   ctx->plan.reset();
   ctx->train.reset();
   ctx->warm_plan.reset();
@@ -152,6 +175,7 @@ ideq_status ensure_plan(ideq_ctx* ctx, const ideq_shape& s) {
   v.part_s = (double*)(m + o_p);
   v.part_x = v.part_s + (size_t)n * nblk;
   v.n_running = (int*)(m + o_r);
+  v.loop_count = v.n_running + 1;
   ctx->dot_part = (double*)(m + o_dp);
   ctx->ubuf = (float*)(m + o_u);
   ctx->fsum = v.fsum;
@@ -225,6 +249,100 @@ ideq_status iterate(ideq_ctx* ctx, const OpDev& od, const ideq_shape& s, const f
                      p->lambda, logic, avg_K, st));
   ctx->launches += 3;
   return IDEQ_OK;
+}
+
+// IDEQ_SOLVE_GRAPH=0 drives every iteration from the host (for comparisons).
+bool graph_enabled() {
+  static const bool on = [] {
+    const char* v = std::getenv("IDEQ_SOLVE_GRAPH");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
+
+bool same_op(const OpDev& a, const OpDev& b) {
+  return a.kind == b.kind && a.kh == b.kh && a.kw == b.kw && a.kernel == b.kernel &&
+         a.mask == b.mask && a.gain == b.gain;
+}
+
+bool same_params(const ideq_params& a, const ideq_params& b) {
+  return a.lambda == b.lambda && a.tau == b.tau && a.beta == b.beta &&
+         a.restart_B == b.restart_B && a.tol == b.tol && a.max_iter == b.max_iter &&
+         a.average == b.average;
+}
+
+// Build the solve graph for (plan, operator, y, params): a kernel setting the
+// while condition from the solver state, then a while node whose body is two
+// iterations (parities 0 and 1) and the condition update.  Returns false (and
+// leaves no graph and the stream out of capture) when the runtime refuses any
+// step; the caller then drives the loop from the host.
+bool build_solve_graph(ideq_ctx* ctx, const OpDev& od, const ideq_shape& s, const float* y,
+                       const ideq_params* p) {
+  ctx->drop_graph();
+  cudaStream_t st = ctx->stream;
+  cudaGraph_t g = nullptr;
+  cudaGraphConditionalHandle h;
+  bool capturing = false;
+  auto give_up = [&]() {
+    if (capturing) {
+      cudaGraph_t junk = nullptr;
+      cudaStreamEndCapture(st, &junk);
+      if (junk && junk != g) cudaGraphDestroy(junk);
+    }
+    if (g) cudaGraphDestroy(g);
+    (void)cudaGetLastError();
+    ctx->graph_ok = false;
+    return false;
+  };
+  if (cudaGraphCreate(&g, 0) != cudaSuccess) return give_up();
+  if (cudaGraphConditionalHandleCreate(&h, g, 0, 0) != cudaSuccess) return give_up();
+  if (cudaStreamBeginCaptureToGraph(st, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) !=
+      cudaSuccess)
+    return give_up();
+  capturing = true;
+  // bodies needed: (max_iter - 2) / 2 rounded up, plus one spare
+  const int max_bodies = (p->max_iter - 2 + 1) / 2 + 1;
+  if (launch_loop_cond(h, ctx->sv.n_running, ctx->sv.loop_count, 1, max_bodies, ctx->d_err, st) !=
+      cudaSuccess)
+    return give_up();
+  capturing = false;
+  if (cudaStreamEndCapture(st, &g) != cudaSuccess) return give_up();
+  size_t nn = 0;
+  if (cudaGraphGetNodes(g, nullptr, &nn) != cudaSuccess || nn != 1) return give_up();
+  cudaGraphNode_t first;
+  if (cudaGraphGetNodes(g, &first, &nn) != cudaSuccess) return give_up();
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  if (cudaGraphAddNode(&wnode, g, &first, nullptr, 1, &cp) != cudaSuccess) return give_up();
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  if (cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0,
+                                    cudaStreamCaptureModeRelaxed) != cudaSuccess)
+    return give_up();
+  capturing = true;
+  const long long l0 = ctx->launches;
+  for (int par = 0; par < 2; ++par)
+    if (iterate(ctx, od, s, y, p, par, 1, p->average != 0) != IDEQ_OK) return give_up();
+  if (launch_loop_cond(h, ctx->sv.n_running, ctx->sv.loop_count, 0, max_bodies, ctx->d_err,
+                       st) != cudaSuccess)
+    return give_up();
+  const long long body_launches = ctx->launches - l0 + 1;
+  ctx->launches = l0;
+  capturing = false;
+  if (cudaStreamEndCapture(st, &body) != cudaSuccess) return give_up();
+  cudaGraphExec_t exec = nullptr;
+  if (cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) return give_up();
+  ctx->sg.g = g;
+  ctx->sg.exec = exec;
+  ctx->sg.plan = ctx->plan.get();
+  ctx->sg.od = od;
+  ctx->sg.y = y;
+  ctx->sg.p = *p;
+  ctx->sg.body_launches = body_launches;
+  return true;
 }
 
 ideq_status check_timeout(ideq_ctx* ctx) {
@@ -322,6 +440,7 @@ ideq_status ideq_destroy(ideq_ctx* ctx) {
   clear_stale_cuda_error();
   if (!ctx) return IDEQ_ERR_ARG;
   cudaStreamSynchronize(ctx->stream);
+  ctx->drop_graph();
   ctx->plan.reset();
   ctx->train.reset();
   ctx->warm_plan.reset();
@@ -461,13 +580,37 @@ ideq_status ideq_solve(ideq_ctx* ctx, const ideq_operator* op, ideq_shape shape,
   CK(cudaMemcpyAsync(ctx->xb[1], ctx->xb[0], bytes, cudaMemcpyDeviceToDevice, st));
   CK(launch_solver_init(shape.n, ctx->sv, 0.f, st));  // x^{-1} = x^0
   if (p->average) CK(cudaMemsetAsync(ctx->sv.zsum, 0, 2 * bytes, st));
+  // the first two iterations run from the host (they also complete every lazy
+  // kernel set-up), the rest in the device-driven graph unless that is off,
+  // failed, or the profiler is recording per-launch events
+  const bool avg = p->average != 0;
+  const bool use_graph = ctx->graph_ok && !ctx->prof.on && graph_enabled();
+  const int eager = use_graph ? std::min(2, p->max_iter) : p->max_iter;
   const int poll = p->tol > 0.0 ? 2 : 0;
-  for (int it = 0; it < p->max_iter; ++it) {
-    if ((s = iterate(ctx, od, shape, y, p, it & 1, 1, p->average != 0)) != IDEQ_OK) return s;
-    if (poll && ((it + 1) % poll == 0) && it + 1 < p->max_iter) {
+  bool graphed = false;
+  for (int it = 0; it < eager; ++it) {
+    if ((s = iterate(ctx, od, shape, y, p, it & 1, 1, avg)) != IDEQ_OK) return s;
+    if (!use_graph && poll && ((it + 1) % poll == 0) && it + 1 < p->max_iter) {
       CK(cudaMemcpyAsync(ctx->h_running, ctx->sv.n_running, 4, cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       if (*ctx->h_running == 0) break;
+    }
+  }
+  if (use_graph && eager < p->max_iter) {
+    const bool have = ctx->sg.exec && ctx->sg.plan == ctx->plan.get() && same_op(ctx->sg.od, od) &&
+                      ctx->sg.y == y && same_params(ctx->sg.p, *p);
+    if (have || build_solve_graph(ctx, od, shape, y, p)) {
+      CK(cudaGraphLaunch(ctx->sg.exec, st));
+      graphed = true;
+    } else {  // no graph: finish from the host
+      for (int it = eager; it < p->max_iter; ++it) {
+        if ((s = iterate(ctx, od, shape, y, p, it & 1, 1, avg)) != IDEQ_OK) return s;
+        if (poll && ((it + 1) % poll == 0) && it + 1 < p->max_iter) {
+          CK(cudaMemcpyAsync(ctx->h_running, ctx->sv.n_running, 4, cudaMemcpyDeviceToHost, st));
+          CK(cudaStreamSynchronize(st));
+          if (*ctx->h_running == 0) break;
+        }
+      }
     }
   }
   CK(launch_gather_parity(shape.n, ctx->sv_per, ctx->sv.parity, ctx->xb[0], ctx->xb[1], x_out, st));
@@ -479,8 +622,13 @@ ideq_status ideq_solve(ideq_ctx* ctx, const ideq_operator* op, ideq_shape shape,
   if (info) CK(launch_fill_info(shape.n, ctx->sv, *info, st));
   if ((s = check_timeout(ctx)) != IDEQ_OK) return s;
   // overall status (stream already synchronised by check_timeout)
-  std::vector<int> hs(shape.n);
+  std::vector<int> hs(shape.n), ht(shape.n);
   CK(cudaMemcpy(hs.data(), ctx->sv.status, shape.n * 4, cudaMemcpyDeviceToHost));
+  if (graphed) {  // launches the graph ran: one condition kernel, then bodies of two iterations
+    CK(cudaMemcpy(ht.data(), ctx->sv.total, shape.n * 4, cudaMemcpyDeviceToHost));
+    const int last = *std::max_element(ht.begin(), ht.end());
+    ctx->launches += 1 + (long long)std::max(0, (last - 2 + 1) / 2) * ctx->sg.body_launches;
+  }
   bool div = false, maxit = false;
   for (int v : hs) {
     div |= v == IDEQ_IMG_DIVERGED;

@@ -52,6 +52,11 @@ struct TcArgs {
   const float* a_scale;  // FP8 operands: activation scale (device scalar)
   const float* w_scale;  // FP8 operands: weight scale per GEMM column
   int slide;             // halo form: contiguous row runs per CTA reusing row boxes
+  // image-side output (BN = 16): out = aux + sign * acc, f32 planar, c <= 16 channels
+  float sign;
+  const float* img_aux;
+  float* img_out;
+  double* sumsq;
   int* err;
 };
 
@@ -239,6 +244,22 @@ IDEQ_DEV void tmem_ld32(uint32_t taddr, float (&v)[32]) {
       : "memory");
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 16 consecutive f32 accumulator columns of this warp's 32 TMEM lanes.
+IDEQ_DEV void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 IDEQ_DEV void mbar_arrive(uint32_t bar) {
@@ -486,12 +507,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                    const __grid_constant__ CUtensorMap tmX2, TcArgs a) {
   static_assert(!HALO || MS == 1, "the halo form has one 128-row sub-tile");
   constexpr int B_BYTES = BN * 128;
-  constexpr int A_STAGE = HALO ? HALO_BOX : MS * A_BYTES;  // ring slot: one row box (HALO)
-  constexpr uint32_t STAGE_TX = HALO ? HALO_ROWS * 128u : (uint32_t)(MS * A_BYTES + B_BYTES);
-  constexpr int NPANEL = BN / 64;
+  // ring slot: the A (and B) boxes of one K chunk; in the halo form the three row
+  // boxes of a tile, or a single row box in the sliding form
+  const int A_STAGE = HALO ? (a.slide ? HALO_BOX : 3 * HALO_BOX) : MS * A_BYTES;
+  const uint32_t STAGE_TX =
+      HALO ? (a.slide ? 1u : 3u) * HALO_ROWS * 128u : (uint32_t)(MS * A_BYTES + B_BYTES);
+  constexpr bool IMG = BN == 16;  // image-side output: c <= 16 planar f32 channels
+  constexpr int NPANEL = IMG ? 1 : BN / 64;
   constexpr int KCH = 128 / (int)sizeof(TA);  // K elements per 128-byte ring row
   static_assert(!HALO || sizeof(TA) == 2, "the halo form has 16-bit operands");
-  constexpr int TCOLS = MS * BN;  // TMEM columns of one accumulator buffer
+  constexpr int TCOLS = MS * BN;  // TMEM columns of one accumulator buffer (2 x >= 32 allocated)
   const int ST = a.stages;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -561,16 +586,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
       int g = 0;  // ring position across tiles (row boxes in the halo form)
       bool ok = true;
-      if constexpr (HALO) {
+      if (HALO && !a.slide) {  // one slot of three row boxes per tile
+        for (int i = 0; i < my_tiles && ok; ++i) {
+          const TileCoord tc = halo_coord(a, t_first + i * t_step);
+          const int s = g % ST, j = g / ST;
+          if (j > 0 && !mbar_wait(empty0 + 8 * s, (j - 1) & 1, a.err, 1)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(full0 + 8 * s, STAGE_TX);
+          for (int dy = 0; dy < 3; ++dy)
+            tma_load_4d(smem_u32(sA + s * A_STAGE + dy * HALO_BOX), &tmA, 0, tc.w0 - 1,
+                        tc.h0 + dy - 1, tc.img, full0 + 8 * s);
+          ++g;
+        }
+      } else if (HALO) {  // sliding: single row boxes, reused across consecutive rows
         for (int i = 0; i < my_tiles && ok; ++i) {
           const int t = t_first + i * t_step;
           const TileCoord tc = halo_coord(a, t);
-          const bool fresh = !a.slide || i == 0 || t % a.tiles_h == 0;  // three new boxes
+          const bool fresh = i == 0 || t % a.tiles_h == 0;  // three new boxes
           // rows loaded a few tiles from now are pulled into L2 first: each row is
           // read by this CTA alone, so its load would otherwise wait on DRAM
-          if (a.slide)
-            for (int r = fresh ? 2 : HALO_PF + 1; r <= HALO_PF + 1; ++r)
-              if (tc.h0 + r < a.H) tma_prefetch_4d(&tmA, 0, tc.w0 - 1, tc.h0 + r, tc.img);
+          for (int r = fresh ? 2 : HALO_PF + 1; r <= HALO_PF + 1; ++r)
+            if (tc.h0 + r < a.H) tma_prefetch_4d(&tmA, 0, tc.w0 - 1, tc.h0 + r, tc.img);
           for (int dy = fresh ? -1 : 1; dy <= 1; ++dy) {
             const int s = g % ST, j = g / ST;
             if (j > 0 && !mbar_wait(empty0 + 8 * s, (j - 1) & 1, a.err, 1)) {
@@ -645,8 +683,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         tc_fence_after();
         const uint32_t td = tmem + (uint32_t)(b * TCOLS);
-        if constexpr (HALO) {
-          const bool fresh = !a.slide || lt == 0 || t % a.tiles_h == 0;
+        if (HALO && !a.slide) {
+          const int s = g % ST, j = g / ST;
+          if (!mbar_wait(full0 + 8 * s, j & 1, a.err, 3)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t abase = smem_u32(sA + s * A_STAGE);
+#pragma unroll 1
+          for (int tap = 0; tap < 9; ++tap) {
+            const int dy = tap / 3, dx = tap - 3 * dy;
+            const uint64_t ad = umma_desc_sw128_rows(abase + dy * HALO_BOX, dx);
+            const uint64_t bd = umma_desc_sw128(smem_u32(sB + tap * B_BYTES));
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+              umma<TA>(td, ad + 2 * kk, bd + 2 * kk, idesc, (tap | kk) != 0 ? 1u : 0u);
+          }
+          umma_commit(empty0 + 8 * s);
+          umma_commit(tfull0 + 8 * b);
+          ++g;
+        } else if (HALO) {
+          const bool fresh = lt == 0 || t % a.tiles_h == 0;
           if (fresh) {
             base = g;
             g += 3;
@@ -673,7 +731,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           umma_commit(tfull0 + 8 * b);
           // release the boxes the next tile does not read: row y-1, or all three
           // when the next tile starts a new strip run (or there is none)
-          const bool next_fresh = !a.slide || lt + 1 == my_tiles || (t + 1) % a.tiles_h == 0;
+          const bool next_fresh = lt + 1 == my_tiles || (t + 1) % a.tiles_h == 0;
           for (int dy = 0; dy < (next_fresh ? 3 : 1); ++dy)
             umma_commit(empty0 + 8 * ((base + dy) % ST));
         } else {
@@ -702,6 +760,51 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (!ok) {  // let every issued MMA finish before TMEM is released
         umma_commit(drain);
         mbar_wait(drain, 0, a.err, 6);
+      }
+    }
+  } else if constexpr (IMG) {
+    // ---------------- image-side epilogue: the four warps of the first half own
+    // one TMEM quadrant each (one pixel row per lane), read the c valid columns
+    // and write out = aux + sign * acc to the f32 planar image, adding 1/2 out^2
+    // to the image's sum; the other four only hand the accumulator back.
+    const int e = warp - 2, q = warp & 3, half = e >> 2;
+    bool ok = true;
+    for (int lt = 0; lt < my_tiles && ok; ++lt) {
+      const int t = t_first + lt * t_step;
+      const int b = lt & 1, u = lt >> 1;
+      ok = __all_sync(0xffffffffu, mbar_wait(tfull0 + 8 * b, u & 1, a.err, 4));
+      if (!ok) break;
+      tc_fence_after();
+      if (half == 0) {
+        float v[16];
+        tmem_ld16(tmem + (uint32_t)(b * TCOLS) + ((uint32_t)(q * 32) << 16), v);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty0 + 8 * b);
+        const TileCoord tc = HALO ? halo_coord(a, t) : tile_coord(a, t, BN, MS, 0);
+        const int m = 32 * q + lane;
+        const int x = tc.w0 + m % a.Wt, y = tc.h0 + m / a.Wt;
+        double ssq = 0.0;
+        if (tc.img < a.n && x < a.W && y < a.H) {
+#pragma unroll
+          for (int o = 0; o < 16; ++o) {
+            if (o < a.Cout) {
+              const size_t idx = (((size_t)tc.img * a.Cout + o) * a.H + y) * a.W + x;
+              const float r = a.img_aux[idx] + a.sign * v[o];
+              a.img_out[idx] = r;
+              ssq += 0.5 * (double)r * (double)r;
+            }
+          }
+        }
+        if (a.sumsq) {
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) ssq += __shfl_xor_sync(0xffffffffu, ssq, off);
+          if (lane == 0 && tc.img < a.n) atomicAdd(a.sumsq + tc.img, ssq);
+        }
+      } else {
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty0 + 8 * b);
       }
     }
   } else {
@@ -813,6 +916,12 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 
 static int tiling_override(const char* name, int dflt);
 
+// image-side output: c <= 16 f32 planar channels out of a 16-bit NHWC input
+static bool image_side(const ConvArgs& a) {
+  return a.out_nchw && !a.in_nchw && a.epi == EP_AXPY_NCHW && a.mode == CM_CONV3 &&
+         a.outmap == OM_IDENT && a.Cout >= 1 && a.Cout <= 16;
+}
+
 static int pick_bn(int N) {
   // smallest N tiled 256 wide (measured: 256-wide tiles win from N = 256 up)
   const int n256 = tiling_override("IDEQ_TC_BN256_MIN", 256);
@@ -821,7 +930,10 @@ static int pick_bn(int N) {
   return 64;
 }
 
-static int epi_nout(int epi) { return (epi == EP_ACT || epi == EP_MUL_KEEP) ? 2 : 1; }
+static int epi_nout(int epi) {
+  if (epi == EP_AXPY_NCHW) return 0;  // written by the image-side epilogue, not staged
+  return (epi == EP_ACT || epi == EP_MUL_KEEP) ? 2 : 1;
+}
 static int epi_naux(int epi) {
   if (epi == EP_DUAL) return 3;
   if (epi == EP_ADD || epi == EP_MUL || epi == EP_MUL_KEEP) return 1;
@@ -831,6 +943,8 @@ static int epi_naux(int epi) {
 static int k_chunk(int op_dt) { return op_dt == DT_FP8 ? 128 : 64; }  // K per 128-B row
 
 bool tc_supported(const ConvArgs& a, int op_dt) {
+  if (image_side(a))  // weights padded to 16 rows [16][K] by the caller
+    return op_dt != DT_FP8 && a.Cin % 64 == 0 && a.aux0 && a.out;
   if (a.in_nchw || a.out_nchw || a.epi == EP_AXPY_NCHW) return false;
   if (a.Cin % k_chunk(op_dt) != 0) return false;
   if (op_dt == DT_FP8 && (!a.a_scale || !a.w_scale)) return false;
@@ -904,8 +1018,9 @@ TcPlan* tc_plan_create(const ConvArgs& a, int op_dt, int epi_dt, std::string* er
   p->op_dt = op_dt;
   p->epi_dt = epi_dt;
   const int KCH = k_chunk(op_dt);
-  const int N = a.N();
-  p->bn = pick_bn(N);
+  const bool img = image_side(a);
+  const int N = img ? 16 : a.N();  // image side: weight rows padded to 16
+  p->bn = img ? 16 : pick_bn(N);
   p->nout = epi_nout(a.epi);
   p->naux = epi_naux(a.epi);
   // M tile: Ht x Wt pixels of the grid, Wt a power of two
@@ -935,10 +1050,11 @@ TcPlan* tc_plan_create(const ConvArgs& a, int op_dt, int epi_dt, std::string* er
   // shared memory: ring depth and staging buffers, preferring a deep ring
   // (halo: >= 5 row boxes, three in use and two in flight; else >= 3 stages),
   // then double-buffered staging
-  const size_t stage = p->halo ? (size_t)HALO_BOX : (size_t)p->ms * A_BYTES + (size_t)p->bn * 128;
+  const size_t stage = p->halo ? (size_t)(p->slide ? 1 : 3) * HALO_BOX
+                               : (size_t)p->ms * A_BYTES + (size_t)p->bn * 128;
   const size_t resident = p->halo ? bres : 0;
   p->stages = 0;
-  const int min_stages[2] = {p->halo ? 5 : 3, p->halo ? 4 : 2};
+  const int min_stages[2] = {p->halo ? (p->slide ? 5 : 3) : 3, p->halo ? (p->slide ? 4 : 2) : 2};
   for (int min_st : min_stages) {
     for (int nbuf : {2, 1}) {
       int st = 8;
@@ -1005,10 +1121,15 @@ TcPlan* tc_plan_create(const ConvArgs& a, int op_dt, int epi_dt, std::string* er
   }
   const void* outs[2] = {a.out, a.out2};
   const void* auxs[3] = {a.aux0, a.aux1, a.aux2};
-  for (int i = 0; i < 2; ++i)
-    ok = ok && encode_epi(enc, &p->tmO[i], edt, a, p, i < p->nout ? outs[i] : a.out);
-  for (int i = 0; i < 3; ++i)
-    ok = ok && encode_epi(enc, &p->tmX[i], edt, a, p, i < p->naux ? auxs[i] : a.out);
+  if (img) {  // no staged epilogue tensors: copy the A map into the unused slots
+    for (int i = 0; i < 2; ++i) p->tmO[i] = p->tmA;
+    for (int i = 0; i < 3; ++i) p->tmX[i] = p->tmA;
+  } else {
+    for (int i = 0; i < 2; ++i)
+      ok = ok && encode_epi(enc, &p->tmO[i], edt, a, p, i < p->nout ? outs[i] : a.out);
+    for (int i = 0; i < 3; ++i)
+      ok = ok && encode_epi(enc, &p->tmX[i], edt, a, p, i < p->naux ? auxs[i] : a.out);
+  }
   if (!ok) {
     *err = "cuTensorMapEncodeTiled failed";
     delete p;
@@ -1042,6 +1163,10 @@ static cudaError_t launch_typed(const TcPlan* p, const TcArgs& t, cudaStream_t s
       case 128: return launch_bn<__nv_fp8_e4m3, T, 128, false, 1>(p, t, st);
       default: return launch_bn<__nv_fp8_e4m3, T, 256, false, 1>(p, t, st);
     }
+  }
+  if (p->bn == 16) {
+    if (p->halo) return launch_bn<T, T, 16, true, 1>(p, t, st);
+    return launch_bn<T, T, 16, false, 1>(p, t, st);
   }
   if (p->halo) {
     switch (p->bn) {
@@ -1087,6 +1212,10 @@ cudaError_t launch_conv_tc(const TcPlan* p, const ConvArgs& a, int* err_flag, cu
   t.nbo = p->nbo;
   t.nba = p->nba;
   t.slide = p->slide ? 1 : 0;
+  t.sign = a.sign;
+  t.img_aux = (const float*)a.aux0;
+  t.img_out = (float*)a.out;
+  t.sumsq = a.sumsq;
   t.a_scale = a.a_scale;
   t.w_scale = a.w_scale;
   t.err = err_flag;

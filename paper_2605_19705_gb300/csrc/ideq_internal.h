@@ -143,6 +143,7 @@ struct SolverDev {
   double* part_s;  // [n][nblk] partial sums of ||x_new - x||^2
   double* part_x;  // [n][nblk] partial sums of ||x||^2
   int* n_running;
+  int* loop_count;  // bodies run by the device-driven solve loop
   // averaging step of Algorithm 1 (used when the solve asks for it)
   double* best;    // smallest step norm inside the averaging window so far
   int* k0;         // its index K0 (-1: none)
@@ -170,6 +171,11 @@ cudaError_t launch_finalize(int n, int nblk, const SolverDev& s, int parity_new,
 cudaError_t launch_gather_parity(int n, int per_img, const int* parity, const float* b0,
                                  const float* b1, float* out, cudaStream_t st);
 cudaError_t launch_solver_init(int n, const SolverDev& s, float beta, cudaStream_t st);
+// Device-driven solve loop: set a graph's while-condition to (*n_running > 0).
+// `first` resets the body counter; a body past max_bodies stops the loop and
+// raises *err (code 10) instead.
+cudaError_t launch_loop_cond(cudaGraphConditionalHandle h, const int* n_running, int* counter,
+                             int first, int max_bodies, int* err, cudaStream_t st);
 cudaError_t launch_fill_info(int n, const SolverDev& s, ideq_info info, cudaStream_t st);
 int update_blocks_per_image(int per_img);
 

@@ -540,6 +540,23 @@ __global__ void solver_init_kernel(int n, SolverDev s, float beta) {
   if (b == 0) *s.n_running = n;
 }
 
+// Every image freezes by max_iter updates, so the loop ends by itself; the body
+// counter is a guard against a loop that would not (it then stops with an error).
+__global__ void loop_cond_kernel(cudaGraphConditionalHandle h, const int* n_running,
+                                 int* counter, int first, int max_bodies, int* err) {
+  const int c = first ? 0 : *counter + 1;
+  *counter = c;
+  const bool running = *n_running > 0;
+  if (running && c >= max_bodies) atomicCAS(err, 0, 10);
+  cudaGraphSetConditional(h, (running && c < max_bodies) ? 1u : 0u);
+}
+
+cudaError_t launch_loop_cond(cudaGraphConditionalHandle h, const int* n_running, int* counter,
+                             int first, int max_bodies, int* err, cudaStream_t st) {
+  loop_cond_kernel<<<1, 1, 0, st>>>(h, n_running, counter, first, max_bodies, err);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_solver_init(int n, const SolverDev& s, float beta, cudaStream_t st) {
   solver_init_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, s, beta);
   return cudaGetLastError();
@@ -826,12 +843,27 @@ cudaError_t launch_weight_fp8(const float* w32, int N, int K, uint8_t* w8, float
   return cudaGetLastError();
 }
 
+// 8 consecutive 16-bit values (one 16-byte load) as floats
+template <typename T>
+IDEQ_DEV void load8(const T* p, float (&v)[8]) {
+  const uint4 u = *(const uint4*)p;
+  const T* h = (const T*)&u;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = ld_f(h + i);
+}
+
+// n is a multiple of 8 (the channel count of every quantised tensor is)
 template <typename T>
 __global__ void __launch_bounds__(256) act_amax_kernel(const T* __restrict__ x, long long n,
                                                        float* __restrict__ amax) {
   float m = 0.f;
-  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256)
-    m = fmaxf(m, fabsf(ld_f(x + i)));
+  for (long long i = (blockIdx.x * 256LL + threadIdx.x) * 8; i < n;
+       i += (long long)gridDim.x * 256 * 8) {
+    float v[8];
+    load8(x + i, v);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) m = fmaxf(m, fabsf(v[j]));
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   // non-negative floats order like their bit patterns read as ints
@@ -846,15 +878,24 @@ __global__ void __launch_bounds__(256) act_fp8_kernel(const T* __restrict__ x, l
   const float a = *amax;
   const float s = a > 0.f ? a / kE4M3Max : 1.f;
   if (blockIdx.x == 0 && threadIdx.x == 0) *scale = s;
-  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256)
-    x8[i] = to_e4m3(ld_f(x + i) / s);
+  for (long long i = (blockIdx.x * 256LL + threadIdx.x) * 8; i < n;
+       i += (long long)gridDim.x * 256 * 8) {
+    float v[8];
+    load8(x + i, v);
+    uint2 q;
+    uint8_t* qb = (uint8_t*)&q;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) qb[j] = to_e4m3(v[j] / s);
+    *(uint2*)(x8 + i) = q;
+  }
 }
 
-static int elem_blocks(long long n) {
-  return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152 * 8));
+static int elem_blocks(long long n) {  // blocks of 256 threads, 8 values per thread
+  return (int)std::max<long long>(1, std::min<long long>((n / 8 + 255) / 256, 152 * 8));
 }
 
 cudaError_t launch_act_amax(const void* x, int dt, long long n, float* amax, cudaStream_t st) {
+  if (n % 8 != 0) return cudaErrorInvalidValue;
   if (dt == DT_BF16)
     act_amax_kernel<<<elem_blocks(n), 256, 0, st>>>((const __nv_bfloat16*)x, n, amax);
   else
@@ -864,6 +905,7 @@ cudaError_t launch_act_amax(const void* x, int dt, long long n, float* amax, cud
 
 cudaError_t launch_act_fp8(const void* x, int dt, long long n, const float* amax, uint8_t* x8,
                            float* scale, cudaStream_t st) {
+  if (n % 8 != 0) return cudaErrorInvalidValue;
   if (dt == DT_BF16)
     act_fp8_kernel<<<elem_blocks(n), 256, 0, st>>>((const __nv_bfloat16*)x, n, amax, x8, scale);
   else

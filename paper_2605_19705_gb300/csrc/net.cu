@@ -110,14 +110,27 @@ bool NetWeights::build(const ideq_net_desc& d, std::string* err) {
     return false;
   }
   for (auto& l : layers) {
+    // 16-bit forms keep at least 16 rows (zero rows past N): the tensor-core conv
+    // that writes c <= 16 image channels runs a 16-wide N tile
+    int Nf, Kf, Nd, Kd;
+    weight_form_dims(l.fwd_form, l.cin, l.cout, &Nf, &Kf);
+    weight_form_dims(l.dg_form, l.cin, l.cout, &Nd, &Kd);
+    const size_t f16n = (size_t)std::max(Nf, 16) * Kf, d16n = (size_t)std::max(Nd, 16) * Kd;
     l.fwd32 = (float*)al(l.numel * 4);
     l.dg32 = (float*)al(l.numel * 4);
-    l.fwd16 = (__nv_bfloat16*)al(l.numel * 2);
-    l.dg16 = (__nv_bfloat16*)al(l.numel * 2);
-    l.fwdh = (__half*)al(l.numel * 2);
-    l.dgh = (__half*)al(l.numel * 2);
+    l.fwd16 = (__nv_bfloat16*)al(f16n * 2);
+    l.dg16 = (__nv_bfloat16*)al(d16n * 2);
+    l.fwdh = (__half*)al(f16n * 2);
+    l.dgh = (__half*)al(d16n * 2);
     if (!l.fwd32 || !l.dg32 || !l.fwd16 || !l.dg16 || !l.fwdh || !l.dgh) {
       *err = "cudaMalloc(weight forms) failed";
+      return false;
+    }
+    if (cudaMemset(l.fwd16, 0, f16n * 2) != cudaSuccess ||
+        cudaMemset(l.dg16, 0, d16n * 2) != cudaSuccess ||
+        cudaMemset(l.fwdh, 0, f16n * 2) != cudaSuccess ||
+        cudaMemset(l.dgh, 0, d16n * 2) != cudaSuccess) {
+      *err = "cudaMemset(weight forms) failed";
       return false;
     }
     int N, K;
@@ -268,7 +281,7 @@ struct Builder {
         *err = e;
         ok = false;
       }
-    } else if (adt != DT_F32 && !in_nchw && !out_nchw && tc_supported(a)) {
+    } else if (adt != DT_F32 && !in_nchw && tc_supported(a)) {  // incl. feature -> image
       if (adt == DT_F16)
         a.wB = dgrad ? (const void*)L.dgh : (const void*)L.fwdh;
       else

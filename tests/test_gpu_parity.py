@@ -39,7 +39,8 @@ def B():
 
 
 PREC = {"fp32": lambda: B().IDEQ_FP32, "bf16": lambda: B().IDEQ_BF16,
-        "fp16": lambda: B().IDEQ_FP16}
+        "fp16": lambda: B().IDEQ_FP16, "fp16_fp8": lambda: B().IDEQ_FP16_FP8,
+        "bf16_fp8": lambda: B().IDEQ_BF16_FP8}
 
 
 # ---------------------------------------------------------------- operators
@@ -103,6 +104,11 @@ def test_operator_argument_errors():
     ("C1a", dict(n=1), "bf16", 1e-2),
     ("C1a", dict(n=1, h=136, w=200), "fp16", 2e-3),  # halo tiles with ragged row ends
     ("C3", dict(n=1, h=32, w=32), "fp32", 1e-5),
+    # e4m3 operands (unit roundoff 2^-4) on the 256- and 512-channel convs, averaged
+    # over K >= 1024 terms and damped by the 0.1 residual gains: measured 1.2e-2
+    ("C1a", dict(n=1, h=64, w=64), "fp16_fp8", 3e-2),
+    ("C1a", dict(n=1), "fp16_fp8", 3e-2),
+    ("C1a", dict(n=2, h=40, w=56), "bf16_fp8", 3e-2),
 ])
 def test_grad_reg_matches_oracle(name, over, prec, tol):
     cfg, wl, net, ops, ys = setup(name, **over)
@@ -210,6 +216,32 @@ def test_solve_averaging_step_fp32(name, n, h, w):
         assert rel(xg[i], xo) < 1e-5
 
 
+@pytest.mark.parametrize("tol,max_iter", [(1e-4, 400), (0.0, 37), (0.0, 3)])
+def test_device_driven_loop_matches_host_loop(tol, max_iter):
+    """The solve's CUDA graph (a while node repeating two iterations until no image
+    runs) gives the same iterates, counts and statuses as the host-driven loop
+    (forced here by recording per-launch profiler events)."""
+    cfg, wl, net, ops, ys = setup("C0", n=2, h=48, w=40)
+    b = B()
+    y = torch.tensor(ys, device="cuda")
+    out = []
+    for host in (False, True):
+        ctx = ctx_for(cfg, wl, b.IDEQ_FP32)
+        b.ideq_prof_enable(ctx, host)
+        params = b.make_params(cfg["lam"], cfg["tau"], cfg["beta"], tol=tol, max_iter=max_iter)
+        info = b.InfoBuffers(2)
+        op = op_for(cfg, wl)
+        for _ in range(2):  # the second solve reuses the graph built by the first
+            x, st = b.ideq_solve(ctx, op, y, params, info=info, allow_maxiter=True)
+        torch.cuda.synchronize()
+        out.append((to_np(x), info.iters.cpu().numpy(), info.status.cpu().numpy()))
+    (xg, ig, sg), (xh, ih, sh) = out
+    assert np.array_equal(ig, ih) and np.array_equal(sg, sh)
+    assert np.array_equal(xg, xh)
+    if tol == 0.0:
+        assert list(ig) == [max_iter, max_iter]
+
+
 def test_solve_averaging_rejects_runs_it_does_not_define():
     cfg, wl, net, ops, ys = setup("C0")
     b = B()
@@ -223,6 +255,19 @@ def test_solve_averaging_rejects_runs_it_does_not_define():
         with pytest.raises(b.IdeqError) as e:
             b.ideq_solve(ctx, op_for(cfg, wl), y, params, allow_maxiter=True)
         assert e.value.status == b.IDEQ_ERR_ARG
+
+
+@pytest.mark.parametrize("prec", ["fp16_fp8", "bf16_fp8"])
+def test_solve_unet_fp8_form_stated_error(prec):
+    """FP8 operands on the deep convs leave the relative step near 8e-4 (measured),
+    above the 1e-4 stopping residual, so the solve runs to max_iter; the iterate
+    still stays within 2e-2 of the FP64 fixed point and 0.05 dB of its PSNR."""
+    cfg, wl, net, ops, ys = setup("C2", n=1, h=64, w=64)
+    xo, infos = _oracle_solve(cfg, net, ops, ys, max_iter=300)
+    xg, info, st = _gpu_solve(cfg, wl, ys, PREC[prec](), max_iter=120)
+    assert float(info.rel_res[0]) < 5e-3
+    assert rel(xg, xo) < 2e-2
+    assert abs(solver.psnr(xo[0], wl["x_true"][0]) - solver.psnr(xg[0], wl["x_true"][0])) < 0.05
 
 
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
