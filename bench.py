@@ -30,8 +30,31 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "256² RGB restorations/s at matched PSNR (±0.05 dB), chosen form vs plain FP32"
-WORKLOAD = ("C1a: 8 x RGB 256x256, 25x25 random-walk motion blur, sigma 0.02, "
-            "U-Net 64/128/256/512 (17.0M params), lambda 0.1, tau 0.75, beta 0.8, tol 1e-4")
+WORKLOADS = {
+    "C1a": "C1a: 8 x RGB 256x256, 25x25 random-walk motion blur, sigma 0.02, "
+           "U-Net 64/128/256/512 (17.0M params), lambda 0.1, tau 0.75, beta 0.8, tol 1e-4",
+    "C1b": "C1b: 8 x RGB 256x256 inpainting (30% of pixels kept), sigma 0.02, "
+           "U-Net 64/128/256/512, lambda 0.1, tau 0.75, beta 0.8, tol 1e-4",
+    "C5": "C5: 4 x complex 256x256 MRI (x4 Cartesian undersampling, 8% centre), "
+          "k-space sigma 0.01, 2-channel U-Net 32/64/128/256, lambda 0.1, tau 0.75, beta 0.8, tol 1e-4",
+}
+WORKLOAD = WORKLOADS["C1a"]
+
+
+def make_op_and_y(B, cfg, wl, ctx, x_true, dev):
+    """The forward model of the workload and y = A(x*) + n formed on the device by
+    the library (inpainting: y = M(x* + n); MRI: y = M(F x* + n))."""
+    import torch
+    noise = torch.tensor(wl["noise"], device=dev)
+    if cfg["op"] == "mask":
+        op = B.make_operator(B.IDEQ_OP_MASK, None, torch.tensor(wl["mask"], device=dev))
+        return op, B.ideq_apply_A(ctx, op, x_true + noise)
+    if cfg["op"] == "mri":
+        m = torch.tensor(wl["mask"], device=dev)
+        op = B.make_operator(B.IDEQ_OP_MRI, None, m)
+        return op, B.ideq_apply_A(ctx, op, x_true) + noise * m[:, None].float()
+    op = B.make_operator(B.IDEQ_OP_BLUR, torch.tensor(wl["kern"], device=dev))
+    return op, B.ideq_apply_A(ctx, op, x_true) + noise
 
 
 def parse():
@@ -48,6 +71,8 @@ def parse():
     ap.add_argument("--precision", default="fp16", choices=["fp16", "bf16", "fp32"],
                     help="convolution arithmetic of the profiling mode")
     ap.add_argument("--batch", type=int, default=0, help="profiling mode: batch size override")
+    ap.add_argument("--workload", default="C1a", choices=sorted(WORKLOADS),
+                    help="synthetic workload (default: the 8 x RGB 256^2 motion-blur batch)")
     return ap.parse_args()
 
 
@@ -169,10 +194,10 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def load_workload(n_override=None):
+def load_workload(n_override=None, name="C1a"):
     import numpy as np
     from synth import get_config, workload
-    cfg = get_config("C1a")
+    cfg = get_config(name)
     if n_override:
         cfg["n"] = n_override
     wl = workload(cfg)
@@ -191,17 +216,15 @@ def run_ours(args):
     pbuild.build()
     from paper_2605_19705_gb300 import binding as B
 
-    cfg, wl, _ = load_workload()
+    cfg, wl, _ = load_workload(name=args.workload)
     n = cfg["n"]
     dev = torch.device("cuda", local)
-    kern = torch.tensor(wl["kern"], device=dev)
-    op = B.make_operator(B.IDEQ_OP_BLUR, kern)
     weights = torch.tensor(wl["weights"], device=dev)
     desc = B.net_desc(cfg["net"], cfg["c"])
     # observations y = A(x*) + n formed on the device by the library's forward model
     x_true = torch.tensor(wl["x_true"], device=dev)
     ctx = B.Context(desc, weights, B.IDEQ_FP16)
-    y = B.ideq_apply_A(ctx, op, x_true) + torch.tensor(wl["noise"], device=dev)
+    op, y = make_op_and_y(B, cfg, wl, ctx, x_true, dev)
     params = B.make_params(cfg["lam"], cfg["tau"], cfg["beta"], cfg["B"], cfg["tol"],
                            cfg["max_iter"])
     info = B.InfoBuffers(n, dev)
@@ -296,7 +319,8 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16",
         "data": "synthetic (seeded images, kernels, noise; random-init U-Net weights)",
-        "config": {"workload": WORKLOAD, "batch_per_gpu": n, "image": "3x256x256",
+        "config": {"workload": WORKLOADS[args.workload], "batch_per_gpu": n,
+                   "image": f"{cfg['c']}x{cfg['h']}x{cfg['w']}",
                    "form": "fp16 tcgen05 convolutions (fp32 accumulate), fp32 iterate and data step, fp64 reductions, x0 = A^T y",
                    "parallelism": f"replicas x{world} (independent batches)",
                    "l2": "working set ~1.5 GB per solve (> 129 MB L2); no flush needed"},
@@ -316,20 +340,20 @@ def run_ours(args):
         res["plain_fp32"] = plain
         res["speedup_vs_plain_fp32"] = value / world / plain["value"]
     if rank == 0 and not args.no_cpu:
-        res["cpu_baseline"] = cpu_baseline(it_c)
+        res["cpu_baseline"] = cpu_baseline(it_c, args.workload)
     if rank == 0:
         print(json.dumps(res), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
-def cpu_baseline(iters_per_image):
+def cpu_baseline(iters_per_image, name="C1a"):
     """The FP64 oracle timed on the host cores on a bounded sample (one inertial
-    step of one 256^2 RGB image of the same workload), extrapolated to
+    step of one 256^2 image of the same workload), extrapolated to
     restorations/s with the iteration count per image."""
     import numpy as np
     from oracle import nets, operators, solver
-    cfg, wl, _ = load_workload()
+    cfg, wl, _ = load_workload(name=name)
     net = nets.Net.from_config(cfg["net"], cfg["c"], wl["weights"])
     ops = operators.make_operators(cfg, wl)
     y0 = operators.observe(ops[:1], wl["x_true"][:1], wl["noise"][:1])[0]
@@ -339,7 +363,7 @@ def cpu_baseline(iters_per_image):
     dt = time.perf_counter() - t0
     return {"value": 1.0 / (dt * iters_per_image), "unit": "restorations/s",
             "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"1 inertial step of 1 image (3x256x256) = {dt:.2f} s, extrapolated "
+            "sample": f"1 inertial step of 1 image ({cfg['c']}x{cfg['h']}x{cfg['w']}) = {dt:.2f} s, extrapolated "
                       f"to {iters_per_image:.1f} iterations per restoration"}
 
 

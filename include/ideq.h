@@ -50,7 +50,7 @@ enum { IDEQ_IMG_RUNNING = 0, IDEQ_IMG_CONVERGED = 1, IDEQ_IMG_MAXITER = 2, IDEQ_
 
 enum { IDEQ_NET_CNN = 0, IDEQ_NET_UNET = 1 };
 enum { IDEQ_ACT_SOFTPLUS = 0, IDEQ_ACT_RELU = 1 };
-enum { IDEQ_OP_BLUR = 0, IDEQ_OP_MASK = 1, IDEQ_OP_SATBLUR = 2 };
+enum { IDEQ_OP_BLUR = 0, IDEQ_OP_MASK = 1, IDEQ_OP_SATBLUR = 2, IDEQ_OP_MRI = 3 };
 /* Arithmetic of the regulariser network's convolutions: operands in FP32
  * (SIMT), BF16 or FP16 (tensor cores, FP32 accumulation), activations stored in
  * the operand type.  The _FP8 forms run the tensor-core convolutions whose
@@ -93,7 +93,12 @@ typedef struct { int n, c, h, w; } ideq_shape;  /* batch, channels, height, widt
  *  IDEQ_OP_BLUR    A x = k_b * x, circular convolution with per-image kernel
  *                  k_b (centre (kh/2, kw/2)), shared by the channels.
  *  IDEQ_OP_MASK    A x = M_b . x, per-pixel 0/1 mask shared by the channels.
- *  IDEQ_OP_SATBLUR A x = tanh(s (k_b * x)) / tanh(s), s = sat_gain.       */
+ *  IDEQ_OP_SATBLUR A x = tanh(s (k_b * x)) / tanh(s), s = sat_gain.
+ *  IDEQ_OP_MRI     A x = M_b . F x (App. E, MRI): x a complex image stored as
+ *                  c = 2 planes (re, im), F the orthonormal 2-D DFT, M_b a 0/1
+ *                  k-space mask (n*h*w, unshifted FFT layout); y is complex
+ *                  k-space in the same 2-plane layout, zero off the mask.
+ *                  h and w must be powers of two in [8, 1024].              */
 typedef struct {
   int kind;
   int kh, kw;              /* odd kernel sizes (<= 31) for blur kinds        */
@@ -111,13 +116,19 @@ typedef struct {
  * minimiser of ||x^{k+1}-x^k|| over floor(K/2) < k < K-1 and K = max_iter.
  * Averaging needs a fixed run -- tol = 0, no restart, max_iter >= 5 -- and is
  * otherwise an argument error; ideq_step ignores it.  An image that diverged
- * returns its last iterate. */
+ * returns its last iterate.  prox = 1 replaces the RED step by the proximal step
+ * of i-DEQ-P (Algorithm 2, Eq. red_prox): x^{k+1} = prox_{tau f}(z - tau lambda
+ * grad g(z)), in closed form for the inpainting mask (App. E:
+ * (tau M y + v) / (tau M + 1) per pixel) and for MRI (the same in k-space,
+ * F^{-1}((tau M y + F v) / (tau M + 1))); other operators return
+ * IDEQ_ERR_UNSUPPORTED.  The restart keeps Algorithm 1's form. */
 typedef struct {
   float lambda, tau, beta, restart_B;
   double tol;
   int max_iter;
   int init;               /* IDEQ_INIT_ATY, IDEQ_INIT_X0 (x0 given) or IDEQ_INIT_WARM */
   int average;            /* 0: last iterate; 1: averaging step (ideq_solve)         */
+  int prox;               /* 0: RED step (Algorithm 1); 1: proximal step of i-DEQ-P  */
 } ideq_params;
 
 /* Per-image results, device arrays of length n; any member may be NULL. */

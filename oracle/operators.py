@@ -10,6 +10,9 @@ of shape (c, h, w); blur kernels and masks are shared by the c channels.
   blur    : A x = k * x, circular 2-D convolution, kernel centre (kh//2, kw//2)
   mask    : A x = M . x, M in {0,1}^(h,w)                    (App. E, inpainting)
   satblur : A x = tanh(s (k * x)) / tanh(s), a smooth saturation after the blur
+  mri     : A x = M . F x for a complex image x stored as (re, im) channels, F the
+            orthonormal 2-D DFT, M in {0,1}^(h,w) a k-space mask (App. E, MRI);
+            A^T r = F^{-1}(M . r), prox_{tau f}(v) = F^{-1}((tau M y + F v) / (tau M + 1))
 """
 from __future__ import annotations
 
@@ -40,8 +43,16 @@ def corr_circ(r: np.ndarray, k: np.ndarray) -> np.ndarray:
     return out
 
 
+def _cplx(x):
+    return x[0] + 1j * x[1]
+
+
+def _planes(z):
+    return np.stack([z.real, z.imag])
+
+
 class Operator:
-    """Forward model of one image: kind in {"blur", "mask", "satblur"}."""
+    """Forward model of one image: kind in {"blur", "mask", "satblur", "mri"}."""
 
     def __init__(self, kind, kern=None, mask=None, gain=2.0):
         self.kind = kind
@@ -50,8 +61,8 @@ class Operator:
         self.s = float(gain)
         if kind in ("blur", "satblur") and self.k is None:
             raise ValueError("blur operators need a kernel")
-        if kind == "mask" and self.m is None:
-            raise ValueError("mask operator needs a mask")
+        if kind in ("mask", "mri") and self.m is None:
+            raise ValueError("mask and MRI operators need a mask")
 
     @property
     def linear(self) -> bool:
@@ -62,6 +73,8 @@ class Operator:
             return conv_circ(x, self.k)
         if self.kind == "mask":
             return self.m * x
+        if self.kind == "mri":
+            return _planes(self.m * np.fft.fft2(_cplx(x), norm="ortho"))
         q = conv_circ(x, self.k)
         return np.tanh(self.s * q) / np.tanh(self.s)
 
@@ -72,6 +85,8 @@ class Operator:
         paper leaves x0 free, Alg. 1), not a Jacobian transpose."""
         if self.kind == "mask":
             return self.m * r
+        if self.kind == "mri":
+            return _planes(np.fft.ifft2(self.m * _cplx(r), norm="ortho"))
         return corr_circ(r, self.k)
 
     def JA(self, x, w):
@@ -97,6 +112,17 @@ class Operator:
 
     def grad_f(self, x, y):
         return self.JAT(x, self.A(x) - y)
+
+    def prox_f(self, v, y, tau):
+        """prox_{tau f}(v) = argmin_x 1/2||A x - y||^2 + 1/(2 tau)||x - v||^2 for the
+        inpainting mask (App. E): (tau M y + v) / (tau M + 1) per pixel, i.e. v where
+        the pixel is unobserved.  Other forward models have no closed form here."""
+        if self.kind == "mri":  # k-space: (tau M y + F v) / (tau M + 1), App. E
+            Y = (tau * self.m * _cplx(y) + np.fft.fft2(_cplx(v), norm="ortho")) / (tau * self.m + 1.0)
+            return _planes(np.fft.ifft2(Y, norm="ortho"))
+        if self.kind != "mask":
+            raise NotImplementedError("closed-form prox only for the mask and MRI models")
+        return (tau * self.m * y + v) / (tau * self.m + 1.0)
 
     def hvp_f(self, x, y, u):
         """Hessian of f at x applied to u.
@@ -139,11 +165,14 @@ def make_operators(cfg: dict, wl: dict):
 
 
 def observe(ops, x_true, noise, mask=None):
-    """y = A(x*) + n per image (FP64).  For inpainting y = M (x* + n)."""
+    """y = A(x*) + n per image (FP64).  For inpainting y = M (x* + n); for MRI
+    y = M (F x* + n), the noise (re, im planes) on the sampled k-space entries."""
     ys = []
     for i, op in enumerate(ops):
         if op.kind == "mask":
             ys.append(op.m * (x_true[i].astype(np.float64) + noise[i]))
+        elif op.kind == "mri":
+            ys.append(op.A(x_true[i].astype(np.float64)) + op.m * noise[i])
         else:
             ys.append(op.A(x_true[i].astype(np.float64)) + noise[i])
     return np.stack(ys)

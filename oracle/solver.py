@@ -20,6 +20,9 @@ with beta = 1 - alpha.  Readings where the paper is silent or loose:
     ||x^{k+1} - x^k|| over floor(K/2) < k < K - 1, for a run of exactly K =
     max_iter updates without restarts (tol = 0, B = inf), K >= 5;
   * a non-finite step norm marks the image diverged and freezes it.
+With prox=True the update is the proximal step of Algorithm 2 (i-DEQ-P):
+x^{k+1} = prox_{tau f}(z^k - tau lambda grad g(z^k)) (Eq. red_prox with the inertial
+step), with the restart of Algorithm 1 (the reading shared by both variants).
 Alpha = 1 (beta = 0) is RED, i.e. gradient descent on F = f + lambda g (Sec. 2.1).
 """
 from __future__ import annotations
@@ -33,11 +36,15 @@ from . import nets
 RUNNING, CONVERGED, MAXITER, DIVERGED = 0, 1, 2, 3
 
 
-def red_step(net, op, y, z, lam, tau):
-    """T^RED(z) = z - tau (grad f(z) + lambda grad g(z)); also f(z), g(z)."""
+def red_step(net, op, y, z, lam, tau, prox=False):
+    """T^RED(z) = z - tau (grad f(z) + lambda grad g(z)), or with prox=True the
+    proximal step T^RED-P(z) = prox_{tau f}(z - tau lambda grad g(z)) (Eq. red_prox);
+    also f(z), g(z)."""
     gg, gval = nets.grad_g(net, z)
-    gf = op.grad_f(z, y)
     fval = op.f(z, y)
+    if prox:
+        return op.prox_f(z - tau * lam * gg, y, tau), fval, gval
+    gf = op.grad_f(z, y)
     return z - tau * (gf + lam * gg), fval, gval
 
 
@@ -54,7 +61,7 @@ def averaging_step(zs, steps):
 
 
 def solve_image(net, op, y, x0, lam, tau, beta, B=math.inf, tol=0.0, max_iter=50,
-                keep_history=False, average=False):
+                keep_history=False, average=False, prox=False):
     """Run the iteration on one image.  Returns (x_hat, info dict)."""
     if average and (tol > 0.0 or B < math.inf):
         raise ValueError("the averaging step needs a fixed run: tol = 0 and no restart")
@@ -68,7 +75,7 @@ def solve_image(net, op, y, x0, lam, tau, beta, B=math.inf, tol=0.0, max_iter=50
     zs, norms = [], []
     while total < max_iter:
         z = x + beta * (x - x_prev)
-        x_new, fval, gval = red_step(net, op, y, z, lam, tau)
+        x_new, fval, gval = red_step(net, op, y, z, lam, tau, prox)
         s = float(np.sum((x_new - x) ** 2))
         if average:
             zs.append(z)
@@ -103,12 +110,12 @@ def solve_image(net, op, y, x0, lam, tau, beta, B=math.inf, tol=0.0, max_iter=50
 
 
 def solve_batch(net, ops, ys, x0s, lam, tau, beta, B=math.inf, tol=0.0, max_iter=50,
-                keep_history=False, average=False):
+                keep_history=False, average=False, prox=False):
     """Independent solves of a batch (images never interact)."""
     xs, infos = [], []
     for i in range(len(ops)):
         x, inf = solve_image(net, ops[i], ys[i], x0s[i], lam, tau, beta, B, tol, max_iter,
-                             keep_history, average)
+                             keep_history, average, prox)
         xs.append(x)
         infos.append(inf)
     return np.stack(xs), infos

@@ -27,7 +27,7 @@ IDEQ_MAXITER, IDEQ_DIVERGED, IDEQ_ADJ_MAXITER, IDEQ_ERR_TIMEOUT = 5, 6, 7, 8
 IDEQ_IMG_RUNNING, IDEQ_IMG_CONVERGED, IDEQ_IMG_MAXITER, IDEQ_IMG_DIVERGED = 0, 1, 2, 3
 IDEQ_NET_CNN, IDEQ_NET_UNET = 0, 1
 IDEQ_ACT_SOFTPLUS, IDEQ_ACT_RELU = 0, 1
-IDEQ_OP_BLUR, IDEQ_OP_MASK, IDEQ_OP_SATBLUR = 0, 1, 2
+IDEQ_OP_BLUR, IDEQ_OP_MASK, IDEQ_OP_SATBLUR, IDEQ_OP_MRI = 0, 1, 2, 3
 IDEQ_FP32, IDEQ_BF16, IDEQ_BF16_FP8, IDEQ_FP16, IDEQ_FP16_FP8 = 0, 1, 2, 3, 4
 IDEQ_INIT_ATY, IDEQ_INIT_X0, IDEQ_INIT_WARM = 0, 1, 2
 IDEQ_ADJ_JFB, IDEQ_ADJ_IMPLICIT = 0, 1
@@ -49,7 +49,8 @@ class Operator(ctypes.Structure):
 
 class Params(ctypes.Structure):
     _fields_ = [("lam", c_float), ("tau", c_float), ("beta", c_float), ("restart_B", c_float),
-                ("tol", c_double), ("max_iter", c_int), ("init", c_int), ("average", c_int)]
+                ("tol", c_double), ("max_iter", c_int), ("init", c_int), ("average", c_int),
+                ("prox", c_int)]
 
 
 class Info(ctypes.Structure):
@@ -232,10 +233,11 @@ def ideq_grad_reg(ctx: Context, z, grad=None, g_val=None):
 
 
 def make_params(lam, tau, beta, B=float("inf"), tol=0.0, max_iter=50, init=IDEQ_INIT_ATY,
-                average=False):
+                average=False, prox=False):
     p = Params()
     p.lam, p.tau, p.beta, p.restart_B = lam, tau, beta, (B if B != float("inf") else 0.0)
     p.tol, p.max_iter, p.init, p.average = tol, max_iter, init, 1 if average else 0
+    p.prox = 1 if prox else 0
     return p
 
 

@@ -18,7 +18,7 @@ OUT = os.path.join(HERE, "libideq.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "net.cu", "kernels_elem.cu", "conv_simt.cu", "conv_tc.cu", "conv_edge.cu",
-           "conv_edge_rb.cu", "wgrad.cu",
+           "conv_edge_rb.cu", "fft.cu", "wgrad.cu",
            "net_train.cu", "noalloc.cu"]
 
 

@@ -112,6 +112,11 @@ ideq_status check_op(ideq_ctx* ctx, const ideq_operator* op, const ideq_shape& s
       return fail(ctx, IDEQ_ERR_ARG, "sat_gain must be > 0");
   } else if (op->kind == IDEQ_OP_MASK) {
     if (!op->mask) return fail(ctx, IDEQ_ERR_ARG, "mask operator needs a mask");
+  } else if (op->kind == IDEQ_OP_MRI) {
+    if (!op->mask) return fail(ctx, IDEQ_ERR_ARG, "MRI operator needs a k-space mask");
+    if (s.c != 2) return fail(ctx, IDEQ_ERR_ARG, "MRI images are complex: c = 2 (re, im)");
+    if (!fft_size_ok(s.h) || !fft_size_ok(s.w))
+      return fail(ctx, IDEQ_ERR_UNSUPPORTED, "MRI needs h, w powers of two in [8, 1024]");
   } else {
     return fail(ctx, IDEQ_ERR_ARG, "unknown operator kind");
   }
@@ -211,6 +216,10 @@ cudaError_t data_grad(ideq_ctx* ctx, const OpDev& od, const ideq_shape& s, const
     ctx->launches += 1;
     return launch_data_fwd(od, s.n, s.c, s.h, s.w, z, y, gf, fsum, st);
   }
+  if (od.kind == IDEQ_OP_MRI) {
+    ctx->launches += 5;
+    return launch_mri_grad(s.n, s.h, s.w, z, y, od.mask, tmp, gf, fsum, st);
+  }
   cudaError_t e = launch_data_fwd(od, s.n, s.c, s.h, s.w, z, y, tmp, fsum, st);
   if (e != cudaSuccess) return e;
   ctx->launches += 2;
@@ -222,6 +231,10 @@ cudaError_t back_project(ideq_ctx* ctx, const OpDev& od, const ideq_shape& s, co
                          float* out) {
   ctx->launches += 1;
   if (od.kind == IDEQ_OP_MASK) return launch_apply_A(od, s.n, s.c, s.h, s.w, y, out, ctx->stream);
+  if (od.kind == IDEQ_OP_MRI) {
+    ctx->launches += 2;
+    return launch_mri_apply(s.n, s.h, s.w, y, od.mask, 1, out, ctx->stream);
+  }
   return launch_blur_adj(od, s.n, s.c, s.h, s.w, y, out, ctx->stream);
 }
 
@@ -241,9 +254,21 @@ ideq_status iterate(ideq_ctx* ctx, const OpDev& od, const ideq_shape& s, const f
     CK(launch_extrapolate(n, per, x, xp, ctx->sv.beta_eff, P->z, st));
   CK(run_steps(P->fwd, ctx->d_err, st, &ctx->prof, &ctx->launches));
   CK(run_steps(P->vjp, ctx->d_err, st, &ctx->prof, &ctx->launches));
-  CK(data_grad(ctx, od, s, P->z, y, ctx->gf, ctx->tmp, ctx->sv.fsum));
-  CK(launch_red_update(n, per, ctx->sv_nblk, P->z, ctx->gf, P->grad, x, xp, p->lambda, p->tau,
-                       ctx->sv.status, ctx->sv.part_s, ctx->sv.part_x, st));
+  CK(data_grad(ctx, od, s, P->z, y, ctx->gf, ctx->tmp, ctx->sv.fsum));  // also f(z)
+  if (p->prox && od.kind == IDEQ_OP_MRI) {
+    // v = z - tau lambda grad g into gf (the data gradient is not used by the
+    // proximal step), its prox into tmp, accepted for the running images
+    CK(launch_axpby((long long)n * per, 1.f, P->z, -p->tau * p->lambda, P->grad, ctx->gf, st));
+    CK(launch_mri_prox(n, s.h, s.w, ctx->gf, y, od.mask, p->tau, ctx->tmp, st));
+    CK(launch_commit_update(n, per, ctx->sv_nblk, ctx->tmp, x, xp, ctx->sv.status,
+                            ctx->sv.part_s, ctx->sv.part_x, st));
+    ctx->launches += 7;
+  } else if (p->prox)
+    CK(launch_prox_update(n, per, s.h * s.w, ctx->sv_nblk, P->z, P->grad, y, od.mask, x, xp,
+                          p->lambda, p->tau, ctx->sv.status, ctx->sv.part_s, ctx->sv.part_x, st));
+  else
+    CK(launch_red_update(n, per, ctx->sv_nblk, P->z, ctx->gf, P->grad, x, xp, p->lambda, p->tau,
+                         ctx->sv.status, ctx->sv.part_s, ctx->sv.part_x, st));
   const float B = (std::isfinite(p->restart_B) && p->restart_B > 0.f) ? p->restart_B : INFINITY;
   CK(launch_finalize(n, ctx->sv_nblk, ctx->sv, 1 - par, p->beta, B, p->tol, p->max_iter,
                      p->lambda, logic, avg_K, st));
@@ -268,7 +293,7 @@ bool same_op(const OpDev& a, const OpDev& b) {
 bool same_params(const ideq_params& a, const ideq_params& b) {
   return a.lambda == b.lambda && a.tau == b.tau && a.beta == b.beta &&
          a.restart_B == b.restart_B && a.tol == b.tol && a.max_iter == b.max_iter &&
-         a.average == b.average;
+         a.average == b.average && a.prox == b.prox;
 }
 
 // Build the solve graph for (plan, operator, y, params): a kernel setting the
@@ -366,6 +391,7 @@ ideq_status check_params(ideq_ctx* ctx, const ideq_params* p) {
   if (!(p->tau > 0.f) || !(p->lambda >= 0.f) || !(p->beta >= 0.f && p->beta < 1.f))
     return fail(ctx, IDEQ_ERR_ARG, "need tau > 0, lambda >= 0, 0 <= beta < 1");
   if (p->max_iter < 1) return fail(ctx, IDEQ_ERR_ARG, "max_iter must be >= 1");
+  if (p->prox != 0 && p->prox != 1) return fail(ctx, IDEQ_ERR_ARG, "prox must be 0 or 1");
   if (!(p->tol >= 0.0)) return fail(ctx, IDEQ_ERR_ARG, "tol must be >= 0");
   return IDEQ_OK;
 }
@@ -489,6 +515,11 @@ ideq_status ideq_apply_A(ideq_ctx* ctx, const ideq_operator* op, ideq_shape shap
   OpDev od;
   ideq_status s = check_op(ctx, op, shape, &od);
   if (s != IDEQ_OK) return s;
+  if (od.kind == IDEQ_OP_MRI) {
+    CK(launch_mri_apply(shape.n, shape.h, shape.w, x, od.mask, 0, Ax, ctx->stream));
+    ctx->launches += 3;
+    return IDEQ_OK;
+  }
   CK(launch_apply_A(od, shape.n, shape.c, shape.h, shape.w, x, Ax, ctx->stream));
   ctx->launches += 1;
   return IDEQ_OK;
@@ -539,6 +570,8 @@ ideq_status ideq_step(ideq_ctx* ctx, const ideq_operator* op, ideq_shape shape, 
   if (s != IDEQ_OK) return s;
   OpDev od;
   if ((s = check_op(ctx, op, shape, &od)) != IDEQ_OK) return s;
+  if (p->prox && od.kind != IDEQ_OP_MASK && od.kind != IDEQ_OP_MRI)
+    return fail(ctx, IDEQ_ERR_UNSUPPORTED, "the proximal step has a closed form for mask and MRI");
   if ((s = ensure_plan(ctx, shape)) != IDEQ_OK) return s;
   const size_t bytes = (size_t)shape.n * shape.c * shape.h * shape.w * 4;
   cudaStream_t st = ctx->stream;
@@ -560,6 +593,8 @@ ideq_status ideq_solve(ideq_ctx* ctx, const ideq_operator* op, ideq_shape shape,
   if (s != IDEQ_OK) return s;
   OpDev od;
   if ((s = check_op(ctx, op, shape, &od)) != IDEQ_OK) return s;
+  if (p->prox && od.kind != IDEQ_OP_MASK && od.kind != IDEQ_OP_MRI)
+    return fail(ctx, IDEQ_ERR_UNSUPPORTED, "the proximal step has a closed form for mask and MRI");
   if (p->init == IDEQ_INIT_X0 && !x0) return fail(ctx, IDEQ_ERR_ARG, "init X0 needs x0");
   if (p->init == IDEQ_INIT_WARM && !ctx->warm_w)
     return fail(ctx, IDEQ_ERR_ARG, "init WARM needs ideq_warm_set");
@@ -650,8 +685,9 @@ ideq_status ideq_solve_backward(ideq_ctx* ctx, const ideq_operator* op, ideq_sha
   if (s != IDEQ_OK) return s;
   OpDev od;
   if ((s = check_op(ctx, op, shape, &od)) != IDEQ_OK) return s;
+  if (p->prox) return fail(ctx, IDEQ_ERR_UNSUPPORTED, "backward of the proximal variant");
   if (od.kind == IDEQ_OP_SATBLUR)
-    return fail(ctx, IDEQ_ERR_UNSUPPORTED, "backward supports linear operators (blur, mask)");
+    return fail(ctx, IDEQ_ERR_UNSUPPORTED, "backward supports linear operators (blur, mask, MRI)");
   if (ap->mode != IDEQ_ADJ_JFB && ap->mode != IDEQ_ADJ_IMPLICIT)
     return fail(ctx, IDEQ_ERR_ARG, "adjoint mode");
   if (ap->mode == IDEQ_ADJ_IMPLICIT && (ap->max_iter < 1 || !(ap->tol > 0.0) ||

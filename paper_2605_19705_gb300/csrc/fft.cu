@@ -1,0 +1,196 @@
+// Orthonormal 2-D DFT of complex images stored as two f32 planes (re, im) per
+// image, and the k-space steps of the MRI data term (App. E):
+//   A x = M . F x,   A^T r = F^{-1}(M . r),   grad f = F^{-1}(M . F z - y),
+//   prox_{tau f}(v) = F^{-1}((tau M y + F v) / (tau M + 1)),
+// F the unitary DFT, M a 0/1 k-space mask per image, y zero off the mask.
+//
+// One launch transforms G lines of one image (rows, or G consecutive columns)
+// held in shared memory: the lines are read in bit-reversed order (coalesced in
+// both directions), then log2 N radix-2 butterfly stages with a per-block table
+// of the N/2 twiddles exp(-+2 pi i k / N), and the 1/sqrt(N) scale on the way
+// out; a row pass and a column pass make the 2-D transform.  N is a power of two,
+// 8 <= N <= 1024.
+#include "common.cuh"
+#include "ideq_internal.h"
+
+namespace ideq {
+
+constexpr int FFT_THREADS = 256;
+
+__device__ __forceinline__ unsigned bitrev(unsigned v, int bits) {
+  return __brev(v) >> (32 - bits);
+}
+
+// lines: G lines of length N; element e of line l of image b sits at
+// base_b + (l0 + l) * line_stride + e * elem_stride in both planes.
+__global__ void __launch_bounds__(FFT_THREADS) fft_lines_kernel(
+    const float* in, float* out, int N, int logN, int G,  // in and out may alias
+    int lines_per_img, int line_stride, int elem_stride, int plane, int inverse) {
+  extern __shared__ float2 sm[];  // [G][N] data, then N/2 twiddles
+  float2* tw = sm + (size_t)G * N;
+  const int b = blockIdx.y;
+  const int l0 = blockIdx.x * G;
+  const size_t ib = (size_t)b * 2 * plane;  // image base (re plane; im at + plane)
+  const bool rows = elem_stride == 1;
+  for (int k = threadIdx.x; k < N / 2; k += FFT_THREADS) {
+    float s, c;
+    sincospif(2.f * (float)k / (float)N, &s, &c);  // exp(-+ 2 pi i k / N)
+    tw[k] = make_float2(c, inverse ? s : -s);
+  }
+  for (int idx = threadIdx.x; idx < G * N; idx += FFT_THREADS) {
+    // consecutive threads walk consecutive addresses: along a row, or across columns
+    const int l = rows ? idx / N : idx % G;
+    const int e = rows ? idx % N : idx / G;
+    if (l0 + l >= lines_per_img) continue;
+    const size_t o = ib + (size_t)(l0 + l) * line_stride + (size_t)e * elem_stride;
+    sm[(size_t)l * N + bitrev((unsigned)e, logN)] = make_float2(in[o], in[o + plane]);
+  }
+  __syncthreads();
+  for (int s = 0; s < logN; ++s) {
+    const int m = 1 << s;  // butterfly half-span
+    for (int t = threadIdx.x; t < G * (N / 2); t += FFT_THREADS) {
+      const int l = t / (N / 2), k = t % (N / 2);
+      const int j = k & (m - 1), i0 = ((k >> s) << (s + 1)) + j;
+      float2* L = sm + (size_t)l * N;
+      const float2 w = tw[j << (logN - 1 - s)];
+      const float2 a = L[i0], bb = L[i0 + m];
+      const float2 wb = make_float2(w.x * bb.x - w.y * bb.y, w.x * bb.y + w.y * bb.x);
+      L[i0] = make_float2(a.x + wb.x, a.y + wb.y);
+      L[i0 + m] = make_float2(a.x - wb.x, a.y - wb.y);
+    }
+    __syncthreads();
+  }
+  const float scale = rsqrtf((float)N);
+  for (int idx = threadIdx.x; idx < G * N; idx += FFT_THREADS) {
+    const int l = rows ? idx / N : idx % G;
+    const int e = rows ? idx % N : idx / G;
+    if (l0 + l >= lines_per_img) continue;
+    const size_t o = ib + (size_t)(l0 + l) * line_stride + (size_t)e * elem_stride;
+    const float2 v = sm[(size_t)l * N + e];
+    out[o] = v.x * scale;
+    out[o + plane] = v.y * scale;
+  }
+}
+
+static int ilog2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+bool fft_size_ok(int n) { return n >= 8 && n <= 1024 && (n & (n - 1)) == 0; }
+
+// out = F x (inverse = 0) or F^{-1} x (inverse = 1) for n complex images (2 planes
+// each) of H x W; in and out may alias.
+cudaError_t launch_fft2(const float* in, float* out, int n, int H, int W, int inverse,
+                        cudaStream_t st) {
+  if (!fft_size_ok(H) || !fft_size_ok(W)) return cudaErrorInvalidValue;
+  const int plane = H * W;
+  // rows: G rows per block
+  {
+    const int G = std::max(1, 4096 / W);
+    const size_t smem = (size_t)G * W * 8 + (size_t)(W / 2) * 8;
+    dim3 grid((H + G - 1) / G, n);
+    fft_lines_kernel<<<grid, FFT_THREADS, smem, st>>>(in, out, W, ilog2(W), G, H, W, 1, plane,
+                                                      inverse);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  // columns: G consecutive columns per block
+  {
+    const int G = std::min(W, std::max(1, 4096 / H));
+    const size_t smem = (size_t)G * H * 8 + (size_t)(H / 2) * 8;
+    dim3 grid((W + G - 1) / G, n);
+    fft_lines_kernel<<<grid, FFT_THREADS, smem, st>>>(out, out, H, ilog2(H), G, W, 1, W, plane,
+                                                      inverse);
+  }
+  return cudaGetLastError();
+}
+
+// k-space residual of the MRI data term: e = M . K - y (both planes; y = null
+// reads as 0, giving M . K for the Hessian product A^T A u), written over K, and
+// 1/2 |e|^2 summed per image into fsum.
+__global__ void __launch_bounds__(256) kspace_residual_kernel(
+    int hw, float* __restrict__ K, const float* __restrict__ y, const uint8_t* __restrict__ mask,
+    double* __restrict__ fsum) {
+  __shared__ double red[32];
+  const int b = blockIdx.y;
+  double part = 0.0;
+  for (int p = blockIdx.x * 256 + threadIdx.x; p < hw; p += gridDim.x * 256) {
+    const float m = (float)mask[(size_t)b * hw + p];
+    const size_t r = (size_t)b * 2 * hw + p, i = r + hw;
+    const float er = m * K[r] - (y ? y[r] : 0.f), ei = m * K[i] - (y ? y[i] : 0.f);
+    K[r] = er;
+    K[i] = ei;
+    part += 0.5 * ((double)er * er + (double)ei * ei);
+  }
+  if (fsum) {
+    const double s = block_sum(part, red);
+    if (threadIdx.x == 0) atomicAdd(fsum + b, s);
+  }
+}
+
+// K <- M . K (plain masking, both planes)
+__global__ void kspace_mask_kernel(int hw, float* __restrict__ K, const uint8_t* __restrict__ mask) {
+  const int b = blockIdx.y;
+  for (int p = blockIdx.x * 256 + threadIdx.x; p < hw; p += gridDim.x * 256) {
+    const float m = (float)mask[(size_t)b * hw + p];
+    const size_t r = (size_t)b * 2 * hw + p;
+    K[r] *= m;
+    K[r + hw] *= m;
+  }
+}
+
+// K <- (tau M y + K) / (tau M + 1): the k-space form of prox_{tau f} (App. E)
+__global__ void kspace_prox_kernel(int hw, float* __restrict__ K, const float* __restrict__ y,
+                                   const uint8_t* __restrict__ mask, float tau) {
+  const int b = blockIdx.y;
+  for (int p = blockIdx.x * 256 + threadIdx.x; p < hw; p += gridDim.x * 256) {
+    const float tm = tau * (float)mask[(size_t)b * hw + p];
+    const size_t r = (size_t)b * 2 * hw + p, i = r + hw;
+    K[r] = (tm * y[r] + K[r]) / (tm + 1.f);
+    K[i] = (tm * y[i] + K[i]) / (tm + 1.f);
+  }
+}
+
+static dim3 kgrid(int n, int hw) {
+  return dim3((unsigned)std::min((hw + 255) / 256, 64), (unsigned)n);
+}
+
+cudaError_t launch_mri_grad(int n, int H, int W, const float* z, const float* y,
+                            const uint8_t* mask, float* kbuf, float* gf, double* fsum,
+                            cudaStream_t st) {
+  cudaError_t e = launch_fft2(z, kbuf, n, H, W, 0, st);
+  if (e != cudaSuccess) return e;
+  kspace_residual_kernel<<<kgrid(n, H * W), 256, 0, st>>>(H * W, kbuf, y, mask, fsum);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return launch_fft2(kbuf, gf, n, H, W, 1, st);
+}
+
+cudaError_t launch_mri_apply(int n, int H, int W, const float* x, const uint8_t* mask,
+                             int adjoint, float* out, cudaStream_t st) {
+  cudaError_t e;
+  if (!adjoint) {  // M . F x
+    if ((e = launch_fft2(x, out, n, H, W, 0, st)) != cudaSuccess) return e;
+    kspace_mask_kernel<<<kgrid(n, H * W), 256, 0, st>>>(H * W, out, mask);
+    return cudaGetLastError();
+  }
+  // F^{-1}(M . r): mask a copy, then transform it in place
+  if ((e = cudaMemcpyAsync(out, x, (size_t)n * 2 * H * W * 4, cudaMemcpyDeviceToDevice, st)) !=
+      cudaSuccess)
+    return e;
+  kspace_mask_kernel<<<kgrid(n, H * W), 256, 0, st>>>(H * W, out, mask);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return launch_fft2(out, out, n, H, W, 1, st);
+}
+
+cudaError_t launch_mri_prox(int n, int H, int W, const float* v, const float* y,
+                            const uint8_t* mask, float tau, float* out, cudaStream_t st) {
+  cudaError_t e = launch_fft2(v, out, n, H, W, 0, st);
+  if (e != cudaSuccess) return e;
+  kspace_prox_kernel<<<kgrid(n, H * W), 256, 0, st>>>(H * W, out, y, mask, tau);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return launch_fft2(out, out, n, H, W, 1, st);
+}
+
+}  // namespace ideq

@@ -127,6 +127,21 @@ cudaError_t launch_apply_A(const OpDev& op, int n, int c, int H, int W, const fl
 cudaError_t launch_sat_jt_weight(const OpDev& op, int n, int c, int H, int W, const float* lin,
                                  const float* r, float* tmp, cudaStream_t st);
 
+// MRI data term (fft.cu): n complex images of h x w as two f32 planes each.
+bool fft_size_ok(int n);
+cudaError_t launch_fft2(const float* in, float* out, int n, int H, int W, int inverse,
+                        cudaStream_t st);
+// gf = F^{-1}(M F z - y), fsum += 1/2 ||M F z - y||^2 per image; kbuf: image-size scratch
+cudaError_t launch_mri_grad(int n, int H, int W, const float* z, const float* y,
+                            const uint8_t* mask, float* kbuf, float* gf, double* fsum,
+                            cudaStream_t st);
+// out = M F x (adjoint = 0) or F^{-1}(M x) (adjoint = 1)
+cudaError_t launch_mri_apply(int n, int H, int W, const float* x, const uint8_t* mask,
+                             int adjoint, float* out, cudaStream_t st);
+// out = F^{-1}((tau M y + F v) / (tau M + 1))
+cudaError_t launch_mri_prox(int n, int H, int W, const float* v, const float* y,
+                            const uint8_t* mask, float tau, float* out, cudaStream_t st);
+
 // ------------------------------------------------------------- solver state
 struct SolverDev {
   int* k;          // steps since last restart
@@ -165,6 +180,17 @@ cudaError_t launch_red_update(int n, int per_img, int nblk, const float* z, cons
                               const float* gg, const float* x, float* xn, float lam, float tau,
                               const int* status, double* part_s, double* part_x,
                               cudaStream_t st, const float* addv = nullptr);
+// Proximal step of i-DEQ-P for the inpainting mask: xn = (tau m y + v)/(tau m + 1),
+// v = z - tau lambda gg, mask [n][hw] shared by the channels.
+cudaError_t launch_prox_update(int n, int per_img, int hw, int nblk, const float* z,
+                               const float* gg, const float* y, const uint8_t* mask,
+                               const float* x, float* xn, float lam, float tau,
+                               const int* status, double* part_s, double* part_x,
+                               cudaStream_t st);
+// xn = cand for running images, with the FP64 step-norm partials of (xn - x)
+cudaError_t launch_commit_update(int n, int per_img, int nblk, const float* cand, const float* x,
+                                 float* xn, const int* status, double* part_s, double* part_x,
+                                 cudaStream_t st);
 cudaError_t launch_finalize(int n, int nblk, const SolverDev& s, int parity_new, float beta,
                             float B, double tol, int max_iter, float lam, int apply_logic,
                             int avg_K, cudaStream_t st);

@@ -364,6 +364,85 @@ cudaError_t launch_average_out(int n, int per_img, const SolverDev& s, float* ou
   return cudaGetLastError();
 }
 
+// Proximal step of i-DEQ-P for the inpainting mask (Eq. red_prox, App. E):
+// v = z - tau lambda grad g, x_new = (tau m y + v) / (tau m + 1) with the image's
+// 0/1 mask m shared by the channels; same FP64 step-norm partials as the RED update.
+__global__ void __launch_bounds__(256) prox_update_kernel(
+    int per_img, int hw, const float* __restrict__ z, const float* __restrict__ gg,
+    const float* __restrict__ y, const uint8_t* __restrict__ mask, const float* __restrict__ x,
+    float* __restrict__ xn, float lam, float tau, const int* __restrict__ status,
+    double* __restrict__ part_s, double* __restrict__ part_x) {
+  __shared__ double red[32];
+  const int b = blockIdx.y;
+  const int nblk = gridDim.x;
+  const bool run = status[b] == IDEQ_IMG_RUNNING;
+  double ss = 0.0, sx = 0.0;
+  const size_t base = (size_t)b * per_img;
+  if (run) {
+    for (int i = blockIdx.x * 256 + threadIdx.x; i < per_img; i += nblk * 256) {
+      const float v = z[base + i] - tau * lam * gg[base + i];
+      const float m = (float)mask[(size_t)b * hw + i % hw];
+      const float o = (tau * m * y[base + i] + v) / (tau * m + 1.f);
+      xn[base + i] = o;
+      const double d = (double)o - x[base + i];
+      ss += d * d;
+      sx += (double)x[base + i] * x[base + i];
+    }
+  }
+  const double ts = block_sum(ss, red);
+  const double tx = block_sum(sx, red);
+  if (threadIdx.x == 0) {
+    part_s[(size_t)b * nblk + blockIdx.x] = ts;
+    part_x[(size_t)b * nblk + blockIdx.x] = tx;
+  }
+}
+
+cudaError_t launch_prox_update(int n, int per_img, int hw, int nblk, const float* z,
+                               const float* gg, const float* y, const uint8_t* mask,
+                               const float* x, float* xn, float lam, float tau,
+                               const int* status, double* part_s, double* part_x,
+                               cudaStream_t st) {
+  prox_update_kernel<<<dim3(nblk, n), 256, 0, st>>>(per_img, hw, z, gg, y, mask, x, xn, lam, tau,
+                                                    status, part_s, part_x);
+  return cudaGetLastError();
+}
+
+// Accept a candidate update computed elsewhere (the MRI proximal step) for the
+// running images, with the same FP64 step-norm partials as the RED update.
+__global__ void __launch_bounds__(256) commit_update_kernel(
+    int per_img, const float* __restrict__ cand, const float* __restrict__ x,
+    float* __restrict__ xn, const int* __restrict__ status, double* __restrict__ part_s,
+    double* __restrict__ part_x) {
+  __shared__ double red[32];
+  const int b = blockIdx.y;
+  const int nblk = gridDim.x;
+  double ss = 0.0, sx = 0.0;
+  const size_t base = (size_t)b * per_img;
+  if (status[b] == IDEQ_IMG_RUNNING) {
+    for (int i = blockIdx.x * 256 + threadIdx.x; i < per_img; i += nblk * 256) {
+      const float o = cand[base + i];
+      xn[base + i] = o;
+      const double d = (double)o - x[base + i];
+      ss += d * d;
+      sx += (double)x[base + i] * x[base + i];
+    }
+  }
+  const double ts = block_sum(ss, red);
+  const double tx = block_sum(sx, red);
+  if (threadIdx.x == 0) {
+    part_s[(size_t)b * nblk + blockIdx.x] = ts;
+    part_x[(size_t)b * nblk + blockIdx.x] = tx;
+  }
+}
+
+cudaError_t launch_commit_update(int n, int per_img, int nblk, const float* cand, const float* x,
+                                 float* xn, const int* status, double* part_s, double* part_x,
+                                 cudaStream_t st) {
+  commit_update_kernel<<<dim3(nblk, n), 256, 0, st>>>(per_img, cand, x, xn, status, part_s,
+                                                      part_x);
+  return cudaGetLastError();
+}
+
 int update_blocks_per_image(int per_img) {
   const int b = (per_img + 256 * 16 - 1) / (256 * 16);
   return std::max(1, std::min(b, 64));

@@ -68,6 +68,15 @@ CONFIGS = {
                precision="fp32",
                seeds={"img": 6000, "noise": 7000, "weights": 2001, "kernel": 0, "mask": 0,
                       "warm": 2004}),
+    # MRI (App. E): 4 complex 256^2 images as (re, im) channels, Cartesian column
+    # undersampling x4 with an 8% fully sampled centre, complex k-space noise on the
+    # sampled entries; y = M (F x + n), F the orthonormal 2-D DFT.
+    "C5": dict(n=4, c=2, h=256, w=256, op="mri",
+               kernel=None, accel=4, center=0.08,
+               noise_sigma=0.01, net=UNET_HALF,
+               lam=0.1, tau=0.75, beta=0.8, B=INF, tol=1e-4, max_iter=3000,
+               precision="fp32",
+               seeds={"img": 8000, "noise": 8100, "weights": 2005, "kernel": 0, "mask": 8200}),
 }
 CONFIGS["C2"] = dict(copy.deepcopy(CONFIGS["C1a"]), precision="bf16")
 
@@ -95,7 +104,10 @@ def workload(cfg: dict) -> dict:
     """
     n, c, h, w = cfg["n"], cfg["c"], cfg["h"], cfg["w"]
     s = cfg["seeds"]
-    x_true = G.synth_batch(s["img"], n, c, h, w)
+    if cfg["op"] == "mri":
+        x_true = np.stack([G.complex_image(s["img"] + i, h, w) for i in range(n)])
+    else:
+        x_true = G.synth_batch(s["img"], n, c, h, w)
     kern = None
     ks = cfg.get("kernel")
     if ks is not None:
@@ -113,6 +125,9 @@ def workload(cfg: dict) -> dict:
     mask = None
     if cfg["op"] == "mask":
         mask = np.stack([G.bernoulli_mask(s["mask"] + i, h, w, cfg["mask_keep"])
+                         for i in range(n)])
+    elif cfg["op"] == "mri":
+        mask = np.stack([G.cartesian_mask(s["mask"] + i, h, w, cfg["accel"], cfg["center"])
                          for i in range(n)])
     ns = cfg["noise_sigma"]
     if isinstance(ns, (list, tuple)):

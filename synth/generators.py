@@ -167,3 +167,36 @@ def init_weights(seed: int, layout) -> np.ndarray:
         std = gain * math.sqrt(v / fan_in)
         parts.append((std * rng.standard_normal(int(np.prod(shape)))).ravel())
     return np.concatenate(parts).astype(np.float32)
+
+
+def complex_image(seed: int, h: int, w: int) -> np.ndarray:
+    """Complex MR-like image as (re, im) planes (2, h, w): the grey synthetic image
+    as magnitude times a smooth phase exp(i phi), phi a sum of 3 low-frequency
+    cosines (<= 2 cycles) of amplitude <= 0.5 rad."""
+    mag = synth_image(seed, 1, h, w)[0].astype(np.float64)
+    rng = np.random.default_rng(seed + 777)
+    yy, xx = np.meshgrid(np.arange(h) / h, np.arange(w) / w, indexing="ij")
+    phi = np.zeros((h, w))
+    for _ in range(3):
+        fy, fx = rng.integers(0, 3, 2)
+        phi += rng.uniform(0.0, 0.5 / 3) * np.cos(2 * np.pi * (fy * yy + fx * xx) +
+                                                 rng.uniform(0, 2 * np.pi))
+    return np.stack([mag * np.cos(phi), mag * np.sin(phi)]).astype(np.float32)
+
+
+def cartesian_mask(seed: int, h: int, w: int, accel: int = 4, center: float = 0.08) -> np.ndarray:
+    """Cartesian k-space sampling (h, w) u8 in the unshifted FFT layout: whole
+    columns (phase-encoding lines), the centre fraction around frequency 0 always
+    sampled and the rest drawn uniformly until w / accel columns are taken."""
+    rng = np.random.default_rng(seed)
+    n_keep = max(1, w // accel)
+    n_c = max(1, int(round(center * w)))
+    freqs = np.fft.fftfreq(w) * w  # integer frequency of each column
+    order = np.argsort(np.abs(freqs), kind="stable")
+    cols = set(order[:n_c].tolist())
+    rest = [c for c in range(w) if c not in cols]
+    extra = rng.choice(rest, size=max(0, n_keep - len(cols)), replace=False)
+    cols.update(int(c) for c in extra)
+    m = np.zeros((h, w), dtype=np.uint8)
+    m[:, sorted(cols)] = 1
+    return m

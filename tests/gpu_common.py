@@ -31,7 +31,8 @@ def ctx_for(cfg, wl, precision):
 def op_for(cfg, wl):
     import torch
     from paper_2605_19705_gb300 import binding as B
-    kind = {"blur": B.IDEQ_OP_BLUR, "mask": B.IDEQ_OP_MASK, "satblur": B.IDEQ_OP_SATBLUR}[cfg["op"]]
+    kind = {"blur": B.IDEQ_OP_BLUR, "mask": B.IDEQ_OP_MASK, "satblur": B.IDEQ_OP_SATBLUR,
+            "mri": B.IDEQ_OP_MRI}[cfg["op"]]
     kern = None if wl["kern"] is None else torch.tensor(wl["kern"], device="cuda").contiguous()
     mask = None if wl["mask"] is None else torch.tensor(wl["mask"], device="cuda").contiguous()
     return B.make_operator(kind, kern, mask, cfg.get("sat_gain", 2.0))

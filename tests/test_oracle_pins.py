@@ -175,16 +175,17 @@ def test_hvp_symmetric_and_matches_fd_of_gradient():
 # ------------------------------------------------------------ forward models
 
 
-@pytest.mark.parametrize("kind", ["blur", "mask", "satblur"])
+@pytest.mark.parametrize("kind", ["blur", "mask", "satblur", "mri"])
 def test_operator_adjoint_identity(kind):
     k = G.motion_kernel(5, 9)
-    m = G.bernoulli_mask(1, 12, 10, 0.3)
+    m = G.cartesian_mask(1, 12, 10, 2, 0.2) if kind == "mri" else G.bernoulli_mask(1, 12, 10, 0.3)
     op = operators.Operator(kind, kern=k, mask=m)
-    x, r = rnd(3, 12, 10), rnd(3, 12, 10)
+    c = 2 if kind == "mri" else 3
+    x, r = rnd(c, 12, 10), rnd(c, 12, 10)
     lin = (lambda v: operators.conv_circ(v, op.k)) if kind == "satblur" else op.A
     lhs = float(np.sum(lin(x) * r))
     assert abs(lhs - float(np.sum(x * op.AT(r)))) < 1e-13 * max(1.0, abs(lhs))
-    xl = RNG.uniform(0, 1, (3, 12, 10))
+    xl = RNG.uniform(0, 1, (c, 12, 10))
     lhs = float(np.sum(op.JA(xl, x) * r))
     assert abs(lhs - float(np.sum(x * op.JAT(xl, r)))) < 1e-13 * max(1.0, abs(lhs))
 
@@ -558,3 +559,77 @@ def test_averaging_step_of_a_constant_sequence_is_that_point():
     assert K0 == 4  # tie: the first minimiser
     with pytest.raises(ValueError):
         solver.averaging_step(zs[:4], [1.0, 0.5, 0.4, 0.3])
+
+
+def test_inpainting_prox_optimality_condition():
+    """prox_{tau f}(v) for the mask is the minimiser: its gradient condition
+    (x - v)/tau + M^T(M x - y) = 0 holds, and a perturbation raises the objective."""
+    rng = np.random.default_rng(21)
+    m = G.bernoulli_mask(4, 12, 10, 0.3)
+    op = operators.Operator("mask", mask=m)
+    y = m * rng.standard_normal((3, 12, 10))
+    v = rng.standard_normal((3, 12, 10))
+    tau = 0.7
+    x = op.prox_f(v, y, tau)
+    np.testing.assert_allclose((x - v) / tau + op.AT(op.A(x) - y), 0.0, atol=1e-13)
+    obj = lambda u: op.f(u, y) + 0.5 / tau * float(np.sum((u - v) ** 2))
+    assert obj(x) < obj(x + 1e-3 * rng.standard_normal(x.shape))
+    np.testing.assert_array_equal(x[:, m[0] == 0] if m.ndim == 3 else x[:, m == 0],
+                                  v[:, m[0] == 0] if m.ndim == 3 else v[:, m == 0])
+
+
+def test_proximal_variant_reaches_tikhonov_fixed_point():
+    """With N == 0 (g = 1/2||x||^2) the fixed point of x = prox_{tau f}(x - tau lam x)
+    is M y / (M + lam), the same Tikhonov point as the gradient form."""
+    lam, tau = 0.1, 0.75
+    net = zero_tail_unet(c=1)
+    m = G.bernoulli_mask(9, 16, 16, 0.3)
+    op = operators.Operator("mask", mask=m)
+    y = m * rnd(1, 16, 16)
+    x, info = solver.solve_image(net, op, y, op.AT(y), lam, tau, 0.8, math.inf, 1e-13, 5000,
+                                 prox=True)
+    assert info["status"] == solver.CONVERGED
+    np.testing.assert_allclose(x, m * y / (m + lam), atol=1e-10)
+
+
+def test_mri_operator_is_masked_unitary_dft_brute_force():
+    """A x = M . F x with F the orthonormal DFT, written out as a double sum over
+    pixels (no FFT) on an 8 x 6 complex image stored as (re, im) planes."""
+    h, w = 8, 6
+    m = G.cartesian_mask(3, h, w, 2, 0.2)
+    op = operators.Operator("mri", mask=m)
+    x = rnd(2, h, w)
+    xc = x[0] + 1j * x[1]
+    ref = np.zeros((h, w), complex)
+    for u in range(h):
+        for v in range(w):
+            s = 0j
+            for a in range(h):
+                for b in range(w):
+                    s += xc[a, b] * np.exp(-2j * np.pi * (u * a / h + v * b / w))
+            ref[u, v] = m[u, v] * s / np.sqrt(h * w)
+    np.testing.assert_allclose(op.A(x), np.stack([ref.real, ref.imag]), atol=1e-12)
+    # F unitary and M a projection: ||A x|| <= ||x||, equality on a fully sampled mask
+    full = operators.Operator("mri", mask=np.ones((h, w)))
+    assert abs(np.linalg.norm(full.A(x)) - np.linalg.norm(x)) < 1e-12
+    assert np.linalg.norm(op.A(x)) <= np.linalg.norm(x) + 1e-12
+
+
+def test_mri_prox_and_tikhonov_fixed_point():
+    """prox_{tau f} for MRI meets its optimality condition, and with N == 0 the
+    inertial solve reaches the Tikhonov point F^{-1}(M y / (M + lambda))."""
+    h, w = 16, 16
+    m = G.cartesian_mask(5, h, w, 4, 0.125)
+    op = operators.Operator("mri", mask=m)
+    y = op.A(rnd(2, h, w)) + m * 0.05 * rnd(2, h, w)
+    v = rnd(2, h, w)
+    tau, lam = 0.7, 0.1
+    x = op.prox_f(v, y, tau)
+    np.testing.assert_allclose((x - v) / tau + op.AT(op.A(x) - y), 0.0, atol=1e-12)
+    net = zero_tail_unet(c=2)
+    ref = np.fft.ifft2(m * (y[0] + 1j * y[1]) / (m + lam), norm="ortho")
+    for prox in (False, True):
+        xs, info = solver.solve_image(net, op, y, op.AT(y), lam, 0.75, 0.8, math.inf, 1e-13,
+                                      5000, prox=prox)
+        assert info["status"] == solver.CONVERGED
+        np.testing.assert_allclose(xs, np.stack([ref.real, ref.imag]), atol=1e-10)
