@@ -37,6 +37,8 @@ WORKLOADS = {
            "U-Net 64/128/256/512, lambda 0.1, tau 0.75, beta 0.8, tol 1e-4",
     "C5": "C5: 4 x complex 256x256 MRI (x4 Cartesian undersampling, 8% centre), "
           "k-space sigma 0.01, 2-channel U-Net 32/64/128/256, lambda 0.1, tau 0.75, beta 0.8, tol 1e-4",
+    "C6": "C6: 4 x grey 256x256 Rician denoising, sigma 0.1, U-Net 32/64/128/256, "
+          "lambda 0.1, tau 0.009, beta 0.8, tol 1e-4",
 }
 WORKLOAD = WORKLOADS["C1a"]
 
@@ -53,6 +55,9 @@ def make_op_and_y(B, cfg, wl, ctx, x_true, dev):
         m = torch.tensor(wl["mask"], device=dev)
         op = B.make_operator(B.IDEQ_OP_MRI, None, m)
         return op, B.ideq_apply_A(ctx, op, x_true) + noise * m[:, None].float()
+    if cfg["op"] == "rician":  # y = |x + n_re + i n_im|
+        op = B.make_operator(B.IDEQ_OP_RICIAN, sigma=cfg["noise_sigma"])
+        return op, torch.sqrt((x_true + noise[:, 0]) ** 2 + noise[:, 1] ** 2).contiguous()
     op = B.make_operator(B.IDEQ_OP_BLUR, torch.tensor(wl["kern"], device=dev))
     return op, B.ideq_apply_A(ctx, op, x_true) + noise
 

@@ -50,7 +50,8 @@ enum { IDEQ_IMG_RUNNING = 0, IDEQ_IMG_CONVERGED = 1, IDEQ_IMG_MAXITER = 2, IDEQ_
 
 enum { IDEQ_NET_CNN = 0, IDEQ_NET_UNET = 1 };
 enum { IDEQ_ACT_SOFTPLUS = 0, IDEQ_ACT_RELU = 1 };
-enum { IDEQ_OP_BLUR = 0, IDEQ_OP_MASK = 1, IDEQ_OP_SATBLUR = 2, IDEQ_OP_MRI = 3 };
+enum { IDEQ_OP_BLUR = 0, IDEQ_OP_MASK = 1, IDEQ_OP_SATBLUR = 2, IDEQ_OP_MRI = 3,
+       IDEQ_OP_RICIAN = 4 };
 /* Arithmetic of the regulariser network's convolutions: operands in FP32
  * (SIMT), BF16 or FP16 (tensor cores, FP32 accumulation), activations stored in
  * the operand type.  The _FP8 forms run the tensor-core convolutions whose
@@ -98,13 +99,17 @@ typedef struct { int n, c, h, w; } ideq_shape;  /* batch, channels, height, widt
  *                  c = 2 planes (re, im), F the orthonormal 2-D DFT, M_b a 0/1
  *                  k-space mask (n*h*w, unshifted FFT layout); y is complex
  *                  k-space in the same 2-plane layout, zero off the mask.
- *                  h and w must be powers of two in [8, 1024].              */
+ *                  h and w must be powers of two in [8, 1024].
+ *  IDEQ_OP_RICIAN  denoising under Rician noise (App. E): y = |x + n_re + i n_im|,
+ *                  f(x, y) = sum x^2/(2 s^2) - log I0(x y / s^2), s = sigma,
+ *                  grad f = x/s^2 - (y/s^2) I1/I0(x y / s^2) (A = identity).  */
 typedef struct {
   int kind;
   int kh, kw;              /* odd kernel sizes (<= 31) for blur kinds        */
   const float *kernel;     /* device, n*kh*kw, row-major per image            */
   const uint8_t *mask;     /* device, n*h*w, values 0/1 (mask kind)           */
   float sat_gain;          /* s for IDEQ_OP_SATBLUR                           */
+  float sigma;             /* noise level of IDEQ_OP_RICIAN (> 0)             */
 } ideq_operator;
 
 /* Parameters of the inertial iteration (Algorithm 1; beta = 1 - alpha of

@@ -10,6 +10,9 @@ of shape (c, h, w); blur kernels and masks are shared by the c channels.
   blur    : A x = k * x, circular 2-D convolution, kernel centre (kh//2, kw//2)
   mask    : A x = M . x, M in {0,1}^(h,w)                    (App. E, inpainting)
   satblur : A x = tanh(s (k * x)) / tanh(s), a smooth saturation after the blur
+  rician  : denoising under Rician noise (App. E): f(x, y) = sum x^2 / (2 s^2)
+            - log I0(x y / s^2), grad f = x / s^2 - (y / s^2) I1/I0(x y / s^2), with
+            SciPy's exponentially scaled Bessel functions i0e, i1e as the primitive
   mri     : A x = M . F x for a complex image x stored as (re, im) channels, F the
             orthonormal 2-D DFT, M in {0,1}^(h,w) a k-space mask (App. E, MRI);
             A^T r = F^{-1}(M . r), prox_{tau f}(v) = F^{-1}((tau M y + F v) / (tau M + 1))
@@ -54,8 +57,11 @@ def _planes(z):
 class Operator:
     """Forward model of one image: kind in {"blur", "mask", "satblur", "mri"}."""
 
-    def __init__(self, kind, kern=None, mask=None, gain=2.0):
+    def __init__(self, kind, kern=None, mask=None, gain=2.0, sigma=None):
         self.kind = kind
+        self.sigma = None if sigma is None else float(sigma)
+        if kind == "rician" and not (self.sigma and self.sigma > 0):
+            raise ValueError("Rician operator needs sigma > 0")
         self.k = None if kern is None else np.asarray(kern, dtype=np.float64)
         self.m = None if mask is None else np.asarray(mask, dtype=np.float64)
         self.s = float(gain)
@@ -69,6 +75,8 @@ class Operator:
         return self.kind != "satblur"
 
     def A(self, x):
+        if self.kind == "rician":
+            return np.asarray(x, np.float64)
         if self.kind == "blur":
             return conv_circ(x, self.k)
         if self.kind == "mask":
@@ -85,6 +93,8 @@ class Operator:
         paper leaves x0 free, Alg. 1), not a Jacobian transpose."""
         if self.kind == "mask":
             return self.m * r
+        if self.kind == "rician":
+            return np.asarray(r, np.float64)
         if self.kind == "mri":
             return _planes(np.fft.ifft2(self.m * _cplx(r), norm="ortho"))
         return corr_circ(r, self.k)
@@ -107,10 +117,20 @@ class Operator:
 
     # data term -------------------------------------------------------------
     def f(self, x, y) -> float:
+        if self.kind == "rician":  # log I0(t) = |t| + log i0e(t)
+            from scipy.special import i0e
+            s2 = self.sigma ** 2
+            t = x * y / s2
+            return float(np.sum(x * x / (2 * s2) - (np.abs(t) + np.log(i0e(t)))))
         e = self.A(x) - y
         return 0.5 * float(np.sum(e * e))
 
     def grad_f(self, x, y):
+        if self.kind == "rician":  # I1/I0 = i1e/i0e
+            from scipy.special import i0e, i1e
+            s2 = self.sigma ** 2
+            t = x * y / s2
+            return x / s2 - (y / s2) * (i1e(t) / i0e(t))
         return self.JAT(x, self.A(x) - y)
 
     def prox_f(self, v, y, tau):
@@ -130,6 +150,14 @@ class Operator:
         J_A^T J_A u + sum_i (A(x)-y)_i Hess(A_i) u; the second term vanishes for
         linear A.  For satblur, Hess(A_i) = (s/t)(-2 s tanh(s q_i) sech^2(s q_i))
         grad q_i grad q_i^T with q = k * x and t = tanh s."""
+        if self.kind == "rician":  # (1/s^2 - (y/s^2)^2 B'(t)) u, B' = 1 - B/t - B^2
+            from scipy.special import i0e, i1e
+            s2 = self.sigma ** 2
+            t = x * y / s2
+            B = i1e(t) / i0e(t)
+            with np.errstate(divide="ignore", invalid="ignore"):
+                Bp = np.where(np.abs(t) > 1e-8, 1.0 - B / t - B * B, 0.5)
+            return (1.0 / s2 - (y / s2) ** 2 * Bp) * u
         out = self.JAT(x, self.JA(x, u))
         if self.kind == "satblur":
             q = conv_circ(x, self.k)
@@ -160,7 +188,8 @@ def make_operators(cfg: dict, wl: dict):
     for i in range(cfg["n"]):
         kern = None if wl["kern"] is None else wl["kern"][i]
         mask = None if wl["mask"] is None else wl["mask"][i]
-        ops.append(Operator(cfg["op"], kern, mask, cfg.get("sat_gain", 2.0)))
+        sigma = cfg["noise_sigma"] if cfg["op"] == "rician" else None
+        ops.append(Operator(cfg["op"], kern, mask, cfg.get("sat_gain", 2.0), sigma))
     return ops
 
 
@@ -173,6 +202,9 @@ def observe(ops, x_true, noise, mask=None):
             ys.append(op.m * (x_true[i].astype(np.float64) + noise[i]))
         elif op.kind == "mri":
             ys.append(op.A(x_true[i].astype(np.float64)) + op.m * noise[i])
+        elif op.kind == "rician":  # magnitude of x + n_re + i n_im (App. E)
+            x = x_true[i].astype(np.float64)
+            ys.append(np.sqrt((x + noise[i][0]) ** 2 + noise[i][1] ** 2))
         else:
             ys.append(op.A(x_true[i].astype(np.float64)) + noise[i])
     return np.stack(ys)

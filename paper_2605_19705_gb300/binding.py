@@ -27,7 +27,7 @@ IDEQ_MAXITER, IDEQ_DIVERGED, IDEQ_ADJ_MAXITER, IDEQ_ERR_TIMEOUT = 5, 6, 7, 8
 IDEQ_IMG_RUNNING, IDEQ_IMG_CONVERGED, IDEQ_IMG_MAXITER, IDEQ_IMG_DIVERGED = 0, 1, 2, 3
 IDEQ_NET_CNN, IDEQ_NET_UNET = 0, 1
 IDEQ_ACT_SOFTPLUS, IDEQ_ACT_RELU = 0, 1
-IDEQ_OP_BLUR, IDEQ_OP_MASK, IDEQ_OP_SATBLUR, IDEQ_OP_MRI = 0, 1, 2, 3
+IDEQ_OP_BLUR, IDEQ_OP_MASK, IDEQ_OP_SATBLUR, IDEQ_OP_MRI, IDEQ_OP_RICIAN = 0, 1, 2, 3, 4
 IDEQ_FP32, IDEQ_BF16, IDEQ_BF16_FP8, IDEQ_FP16, IDEQ_FP16_FP8 = 0, 1, 2, 3, 4
 IDEQ_INIT_ATY, IDEQ_INIT_X0, IDEQ_INIT_WARM = 0, 1, 2
 IDEQ_ADJ_JFB, IDEQ_ADJ_IMPLICIT = 0, 1
@@ -44,7 +44,7 @@ class Shape(ctypes.Structure):
 
 class Operator(ctypes.Structure):
     _fields_ = [("kind", c_int), ("kh", c_int), ("kw", c_int), ("kernel", c_void_p),
-                ("mask", c_void_p), ("sat_gain", c_float)]
+                ("mask", c_void_p), ("sat_gain", c_float), ("sigma", c_float)]
 
 
 class Params(ctypes.Structure):
@@ -178,7 +178,8 @@ class Context:
             pass
 
 
-def make_operator(kind: int, kernel=None, mask=None, sat_gain: float = 2.0) -> Operator:
+def make_operator(kind: int, kernel=None, mask=None, sat_gain: float = 2.0,
+                  sigma: float = 0.0) -> Operator:
     """Operator struct; kernel (n,kh,kw) f32 / mask (n,h,w) u8 CUDA tensors stay owned
     by the caller and must outlive the calls that use it."""
     import torch
@@ -190,6 +191,7 @@ def make_operator(kind: int, kernel=None, mask=None, sat_gain: float = 2.0) -> O
     if mask is not None:
         op.mask = _ptr(mask, torch.uint8)
     op.sat_gain = sat_gain
+    op.sigma = sigma
     op._keep = (kernel, mask)
     return op
 

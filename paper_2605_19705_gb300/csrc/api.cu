@@ -103,6 +103,7 @@ ideq_status check_op(ideq_ctx* ctx, const ideq_operator* op, const ideq_shape& s
   od->kernel = op->kernel;
   od->mask = op->mask;
   od->gain = op->sat_gain;
+  od->sigma = op->sigma;
   if (op->kind == IDEQ_OP_BLUR || op->kind == IDEQ_OP_SATBLUR) {
     if (!op->kernel) return fail(ctx, IDEQ_ERR_ARG, "blur operator needs a kernel");
     if (op->kh < 1 || op->kw < 1 || op->kh > 31 || op->kw > 31 || !(op->kh & 1) || !(op->kw & 1))
@@ -112,6 +113,8 @@ ideq_status check_op(ideq_ctx* ctx, const ideq_operator* op, const ideq_shape& s
       return fail(ctx, IDEQ_ERR_ARG, "sat_gain must be > 0");
   } else if (op->kind == IDEQ_OP_MASK) {
     if (!op->mask) return fail(ctx, IDEQ_ERR_ARG, "mask operator needs a mask");
+  } else if (op->kind == IDEQ_OP_RICIAN) {
+    if (!(op->sigma > 0.f)) return fail(ctx, IDEQ_ERR_ARG, "Rician operator needs sigma > 0");
   } else if (op->kind == IDEQ_OP_MRI) {
     if (!op->mask) return fail(ctx, IDEQ_ERR_ARG, "MRI operator needs a k-space mask");
     if (s.c != 2) return fail(ctx, IDEQ_ERR_ARG, "MRI images are complex: c = 2 (re, im)");
@@ -220,6 +223,10 @@ cudaError_t data_grad(ideq_ctx* ctx, const OpDev& od, const ideq_shape& s, const
     ctx->launches += 5;
     return launch_mri_grad(s.n, s.h, s.w, z, y, od.mask, tmp, gf, fsum, st);
   }
+  if (od.kind == IDEQ_OP_RICIAN) {
+    ctx->launches += 1;
+    return launch_rician_grad(s.n, s.c * s.h * s.w, z, y, od.sigma, gf, fsum, st);
+  }
   cudaError_t e = launch_data_fwd(od, s.n, s.c, s.h, s.w, z, y, tmp, fsum, st);
   if (e != cudaSuccess) return e;
   ctx->launches += 2;
@@ -235,6 +242,9 @@ cudaError_t back_project(ideq_ctx* ctx, const OpDev& od, const ideq_shape& s, co
     ctx->launches += 2;
     return launch_mri_apply(s.n, s.h, s.w, y, od.mask, 1, out, ctx->stream);
   }
+  if (od.kind == IDEQ_OP_RICIAN)  // A = identity: x0 = y
+    return cudaMemcpyAsync(out, y, (size_t)s.n * s.c * s.h * s.w * 4, cudaMemcpyDeviceToDevice,
+                           ctx->stream);
   return launch_blur_adj(od, s.n, s.c, s.h, s.w, y, out, ctx->stream);
 }
 
@@ -520,6 +530,11 @@ ideq_status ideq_apply_A(ideq_ctx* ctx, const ideq_operator* op, ideq_shape shap
     ctx->launches += 3;
     return IDEQ_OK;
   }
+  if (od.kind == IDEQ_OP_RICIAN) {  // A = identity
+    CK(cudaMemcpyAsync(Ax, x, (size_t)shape.n * shape.c * shape.h * shape.w * 4,
+                       cudaMemcpyDeviceToDevice, ctx->stream));
+    return IDEQ_OK;
+  }
   CK(launch_apply_A(od, shape.n, shape.c, shape.h, shape.w, x, Ax, ctx->stream));
   ctx->launches += 1;
   return IDEQ_OK;
@@ -686,7 +701,7 @@ ideq_status ideq_solve_backward(ideq_ctx* ctx, const ideq_operator* op, ideq_sha
   OpDev od;
   if ((s = check_op(ctx, op, shape, &od)) != IDEQ_OK) return s;
   if (p->prox) return fail(ctx, IDEQ_ERR_UNSUPPORTED, "backward of the proximal variant");
-  if (od.kind == IDEQ_OP_SATBLUR)
+  if (od.kind == IDEQ_OP_SATBLUR || od.kind == IDEQ_OP_RICIAN)
     return fail(ctx, IDEQ_ERR_UNSUPPORTED, "backward supports linear operators (blur, mask, MRI)");
   if (ap->mode != IDEQ_ADJ_JFB && ap->mode != IDEQ_ADJ_IMPLICIT)
     return fail(ctx, IDEQ_ERR_ARG, "adjoint mode");

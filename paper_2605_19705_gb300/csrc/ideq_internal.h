@@ -110,7 +110,12 @@ struct OpDev {
   const float* kernel;
   const uint8_t* mask;
   float gain;
+  float sigma;  // Rician noise level
 };
+// Rician data term (App. E), A = identity: gf = x/s^2 - (y/s^2) I1/I0(x y/s^2),
+// fsum += sum x^2/(2 s^2) - log I0(x y/s^2) per image (n images of per_img values).
+cudaError_t launch_rician_grad(int n, int per_img, const float* x, const float* y, float sigma,
+                               float* gf, double* fsum, cudaStream_t st);
 // e = A(in) - y (y nullable): writes to `out` the vector fed to the adjoint
 // pass (e for linear blur; J-weighted e for satblur; M.(M.in - y) directly
 // for the mask, which needs no second pass) and accumulates 1/2||e||^2 per

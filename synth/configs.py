@@ -77,6 +77,13 @@ CONFIGS = {
                lam=0.1, tau=0.75, beta=0.8, B=INF, tol=1e-4, max_iter=3000,
                precision="fp32",
                seeds={"img": 8000, "noise": 8100, "weights": 2005, "kernel": 0, "mask": 8200}),
+    # Rician denoising (App. E): 4 grey 256^2 images, y = |x + n_re + i n_im| with
+    # sigma 25.5/255; L_f = 1/sigma^2, so tau ~ 0.9 sigma^2.
+    "C6": dict(n=4, c=1, h=256, w=256, op="rician", kernel=None,
+               noise_sigma=0.1, net=UNET_HALF,
+               lam=0.1, tau=0.009, beta=0.8, B=INF, tol=1e-4, max_iter=3000,
+               precision="fp32",
+               seeds={"img": 8500, "noise": 8600, "weights": 2006, "kernel": 0, "mask": 0}),
 }
 CONFIGS["C2"] = dict(copy.deepcopy(CONFIGS["C1a"]), precision="bf16")
 
@@ -135,6 +142,8 @@ def workload(cfg: dict) -> dict:
         sig = rng.uniform(ns[0], ns[1], n)
         noise = np.stack([G.gaussian_noise(s["noise"] + i, (c, h, w), float(sig[i]))
                           for i in range(n)])
+    elif cfg["op"] == "rician":  # real and imaginary noise fields
+        noise = np.stack([G.gaussian_noise(s["noise"] + i, (2, c, h, w), ns) for i in range(n)])
     else:
         noise = np.stack([G.gaussian_noise(s["noise"] + i, (c, h, w), ns) for i in range(n)])
     out = dict(x_true=x_true, kern=kern, mask=mask, noise=noise,

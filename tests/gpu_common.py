@@ -32,10 +32,11 @@ def op_for(cfg, wl):
     import torch
     from paper_2605_19705_gb300 import binding as B
     kind = {"blur": B.IDEQ_OP_BLUR, "mask": B.IDEQ_OP_MASK, "satblur": B.IDEQ_OP_SATBLUR,
-            "mri": B.IDEQ_OP_MRI}[cfg["op"]]
+            "mri": B.IDEQ_OP_MRI, "rician": B.IDEQ_OP_RICIAN}[cfg["op"]]
     kern = None if wl["kern"] is None else torch.tensor(wl["kern"], device="cuda").contiguous()
     mask = None if wl["mask"] is None else torch.tensor(wl["mask"], device="cuda").contiguous()
-    return B.make_operator(kind, kern, mask, cfg.get("sat_gain", 2.0))
+    sigma = cfg["noise_sigma"] if cfg["op"] == "rician" else 0.0
+    return B.make_operator(kind, kern, mask, cfg.get("sat_gain", 2.0), sigma)
 
 
 def rel(a, b) -> float:

@@ -301,6 +301,30 @@ def test_mri_solve_matches_oracle_fp32(prox):
         assert abs(float(info.energy[i]) - infos[i]["energy"]) < 1e-5 * infos[i]["energy"]
 
 
+def test_rician_solve_matches_oracle_fp32():
+    """Rician denoising (App. E): 30 inertial updates on two grey 64^2 images with the
+    library's own I1/I0 ratio (series below t = 15, Hankel expansion above) against
+    the oracle's SciPy i1e/i0e; t = x y / sigma^2 spans ~0..100 here."""
+    cfg, wl, net, ops, ys = setup("C6", n=2, h=64, w=64)
+    b = B()
+    x0 = np.stack([ops[i].AT(ys[i].astype(np.float64)) for i in range(2)])
+    xo, infos = solver.solve_batch(net, ops, ys.astype(np.float64), x0, cfg["lam"], cfg["tau"],
+                                   cfg["beta"], math.inf, 0.0, 30)
+    ctx = ctx_for(cfg, wl, b.IDEQ_FP32)
+    params = b.make_params(cfg["lam"], cfg["tau"], cfg["beta"], max_iter=30)
+    info = b.InfoBuffers(2)
+    y = torch.tensor(ys, device="cuda")
+    op = op_for(cfg, wl)
+    x, st = b.ideq_solve(ctx, op, y, params, info=info, allow_maxiter=True)
+    assert rel(to_np(x), xo) < 1e-5
+    for i in range(2):
+        assert abs(float(info.energy[i]) - infos[i]["energy"]) < 1e-5 * abs(infos[i]["energy"])
+    assert np.array_equal(to_np(b.ideq_apply_A(ctx, op, y)), ys.astype(np.float64))
+    with pytest.raises(b.IdeqError) as e:  # no closed-form prox for the Rician term
+        b.ideq_solve(ctx, op, y, b.make_params(cfg["lam"], cfg["tau"], cfg["beta"], prox=True))
+    assert e.value.status == b.IDEQ_ERR_UNSUPPORTED
+
+
 def test_mri_rejects_sizes_without_fft():
     cfg, wl, net, ops, ys = setup("C5", n=1, h=48, w=64)  # 48 is not a power of two
     b = B()

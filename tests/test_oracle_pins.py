@@ -633,3 +633,36 @@ def test_mri_prox_and_tikhonov_fixed_point():
                                       5000, prox=prox)
         assert info["status"] == solver.CONVERGED
         np.testing.assert_allclose(xs, np.stack([ref.real, ref.imag]), atol=1e-10)
+
+
+def test_rician_data_term_is_the_negative_log_likelihood():
+    """f(x, y) + y^2/(2 s^2) - log(y / s^2) is -log p(y | x) of the Rician density
+    (App. E): exp of its negative integrates to 1 over y >= 0, for several x."""
+    from scipy.integrate import quad
+    s = 0.1
+    op = operators.Operator("rician", sigma=s)
+    for xv in (0.0, 0.05, 0.3, 0.9):
+        dens = lambda y: math.exp(-(op.f(np.array([xv]), np.array([y])) + y * y / (2 * s * s)
+                                    - math.log(y / (s * s)))) if y > 0 else 0.0
+        total, _ = quad(dens, 0.0, xv + 12 * s, limit=200)
+        assert abs(total - 1.0) < 1e-7, (xv, total)
+
+
+def test_rician_gradient_and_hessian_finite_differences():
+    s = 0.1
+    op = operators.Operator("rician", sigma=s)
+    x = RNG.uniform(0.05, 1.0, (1, 6, 5))
+    y = np.sqrt((x + s * rnd(1, 6, 5)) ** 2 + (s * rnd(1, 6, 5)) ** 2)
+    g = op.grad_f(x, y)
+    h = 1e-7
+    for idx in [(0, 0, 0), (0, 3, 2), (0, 5, 4)]:
+        e = np.zeros_like(x)
+        e[idx] = h
+        fd = (op.f(x + e, y) - op.f(x - e, y)) / (2 * h)
+        assert abs(fd - g[idx]) < 1e-6 * max(1.0, abs(g[idx]))
+    u = rnd(1, 6, 5)
+    eps = 1e-6
+    fd = (op.grad_f(x + eps * u, y) - op.grad_f(x - eps * u, y)) / (2 * eps)
+    np.testing.assert_allclose(op.hvp_f(x, y, u), fd, rtol=1e-6, atol=1e-4)
+    # special case: y = 0 leaves the quadratic term only
+    np.testing.assert_allclose(op.grad_f(x, np.zeros_like(x)), x / s ** 2, rtol=1e-15)
