@@ -41,6 +41,12 @@ struct ideq_ctx {
   float* gf = nullptr;
   float* tmp = nullptr;
   float* ubuf = nullptr;      // adjoint solution u
+  // spectral blur data step (power-of-two images): kernel and observation spectra,
+  // packed scratch; `spectral` is set per call by prepare_data_step
+  float* khat = nullptr;
+  float* yhat = nullptr;
+  float* pk = nullptr;
+  bool spectral = false;
   double* dot_part = nullptr;
   double* fsum = nullptr;
   double* gsum = nullptr;
@@ -152,6 +158,10 @@ ideq_status ensure_plan(ideq_ctx* ctx, const ideq_shape& s) {
   const size_t o_x0 = take(img), o_x1 = take(img), o_gf = take(img), o_tmp = take(img);
   const size_t o_i = take((size_t)n * 4 * 8), o_f = take((size_t)n * 4), o_d = take((size_t)n * 8 * 6);
   const size_t o_zs = take(2 * img), o_zn = take(2 * img);  // FP64 sums of the averaging step
+  const bool pow2 = fft_size_ok(s.h) && fft_size_ok(s.w);
+  const size_t pk_bytes = (size_t)n * ((s.c + 1) / 2) * 2 * s.h * s.w * 4;
+  const size_t o_kh = pow2 ? take((size_t)n * 2 * s.h * s.w * 4) : 0;
+  const size_t o_yh = pow2 ? take(pk_bytes) : 0, o_pk = pow2 ? take(pk_bytes) : 0;
   const size_t o_p = take((size_t)n * nblk * 8 * 2), o_r = take(16), o_dp = take(128 * 8);
   const size_t o_u = take(img);
   char* m = nullptr;
@@ -185,6 +195,9 @@ ideq_status ensure_plan(ideq_ctx* ctx, const ideq_shape& s) {
   v.n_running = (int*)(m + o_r);
   v.loop_count = v.n_running + 1;
   ctx->dot_part = (double*)(m + o_dp);
+  ctx->khat = pow2 ? (float*)(m + o_kh) : nullptr;
+  ctx->yhat = pow2 ? (float*)(m + o_yh) : nullptr;
+  ctx->pk = pow2 ? (float*)(m + o_pk) : nullptr;
   ctx->ubuf = (float*)(m + o_u);
   ctx->fsum = v.fsum;
   ctx->gsum = v.gsum;
@@ -211,10 +224,41 @@ float* ensure_scratch(ideq_ctx* ctx, size_t bytes) {
   return ctx->scratch;
 }
 
+// IDEQ_SPECTRAL=0 keeps the blur data step on the direct stencils (for comparisons).
+bool spectral_enabled() {
+  static const bool on = [] {
+    const char* v = std::getenv("IDEQ_SPECTRAL");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
+
+// Before a solve / step / backward: choose the blur's data-step form and, for the
+// spectral form, compute the kernel spectra and (when y is given) the spectrum of y.
+// The spectral form serves the large kernels (>= 15 x 15 taps, where the stencil's
+// kh * kw FMAs per pixel dominate); small kernels keep the exact stencil, whose f is
+// not subject to the FFT's cancellation near the fixed point.
+cudaError_t prepare_data_step(ideq_ctx* ctx, const OpDev& od, const ideq_shape& s,
+                              const float* y) {
+  ctx->spectral = od.kind == IDEQ_OP_BLUR && ctx->khat && od.kh * od.kw >= 225 &&
+                  spectral_enabled();
+  if (!ctx->spectral) return cudaSuccess;
+  cudaError_t e = launch_blur_spectrum(s.n, s.h, s.w, od.kh, od.kw, od.kernel, ctx->khat,
+                                       ctx->stream);
+  if (e == cudaSuccess && y) e = launch_pack_fft(s.n, s.c, s.h, s.w, y, ctx->yhat, ctx->stream);
+  ctx->launches += 6;
+  return e;
+}
+
 // grad f(z) = J_A(z)^T (A(z) - y) into gf, 1/2||A z - y||^2 into fsum.
 cudaError_t data_grad(ideq_ctx* ctx, const OpDev& od, const ideq_shape& s, const float* z,
                       const float* y, float* gf, float* tmp, double* fsum) {
   cudaStream_t st = ctx->stream;
+  if (ctx->spectral && od.kind == IDEQ_OP_BLUR) {  // y here is the y prepare_data_step saw
+    ctx->launches += 7;
+    return launch_blur_grad_spectral(s.n, s.c, s.h, s.w, z, ctx->khat, y ? ctx->yhat : nullptr,
+                                     ctx->pk, gf, fsum, st);
+  }
   if (od.kind == IDEQ_OP_MASK) {
     ctx->launches += 1;
     return launch_data_fwd(od, s.n, s.c, s.h, s.w, z, y, gf, fsum, st);
@@ -588,6 +632,7 @@ ideq_status ideq_step(ideq_ctx* ctx, const ideq_operator* op, ideq_shape shape, 
   if (p->prox && od.kind != IDEQ_OP_MASK && od.kind != IDEQ_OP_MRI)
     return fail(ctx, IDEQ_ERR_UNSUPPORTED, "the proximal step has a closed form for mask and MRI");
   if ((s = ensure_plan(ctx, shape)) != IDEQ_OK) return s;
+  CK(prepare_data_step(ctx, od, shape, y));
   const size_t bytes = (size_t)shape.n * shape.c * shape.h * shape.w * 4;
   cudaStream_t st = ctx->stream;
   CK(cudaMemcpyAsync(ctx->xb[0], x_k, bytes, cudaMemcpyDeviceToDevice, st));
@@ -617,6 +662,7 @@ ideq_status ideq_solve(ideq_ctx* ctx, const ideq_operator* op, ideq_shape shape,
   if (p->average && (p->tol > 0.0 || restart_on || p->max_iter < 5))
     return fail(ctx, IDEQ_ERR_ARG, "averaging needs tol = 0, no restart and max_iter >= 5");
   if ((s = ensure_plan(ctx, shape)) != IDEQ_OK) return s;
+  CK(prepare_data_step(ctx, od, shape, y));
   const size_t bytes = (size_t)shape.n * shape.c * shape.h * shape.w * 4;
   cudaStream_t st = ctx->stream;
   if (p->init == IDEQ_INIT_X0) {
@@ -709,6 +755,7 @@ ideq_status ideq_solve_backward(ideq_ctx* ctx, const ideq_operator* op, ideq_sha
                                         !(ap->beta >= 0.f && ap->beta < 1.f)))
     return fail(ctx, IDEQ_ERR_ARG, "adjoint tol > 0, max_iter >= 1, 0 <= beta < 1");
   if ((s = ensure_plan(ctx, shape)) != IDEQ_OK) return s;
+  CK(prepare_data_step(ctx, od, shape, y));
   if (!ctx->train) {
     std::unique_ptr<TrainPlan> tp(new TrainPlan());
     std::string e;

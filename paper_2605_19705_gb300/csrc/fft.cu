@@ -194,3 +194,125 @@ cudaError_t launch_mri_prox(int n, int H, int W, const float* v, const float* y,
 }
 
 }  // namespace ideq
+
+// ===================================================================== spectral blur
+//
+// The circular blur A x = k * x is diagonal in the DFT basis: with the unitary F,
+// F(k * x) = sqrt(hw) F(k~) F(x), k~ the kernel placed on the h x w torus with its
+// centre at the origin.  For power-of-two images the data step runs there:
+//   E = K Z - Y  (K = sqrt(hw) F k~, Z = F z, Y = F y),  f = 1/2 ||E||^2 (Parseval),
+//   grad f = F^{-1}(conj(K) E).
+// Real images are packed two channels per complex image (re = channel 2p,
+// im = channel 2p+1, zero when c is odd); the kernel is real, so each part of the
+// packed product is the blur of its own channel.
+
+namespace ideq {
+
+// khat[b] (complex plane pair) <- kernel b embedded on the torus, centre at (0, 0)
+__global__ void blur_embed_kernel(int H, int W, int kh, int kw, const float* __restrict__ ker,
+                                  float* __restrict__ khat) {
+  const int b = blockIdx.y;
+  const int hw = H * W;
+  for (int p = blockIdx.x * 256 + threadIdx.x; p < hw; p += gridDim.x * 256) {
+    const int i = p / W, j = p % W;
+    // tap (u, v) lands at ((u - cy) mod H, (v - cx) mod W)
+    int u = i + kh / 2, v = j + kw / 2;
+    u -= (u >= H) ? H : 0;
+    v -= (v >= W) ? W : 0;
+    float val = 0.f;
+    if (u < kh && v < kw) val = ker[(size_t)b * kh * kw + u * kw + v];
+    khat[(size_t)b * 2 * hw + p] = val;
+    khat[(size_t)b * 2 * hw + hw + p] = 0.f;
+  }
+}
+
+// pk[b][p] (re, im) <- x[b][2p], x[b][2p+1]
+__global__ void pack_pairs_kernel(int c, int hw, const float* __restrict__ x,
+                                  float* __restrict__ pk) {
+  const int b = blockIdx.y, cc = (c + 1) / 2;
+  for (int q = blockIdx.x * 256 + threadIdx.x; q < cc * hw; q += gridDim.x * 256) {
+    const int p = q / hw, e = q % hw;
+    const size_t o = ((size_t)b * cc + p) * 2 * hw + e;
+    pk[o] = x[((size_t)b * c + 2 * p) * hw + e];
+    pk[o + hw] = (2 * p + 1 < c) ? x[((size_t)b * c + 2 * p + 1) * hw + e] : 0.f;
+  }
+}
+
+__global__ void unpack_pairs_kernel(int c, int hw, const float* __restrict__ pk,
+                                    float* __restrict__ x) {
+  const int b = blockIdx.y, cc = (c + 1) / 2;
+  for (int q = blockIdx.x * 256 + threadIdx.x; q < cc * hw; q += gridDim.x * 256) {
+    const int p = q / hw, e = q % hw;
+    const size_t o = ((size_t)b * cc + p) * 2 * hw + e;
+    x[((size_t)b * c + 2 * p) * hw + e] = pk[o];
+    if (2 * p + 1 < c) x[((size_t)b * c + 2 * p + 1) * hw + e] = pk[o + hw];
+  }
+}
+
+// Z <- conj(K) (K Z - Y) per entry (Y = null: conj(K) K Z), with 1/2 |K Z - Y|^2
+// summed per image into fsum.  K is scaled by sqrt(hw) here.
+__global__ void __launch_bounds__(256) spectral_grad_kernel(int cc, int hw, float kscale,
+                                                            const float* __restrict__ khat,
+                                                            const float* __restrict__ Y,
+                                                            float* __restrict__ Z,
+                                                            double* __restrict__ fsum) {
+  __shared__ double red[32];
+  const int b = blockIdx.y;
+  double part = 0.0;
+  for (int q = blockIdx.x * 256 + threadIdx.x; q < cc * hw; q += gridDim.x * 256) {
+    const int p = q / hw, e = q % hw;
+    const float kr = kscale * khat[(size_t)b * 2 * hw + e];
+    const float ki = kscale * khat[(size_t)b * 2 * hw + hw + e];
+    const size_t o = ((size_t)b * cc + p) * 2 * hw + e;
+    const float zr = Z[o], zi = Z[o + hw];
+    float er = kr * zr - ki * zi, ei = kr * zi + ki * zr;
+    if (Y) {
+      er -= Y[o];
+      ei -= Y[o + hw];
+    }
+    part += 0.5 * ((double)er * er + (double)ei * ei);
+    Z[o] = kr * er + ki * ei;  // conj(K) E
+    Z[o + hw] = kr * ei - ki * er;
+  }
+  if (fsum) {
+    const double s = block_sum(part, red);
+    if (threadIdx.x == 0) atomicAdd(fsum + b, s);
+  }
+}
+
+static dim3 sgrid(int n, long long per) {
+  return dim3((unsigned)std::min<long long>((per + 255) / 256, 128), (unsigned)n);
+}
+
+cudaError_t launch_blur_spectrum(int n, int H, int W, int kh, int kw, const float* ker,
+                                 float* khat, cudaStream_t st) {
+  blur_embed_kernel<<<sgrid(n, (long long)H * W), 256, 0, st>>>(H, W, kh, kw, ker, khat);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_fft2(khat, khat, n, H, W, 0, st);
+}
+
+cudaError_t launch_pack_fft(int n, int c, int H, int W, const float* x, float* pk,
+                            cudaStream_t st) {
+  const int cc = (c + 1) / 2;
+  pack_pairs_kernel<<<sgrid(n, (long long)cc * H * W), 256, 0, st>>>(c, H * W, x, pk);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_fft2(pk, pk, n * cc, H, W, 0, st);
+}
+
+cudaError_t launch_blur_grad_spectral(int n, int c, int H, int W, const float* z,
+                                      const float* khat, const float* yhat, float* pk, float* gf,
+                                      double* fsum, cudaStream_t st) {
+  const int cc = (c + 1) / 2;
+  cudaError_t e = launch_pack_fft(n, c, H, W, z, pk, st);
+  if (e != cudaSuccess) return e;
+  spectral_grad_kernel<<<sgrid(n, (long long)cc * H * W), 256, 0, st>>>(
+      cc, H * W, sqrtf((float)(H * W)), khat, yhat, pk, fsum);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_fft2(pk, pk, n * cc, H, W, 1, st)) != cudaSuccess) return e;
+  unpack_pairs_kernel<<<sgrid(n, (long long)cc * H * W), 256, 0, st>>>(c, H * W, pk, gf);
+  return cudaGetLastError();
+}
+
+}  // namespace ideq

@@ -147,6 +147,18 @@ cudaError_t launch_mri_apply(int n, int H, int W, const float* x, const uint8_t*
 cudaError_t launch_mri_prox(int n, int H, int W, const float* v, const float* y,
                             const uint8_t* mask, float tau, float* out, cudaStream_t st);
 
+// Spectral form of the circular blur data step (power-of-two h, w): khat (n
+// complex planes) = F of each kernel on the torus; pk, yhat: n * ceil(c/2) complex
+// images (channel pairs).  grad f = F^{-1}(conj(K)(K F z - yhat)), fsum as usual;
+// yhat = null gives A^T A z.
+cudaError_t launch_blur_spectrum(int n, int H, int W, int kh, int kw, const float* ker,
+                                 float* khat, cudaStream_t st);
+cudaError_t launch_pack_fft(int n, int c, int H, int W, const float* x, float* pk,
+                            cudaStream_t st);
+cudaError_t launch_blur_grad_spectral(int n, int c, int H, int W, const float* z,
+                                      const float* khat, const float* yhat, float* pk, float* gf,
+                                      double* fsum, cudaStream_t st);
+
 // ------------------------------------------------------------- solver state
 struct SolverDev {
   int* k;          // steps since last restart
