@@ -21,13 +21,21 @@ __device__ __forceinline__ unsigned bitrev(unsigned v, int bits) {
   return __brev(v) >> (32 - bits);
 }
 
+// Shared-memory slot of entry i of a line: one pad slot per 32 entries, so that the
+// bit-reversed scatter of the load (consecutive e -> strides of N/2, N/4, ...)
+// and the butterflies of every stage spread over the banks.
+__device__ __forceinline__ int pad_slot(int i) { return i + (i >> 5); }
+
 // lines: G lines of length N; element e of line l of image b sits at
-// base_b + (l0 + l) * line_stride + e * elem_stride in both planes.
+// base_b + (l0 + l) * line_stride + e * elem_stride in both planes.  Lines are
+// N + N/32 + 1 float2 slots apart in shared memory (an odd count of 8-byte slots
+// modulo the 16 bank pairs, so the column-mode load hits distinct banks).
 __global__ void __launch_bounds__(FFT_THREADS) fft_lines_kernel(
-    const float* in, float* out, int N, int logN, int G,  // in and out may alias
+    const float* in, float* out, int N, int logN, int G, int logG,  // in and out may alias
     int lines_per_img, int line_stride, int elem_stride, int plane, int inverse) {
-  extern __shared__ float2 sm[];  // [G][N] data, then N/2 twiddles
-  float2* tw = sm + (size_t)G * N;
+  extern __shared__ float2 sm[];  // [G][N + N/32 + 1] data, then N/2 twiddles
+  const int LS = N + (N >> 5) + 1;
+  float2* tw = sm + (size_t)G * LS;
   const int b = blockIdx.y;
   const int l0 = blockIdx.x * G;
   const size_t ib = (size_t)b * 2 * plane;  // image base (re plane; im at + plane)
@@ -37,36 +45,39 @@ __global__ void __launch_bounds__(FFT_THREADS) fft_lines_kernel(
     sincospif(2.f * (float)k / (float)N, &s, &c);  // exp(-+ 2 pi i k / N)
     tw[k] = make_float2(c, inverse ? s : -s);
   }
-  for (int idx = threadIdx.x; idx < G * N; idx += FFT_THREADS) {
+  const int total = G << logN;
+  for (int idx = threadIdx.x; idx < total; idx += FFT_THREADS) {
     // consecutive threads walk consecutive addresses: along a row, or across columns
-    const int l = rows ? idx / N : idx % G;
-    const int e = rows ? idx % N : idx / G;
+    const int l = rows ? idx >> logN : idx & (G - 1);
+    const int e = rows ? idx & (N - 1) : idx >> logG;
     if (l0 + l >= lines_per_img) continue;
     const size_t o = ib + (size_t)(l0 + l) * line_stride + (size_t)e * elem_stride;
-    sm[(size_t)l * N + bitrev((unsigned)e, logN)] = make_float2(in[o], in[o + plane]);
+    sm[l * LS + pad_slot((int)bitrev((unsigned)e, logN))] = make_float2(in[o], in[o + plane]);
   }
   __syncthreads();
+  const int half = N >> 1, logh = logN - 1;
   for (int s = 0; s < logN; ++s) {
     const int m = 1 << s;  // butterfly half-span
-    for (int t = threadIdx.x; t < G * (N / 2); t += FFT_THREADS) {
-      const int l = t / (N / 2), k = t % (N / 2);
+    for (int t = threadIdx.x; t < (G << logh); t += FFT_THREADS) {
+      const int l = t >> logh, k = t & (half - 1);
       const int j = k & (m - 1), i0 = ((k >> s) << (s + 1)) + j;
-      float2* L = sm + (size_t)l * N;
-      const float2 w = tw[j << (logN - 1 - s)];
-      const float2 a = L[i0], bb = L[i0 + m];
+      float2* L = sm + l * LS;
+      const float2 w = tw[j << (logh - s)];
+      const int p0 = pad_slot(i0), p1 = pad_slot(i0 + m);
+      const float2 a = L[p0], bb = L[p1];
       const float2 wb = make_float2(w.x * bb.x - w.y * bb.y, w.x * bb.y + w.y * bb.x);
-      L[i0] = make_float2(a.x + wb.x, a.y + wb.y);
-      L[i0 + m] = make_float2(a.x - wb.x, a.y - wb.y);
+      L[p0] = make_float2(a.x + wb.x, a.y + wb.y);
+      L[p1] = make_float2(a.x - wb.x, a.y - wb.y);
     }
     __syncthreads();
   }
   const float scale = rsqrtf((float)N);
-  for (int idx = threadIdx.x; idx < G * N; idx += FFT_THREADS) {
-    const int l = rows ? idx / N : idx % G;
-    const int e = rows ? idx % N : idx / G;
+  for (int idx = threadIdx.x; idx < total; idx += FFT_THREADS) {
+    const int l = rows ? idx >> logN : idx & (G - 1);
+    const int e = rows ? idx & (N - 1) : idx >> logG;
     if (l0 + l >= lines_per_img) continue;
     const size_t o = ib + (size_t)(l0 + l) * line_stride + (size_t)e * elem_stride;
-    const float2 v = sm[(size_t)l * N + e];
+    const float2 v = sm[l * LS + pad_slot(e)];
     out[o] = v.x * scale;
     out[o + plane] = v.y * scale;
   }
@@ -86,23 +97,25 @@ cudaError_t launch_fft2(const float* in, float* out, int n, int H, int W, int in
                         cudaStream_t st) {
   if (!fft_size_ok(H) || !fft_size_ok(W)) return cudaErrorInvalidValue;
   const int plane = H * W;
-  // rows: G rows per block
+  // rows: G rows per block (G a power of two)
   {
     const int G = std::max(1, 4096 / W);
-    const size_t smem = (size_t)G * W * 8 + (size_t)(W / 2) * 8;
+    const int LS = W + W / 32 + 1;
+    const size_t smem = (size_t)G * LS * 8 + (size_t)(W / 2) * 8;
     dim3 grid((H + G - 1) / G, n);
-    fft_lines_kernel<<<grid, FFT_THREADS, smem, st>>>(in, out, W, ilog2(W), G, H, W, 1, plane,
-                                                      inverse);
+    fft_lines_kernel<<<grid, FFT_THREADS, smem, st>>>(in, out, W, ilog2(W), G, ilog2(G), H, W, 1,
+                                                      plane, inverse);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  // columns: G consecutive columns per block
+  // columns: G consecutive columns per block (G a power of two)
   {
     const int G = std::min(W, std::max(1, 4096 / H));
-    const size_t smem = (size_t)G * H * 8 + (size_t)(H / 2) * 8;
+    const int LS = H + H / 32 + 1;
+    const size_t smem = (size_t)G * LS * 8 + (size_t)(H / 2) * 8;
     dim3 grid((W + G - 1) / G, n);
-    fft_lines_kernel<<<grid, FFT_THREADS, smem, st>>>(out, out, H, ilog2(H), G, W, 1, W, plane,
-                                                      inverse);
+    fft_lines_kernel<<<grid, FFT_THREADS, smem, st>>>(out, out, H, ilog2(H), G, ilog2(G), W, 1, W,
+                                                      plane, inverse);
   }
   return cudaGetLastError();
 }
