@@ -52,6 +52,7 @@ struct TcArgs {
   const float* a_scale;  // FP8 operands: activation scale (device scalar)
   const float* w_scale;  // FP8 operands: weight scale per GEMM column
   int slide;             // halo form: contiguous row runs per CTA reusing row boxes
+  int stream;            // streamed halo: per stage one row box and the 3 dx taps of B
   // image-side output (BN = 16): out = aux + sign * acc, f32 planar, c <= 16 channels
   float sign;
   const float* img_aux;
@@ -64,7 +65,7 @@ struct TcPlan {
   CUtensorMap tmA, tmB, tmO[2], tmX[3];
   int bn = 0, stages = 0, op_dt = DT_BF16, epi_dt = DT_BF16, nout = 1, naux = 0, nbo = 2,
       nba = 2, ms = 1;
-  bool halo = false, slide = false;
+  bool halo = false, slide = false, stream = false;
   int Wt = 0, Ht = 0, tiles_w = 0, tiles_h = 0, tiles_n = 0, nk = 0, cpt = 0;
   dim3 grid;
   size_t smem = 0;
@@ -508,10 +509,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   static_assert(!HALO || MS == 1, "the halo form has one 128-row sub-tile");
   constexpr int B_BYTES = BN * 128;
   // ring slot: the A (and B) boxes of one K chunk; in the halo form the three row
-  // boxes of a tile, or a single row box in the sliding form
-  const int A_STAGE = HALO ? (a.slide ? HALO_BOX : 3 * HALO_BOX) : MS * A_BYTES;
+  // boxes of a tile, or a single row box in the sliding form; in the streamed halo
+  // form one row box and the three horizontal taps of B of one (row, channel chunk)
+  const bool STREAM = !HALO && a.stream;
+  const int A_STAGE =
+      HALO ? (a.slide ? HALO_BOX : 3 * HALO_BOX) : (STREAM ? HALO_BOX : MS * A_BYTES);
+  const int B_STAGE = STREAM ? 3 * B_BYTES : B_BYTES;
   const uint32_t STAGE_TX =
-      HALO ? (a.slide ? 1u : 3u) * HALO_ROWS * 128u : (uint32_t)(MS * A_BYTES + B_BYTES);
+      HALO ? (a.slide ? 1u : 3u) * HALO_ROWS * 128u
+           : (STREAM ? HALO_ROWS * 128u + 3u * B_BYTES : (uint32_t)(MS * A_BYTES + B_BYTES));
   constexpr bool IMG = BN == 16;  // image-side output: c <= 16 planar f32 channels
   constexpr int NPANEL = IMG ? 1 : BN / 64;
   constexpr int KCH = 128 / (int)sizeof(TA);  // K elements per 128-byte ring row
@@ -522,7 +528,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
   uint8_t* sB = smem + ST * A_STAGE;  // ring slots, or the resident weights (HALO)
-  uint8_t* sOut = sB + (HALO ? a.nk * B_BYTES : ST * B_BYTES);  // [warp][nbo][nout][WBOX]
+  uint8_t* sOut = sB + (HALO ? a.nk * B_BYTES : ST * B_STAGE);  // [warp][nbo][nout][WBOX]
   uint8_t* sAux = sOut + a.nbo * a.nout * PANEL;                 // [warp][nba][naux][WBOX]
   uint64_t* bars = (uint64_t*)(sAux + a.nba * a.naux * PANEL);
   uint32_t* tmem_slot = (uint32_t*)(bars + 2 * ST + 6 + 2 * EPI_WARPS);
@@ -622,7 +628,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
         }
       }
-      for (int i = 0; i < my_tiles && ok && !HALO; ++i) {
+      for (int i = 0; i < my_tiles && ok && STREAM; ++i) {  // streamed halo
+        const TileCoord tc = tile_coord(a, t_first + i * t_step, BN, MS, 0);
+        for (int kc = 0; kc < 3 * a.cpt; ++kc) {  // (row dy, channel chunk c)
+          const int s = g % ST, j = g / ST;
+          if (j > 0 && !mbar_wait(empty0 + 8 * s, (j - 1) & 1, a.err, 1)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(full0 + 8 * s, STAGE_TX);
+          const int dy = kc / a.cpt, c = kc - dy * a.cpt;
+          tma_load_4d(smem_u32(sA + s * A_STAGE), &tmA, c * KCH, tc.w0 - 1, tc.h0 + dy - 1, tc.img,
+                      full0 + 8 * s);
+          for (int dx = 0; dx < 3; ++dx)
+            tma_load_2d(smem_u32(sB + s * B_STAGE + dx * B_BYTES), &tmB,
+                        ((3 * dy + dx) * a.cpt + c) * KCH, tc.n0, full0 + 8 * s);
+          ++g;
+        }
+      }
+      for (int i = 0; i < my_tiles && ok && !HALO && !STREAM; ++i) {
         const int t = t_first + i * t_step;
         const TileCoord tc = tile_coord(a, t, BN, MS, 0);
         for (int kc = 0; kc < a.nk; ++kc) {
@@ -634,7 +658,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           mbar_expect_tx(full0 + 8 * s, STAGE_TX);
           const uint32_t dA = smem_u32(sA + s * A_STAGE);
           {
-            const uint32_t dB = smem_u32(sB + s * B_BYTES);
+            const uint32_t dB = smem_u32(sB + s * B_STAGE);
 #pragma unroll
             for (int sub = 0; sub < MS; ++sub) {
               const TileCoord sc = sub == 0 ? tc : tile_coord(a, t, BN, MS, sub);
@@ -734,6 +758,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const bool next_fresh = lt + 1 == my_tiles || (t + 1) % a.tiles_h == 0;
           for (int dy = 0; dy < (next_fresh ? 3 : 1); ++dy)
             umma_commit(empty0 + 8 * ((base + dy) % ST));
+        } else if (STREAM) {
+          for (int kc = 0; kc < 3 * a.cpt; ++kc) {
+            const int s = g % ST, j = g / ST;
+            if (!mbar_wait(full0 + 8 * s, j & 1, a.err, 3)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t abox = smem_u32(sA + s * A_STAGE);
+#pragma unroll 1
+            for (int dx = 0; dx < 3; ++dx) {
+              const uint64_t ad = umma_desc_sw128_rows(abox, dx);
+              const uint64_t bd = umma_desc_sw128(smem_u32(sB + s * B_STAGE + dx * B_BYTES));
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk)
+                umma<TA>(td, ad + 2 * kk, bd + 2 * kk, idesc, (kc | dx | kk) != 0 ? 1u : 0u);
+            }
+            umma_commit(empty0 + 8 * s);
+            ++g;
+          }
+          if (ok) umma_commit(tfull0 + 8 * b);
         } else {
           for (int kc = 0; kc < a.nk; ++kc) {
             const int s = g % ST, j = g / ST;
@@ -742,7 +787,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               break;
             }
             tc_fence_after();
-            const uint64_t bd = umma_desc_sw128(smem_u32(sB + s * B_BYTES));
+            const uint64_t bd = umma_desc_sw128(smem_u32(sB + s * B_STAGE));
 #pragma unroll
             for (int sub = 0; sub < MS; ++sub) {
               const uint64_t ad = umma_desc_sw128(smem_u32(sA + s * A_STAGE + sub * A_BYTES));
@@ -1039,22 +1084,28 @@ TcPlan* tc_plan_create(const ConvArgs& a, int op_dt, int epi_dt, std::string* er
   p->halo = op_dt != DT_FP8 && a.mode == CM_CONV3 && p->Wt == 128 && p->Ht == 1 && p->tiles_n == 1 &&
             p->cpt == 1 && bres <= 80 * 1024 && tiling_override("IDEQ_TC_HALO", 1) != 0;
   p->slide = p->halo && tiling_override("IDEQ_TC_SLIDE", 0) != 0;
+  // streamed halo: full-row 3x3 convs whose weights do not stay resident
+  p->stream = !p->halo && op_dt != DT_FP8 && a.mode == CM_CONV3 && p->Wt == 128 &&
+              p->Ht == 1 && p->tiles_n == 1 && p->bn <= 128 &&
+              tiling_override("IDEQ_TC_STREAM", 1) != 0;
   // Two 128-row sub-tiles can share each weight chunk (half the weight traffic
   // per FLOP), but measured on the U-Net layers the coarser tiles balance worse
   // over the SMs than they save, so M = 256 is used only when forced.
   p->ms = 1;
   {
     const int force_ms = tiling_override("IDEQ_TC_MS", 0);  // 2 forces two sub-tiles
-    if (!p->halo && p->bn <= 128 && force_ms == 2) p->ms = 2;
+    if (!p->halo && !p->stream && p->bn <= 128 && force_ms == 2) p->ms = 2;
   }
   // shared memory: ring depth and staging buffers, preferring a deep ring
   // (halo: >= 5 row boxes, three in use and two in flight; else >= 3 stages),
   // then double-buffered staging
-  const size_t stage = p->halo ? (size_t)(p->slide ? 1 : 3) * HALO_BOX
-                               : (size_t)p->ms * A_BYTES + (size_t)p->bn * 128;
+  const size_t stage = p->halo     ? (size_t)(p->slide ? 1 : 3) * HALO_BOX
+                       : p->stream ? (size_t)HALO_BOX + 3 * (size_t)p->bn * 128
+                                   : (size_t)p->ms * A_BYTES + (size_t)p->bn * 128;
   const size_t resident = p->halo ? bres : 0;
   p->stages = 0;
-  const int min_stages[2] = {p->halo ? (p->slide ? 5 : 3) : 3, p->halo ? (p->slide ? 4 : 2) : 2};
+  const int min_stages[2] = {p->halo ? (p->slide ? 5 : 3) : (p->stream ? 2 : 3),
+                             p->halo ? (p->slide ? 4 : 2) : 2};
   for (int min_st : min_stages) {
     for (int nbuf : {2, 1}) {
       int st = 8;
@@ -1108,7 +1159,8 @@ TcPlan* tc_plan_create(const ConvArgs& a, int op_dt, int epi_dt, std::string* er
     cuuint64_t dims[4] = {(cuuint64_t)a.Cin, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.n};
     cuuint64_t strides[3] = {(cuuint64_t)a.Cin * es, (cuuint64_t)a.W * a.Cin * es,
                              (cuuint64_t)a.H * a.W * a.Cin * es};
-    cuuint32_t box[4] = {(cuuint32_t)KCH, (cuuint32_t)(p->halo ? HALO_ROWS : p->Wt),
+    cuuint32_t box[4] = {(cuuint32_t)KCH,
+                         (cuuint32_t)((p->halo || p->stream) ? HALO_ROWS : p->Wt),
                          (cuuint32_t)p->Ht, 1};
     ok = encode(enc, &p->tmA, dt, 4, a.in, dims, strides, box);
   }
@@ -1212,6 +1264,7 @@ cudaError_t launch_conv_tc(const TcPlan* p, const ConvArgs& a, int* err_flag, cu
   t.nbo = p->nbo;
   t.nba = p->nba;
   t.slide = p->slide ? 1 : 0;
+  t.stream = p->stream ? 1 : 0;
   t.sign = a.sign;
   t.img_aux = (const float*)a.aux0;
   t.img_out = (float*)a.out;

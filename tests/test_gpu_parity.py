@@ -334,6 +334,49 @@ def test_mri_rejects_sizes_without_fft():
     assert e.value.status == b.IDEQ_ERR_UNSUPPORTED
 
 
+@pytest.mark.parametrize("lam,beta", [(0.0, 0.8), (0.1, 0.0), (0.0, 0.0)])
+def test_solve_degenerate_parameters_fp32(lam, beta):
+    """lambda = 0 (data term alone, gradient descent on f with inertia), beta = 0
+    (RED, Sec. 2.1: no inertia) and both: 20 updates on a ragged C0 batch vs the oracle."""
+    cfg, wl, net, ops, ys = setup("C0", n=2, h=37, w=45)
+    xo, infos = _oracle_solve(cfg, net, ops, ys, lam=lam, beta=beta, max_iter=20)
+    xg, info, st = _gpu_solve(cfg, wl, ys, B().IDEQ_FP32, lam=lam, beta=beta, max_iter=20)
+    assert rel(xg, xo) < 1e-5
+
+
+def test_empty_and_invalid_shapes_are_argument_errors():
+    """n = 0 (an empty batch), a negative size, a NULL pointer, tau <= 0 and beta >= 1
+    are rejected before any launch, and the context stays usable afterwards."""
+    cfg, wl, net, ops, ys = setup("C0")
+    b = B()
+    ctx = ctx_for(cfg, wl, b.IDEQ_FP32)
+    op = op_for(cfg, wl)
+    y = torch.tensor(ys, device="cuda")
+    shp = b.Shape(0, 1, 64, 64)
+    out = torch.zeros_like(y)
+    st = b._lib.ideq_solve(ctx.h, ctypes_ref(op), shp, y.data_ptr(), None, out.data_ptr(),
+                           ctypes_ref(b.make_params(0.1, 0.8, 0.5)), None)
+    assert st == b.IDEQ_ERR_ARG
+    st = b._lib.ideq_solve(ctx.h, ctypes_ref(op), b.Shape(1, 1, -64, 64), y.data_ptr(), None,
+                           out.data_ptr(), ctypes_ref(b.make_params(0.1, 0.8, 0.5)), None)
+    assert st == b.IDEQ_ERR_ARG
+    st = b._lib.ideq_solve(ctx.h, ctypes_ref(op), b.Shape(1, 1, 64, 64), None, None,
+                           out.data_ptr(), ctypes_ref(b.make_params(0.1, 0.8, 0.5)), None)
+    assert st == b.IDEQ_ERR_ARG
+    for bad in (b.make_params(0.1, 0.0, 0.5), b.make_params(0.1, 0.8, 1.0)):
+        with pytest.raises(b.IdeqError) as e:
+            b.ideq_solve(ctx, op, y, bad)
+        assert e.value.status == b.IDEQ_ERR_ARG
+    x, st = b.ideq_solve(ctx, op, y, b.make_params(cfg["lam"], cfg["tau"], cfg["beta"],
+                                                   max_iter=3), allow_maxiter=True)
+    assert torch.isfinite(x).all()
+
+
+def ctypes_ref(o):
+    import ctypes
+    return ctypes.byref(o)
+
+
 def test_solve_averaging_rejects_runs_it_does_not_define():
     cfg, wl, net, ops, ys = setup("C0")
     b = B()
