@@ -266,10 +266,11 @@ def test_proximal_variant_matches_oracle_fp32():
     assert e.value.status == b.IDEQ_ERR_UNSUPPORTED
 
 
-def test_mri_operator_matches_oracle():
-    """A x = M F x and A^T r = F^{-1}(M r) (orthonormal DFT, own FFT kernel) on two
-    complex 32 x 64 images, against numpy's FFT in FP64."""
-    cfg, wl, net, ops, ys = setup("C5", n=2, h=32, w=64)
+@pytest.mark.parametrize("n,h,w", [(2, 32, 64), (1, 256, 256), (1, 8, 1024)])
+def test_mri_operator_matches_oracle(n, h, w):
+    """A x = M F x and A^T r = F^{-1}(M r) (orthonormal DFT, own FFT kernels: the
+    generic radix-2 one and the four-step 256-point one) against numpy's FFT in FP64."""
+    cfg, wl, net, ops, ys = setup("C5", n=n, h=h, w=w)
     b = B()
     ctx = ctx_for(cfg, wl, b.IDEQ_FP32)
     op = op_for(cfg, wl)
@@ -277,8 +278,8 @@ def test_mri_operator_matches_oracle():
     x = rng.standard_normal(ys.shape).astype(np.float32)
     Ax = to_np(b.ideq_apply_A(ctx, op, torch.tensor(x, device="cuda")))
     ATr = to_np(b.ideq_apply_AT(ctx, op, torch.tensor(x, device="cuda")))
-    ref_A = np.stack([ops[i].A(x[i].astype(np.float64)) for i in range(2)])
-    ref_AT = np.stack([ops[i].AT(x[i].astype(np.float64)) for i in range(2)])
+    ref_A = np.stack([ops[i].A(x[i].astype(np.float64)) for i in range(n)])
+    ref_AT = np.stack([ops[i].AT(x[i].astype(np.float64)) for i in range(n)])
     assert rel(Ax, ref_A) < 1e-6 and rel(ATr, ref_AT) < 1e-6
 
 
