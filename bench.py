@@ -379,13 +379,12 @@ def run_profile_steps(args):
     from paper_2605_19705_gb300 import build as pbuild
     pbuild.build()
     from paper_2605_19705_gb300 import binding as B
-    cfg, wl, _ = load_workload(args.batch or None)
+    cfg, wl, _ = load_workload(args.batch or None, name=args.workload)
     prec = {"fp16": B.IDEQ_FP16, "bf16": B.IDEQ_BF16, "fp32": B.IDEQ_FP32}[args.precision]
     ctx = B.Context(B.net_desc(cfg["net"], cfg["c"]), torch.tensor(wl["weights"], device="cuda"),
                     prec)
-    op = B.make_operator(B.IDEQ_OP_BLUR, torch.tensor(wl["kern"], device="cuda"))
     xt = torch.tensor(wl["x_true"], device="cuda")
-    y = B.ideq_apply_A(ctx, op, xt) + torch.tensor(wl["noise"], device="cuda")
+    op, y = make_op_and_y(B, cfg, wl, ctx, xt, "cuda")
     xk = B.ideq_apply_AT(ctx, op, y)
     xkm1 = xk.clone()
     params = B.make_params(cfg["lam"], cfg["tau"], cfg["beta"])

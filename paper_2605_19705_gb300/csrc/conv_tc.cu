@@ -65,7 +65,8 @@ struct TcPlan {
   CUtensorMap tmA, tmB, tmO[2], tmX[3];
   int bn = 0, stages = 0, op_dt = DT_BF16, epi_dt = DT_BF16, nout = 1, naux = 0, nbo = 2,
       nba = 2, ms = 1;
-  bool halo = false, slide = false, stream = false;
+  bool halo = false, slide = false, stream = false, nw = false;
+  bool pdl = true;  // launched with programmatic stream serialisation
   int Wt = 0, Ht = 0, tiles_w = 0, tiles_h = 0, tiles_n = 0, nk = 0, cpt = 0;
   dim3 grid;
   size_t smem = 0;
@@ -172,6 +173,24 @@ IDEQ_DEV uint64_t umma_desc_sw128(uint32_t saddr) {
   return d;
 }
 
+// K-major with the 64-byte swizzle (rows of 32 16-bit channels): swizzle mode 4
+// in [61,64) and a stride byte offset of 512 B (8 rows x 64 B).  The K steps of
+// 16 elements (32 B) inside a row advance the start address, as with 128 B.
+IDEQ_DEV uint64_t umma_desc_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(16u >> 4) << 16;
+  d |= (uint64_t)(512u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;
+  return d;
+}
+
+template <bool NW>
+IDEQ_DEV uint64_t umma_desc(uint32_t saddr) {
+  return NW ? umma_desc_sw64(saddr) : umma_desc_sw128(saddr);
+}
+
 // Same descriptor for a matrix that starts `rows` 128-byte rows into a
 // 1024-byte-aligned swizzle atom.  The tensor core takes the 8-row phase of the
 // 128-byte swizzle from the address bits themselves (the pattern TMA wrote is
@@ -179,6 +198,14 @@ IDEQ_DEV uint64_t umma_desc_sw128(uint32_t saddr) {
 // base-offset field stays 0 -- measured bit-identical to the unshifted tiles.
 IDEQ_DEV uint64_t umma_desc_sw128_rows(uint32_t atom_base, int rows) {
   return umma_desc_sw128(atom_base + 128u * (uint32_t)rows);
+}
+
+// Either swizzle, `rows` K rows (128 or, for narrow rows, 64 bytes each) into an
+// aligned atom; the 64-byte swizzle is address-based in the same way.
+template <bool NW>
+IDEQ_DEV uint64_t umma_desc_rows(uint32_t atom_base, int rows) {
+  return NW ? umma_desc_sw64(atom_base + 64u * (uint32_t)rows)
+            : umma_desc_sw128_rows(atom_base, rows);
 }
 
 // Instruction descriptor of kind::f16: D f32 (bits [4,6) = 1), A and B of the
@@ -445,7 +472,7 @@ IDEQ_DEV TileCoord tile_coord(const TcArgs& a, int t, int bn, int ms, int sub) {
 
 constexpr int EPI_WARPS = 8;
 constexpr int TC_THREADS = 64 + 32 * EPI_WARPS;
-constexpr int A_BYTES = 128 * 128;  // 128 pixel rows x 64 16-bit channels
+constexpr int MAX_NBA = 4;  // auxiliary staging buffers (and their barriers) per warp, at most
 constexpr int PANEL = EPI_WARPS * WBOX;  // one staging buffer of one tensor, all 8 warps
 
 // Epilogue TMA of one warp's box (load of auxiliary values, store of results):
@@ -478,6 +505,7 @@ IDEQ_DEV void epi_tma(bool store, const TcArgs& a, const CUtensorMap* tm, uint32
 // resident in shared memory.  A is fetched once instead of nine times.
 constexpr int HALO_ROWS = 130;
 constexpr int HALO_BOX = 17408;  // 130 rows x 128 B, rounded up to a 1024-B atom
+constexpr int HALO_BOX_NW = 9216;  // 130 rows x 64 B (narrow rows), rounded the same way
 constexpr int HALO_PF = 4;       // rows prefetched into L2 ahead of the row being loaded
 
 // Halo form: tile t -> row t % tiles_h of 128-pixel column strip t / tiles_h
@@ -497,7 +525,9 @@ IDEQ_DEV TileCoord halo_coord(const TcArgs& a, int t) {
   return c;
 }
 
-template <typename TA, typename T, int BN, bool HALO, int MS>
+// NW ("narrow rows"): the ring's K rows are 64 bytes (32 16-bit channels, for
+// layers of 32 input channels) under the 64-byte swizzle, two MMAs per K chunk.
+template <typename TA, typename T, int BN, bool HALO, int MS, bool NW>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     conv_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                    const __grid_constant__ CUtensorMap tmB,
@@ -507,21 +537,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                    const __grid_constant__ CUtensorMap tmX1,
                    const __grid_constant__ CUtensorMap tmX2, TcArgs a) {
   static_assert(!HALO || MS == 1, "the halo form has one 128-row sub-tile");
-  constexpr int B_BYTES = BN * 128;
+  static_assert(!NW || (MS == 1 && sizeof(TA) == 2), "narrow rows: 16-bit, one sub-tile");
+  constexpr int RB = NW ? 64 : 128;     // bytes of one K row of a ring tile
+  constexpr int A_TILE = 128 * RB;      // one 128-pixel A tile of one K chunk
+  constexpr int B_BYTES = BN * RB;
+  constexpr int KSTEPS = RB / 32;       // MMAs per K chunk (32 bytes of K each)
+  constexpr int HBOX = NW ? HALO_BOX_NW : HALO_BOX;  // one halo row box
   // ring slot: the A (and B) boxes of one K chunk; in the halo form the three row
   // boxes of a tile, or a single row box in the sliding form; in the streamed halo
   // form one row box and the three horizontal taps of B of one (row, channel chunk)
-  const bool STREAM = !HALO && a.stream;
+  const bool STREAM = !HALO && !NW && a.stream;
   const int A_STAGE =
-      HALO ? (a.slide ? HALO_BOX : 3 * HALO_BOX) : (STREAM ? HALO_BOX : MS * A_BYTES);
+      HALO ? (a.slide ? HBOX : 3 * HBOX) : (STREAM ? HALO_BOX : MS * A_TILE);
   const int B_STAGE = STREAM ? 3 * B_BYTES : B_BYTES;
   const uint32_t STAGE_TX =
-      HALO ? (a.slide ? 1u : 3u) * HALO_ROWS * 128u
-           : (STREAM ? HALO_ROWS * 128u + 3u * B_BYTES : (uint32_t)(MS * A_BYTES + B_BYTES));
+      HALO ? (a.slide ? 1u : 3u) * HALO_ROWS * (uint32_t)RB
+           : (STREAM ? HALO_ROWS * 128u + 3u * B_BYTES : (uint32_t)(MS * A_TILE + B_BYTES));
   constexpr bool IMG = BN == 16;  // image-side output: c <= 16 planar f32 channels
-  constexpr int NPANEL = IMG ? 1 : BN / 64;
-  constexpr int KCH = 128 / (int)sizeof(TA);  // K elements per 128-byte ring row
+  constexpr int NPANEL = (IMG || BN < 64) ? 1 : BN / 64;  // 64-column epilogue panels
+  constexpr int KCH = RB / (int)sizeof(TA);  // K elements per ring row
   static_assert(!HALO || sizeof(TA) == 2, "the halo form has 16-bit operands");
+  // tiles of <= 32 columns: the two halves of the epilogue warps take alternate
+  // tiles, half h the accumulator buffer h, so two tiles drain at once
+  constexpr bool SPLIT = BN <= 32;
   constexpr int TCOLS = MS * BN;  // TMEM columns of one accumulator buffer (2 x >= 32 allocated)
   const int ST = a.stages;
   extern __shared__ uint8_t smem_raw[];
@@ -531,7 +569,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint8_t* sOut = sB + (HALO ? a.nk * B_BYTES : ST * B_STAGE);  // [warp][nbo][nout][WBOX]
   uint8_t* sAux = sOut + a.nbo * a.nout * PANEL;                 // [warp][nba][naux][WBOX]
   uint64_t* bars = (uint64_t*)(sAux + a.nba * a.naux * PANEL);
-  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * ST + 6 + 2 * EPI_WARPS);
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * ST + 6 + MAX_NBA * EPI_WARPS);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + ST);
@@ -539,7 +577,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t tempty0 = smem_u32(bars + 2 * ST + 2);
   const uint32_t drain = smem_u32(bars + 2 * ST + 4);
   const uint32_t bres = smem_u32(bars + 2 * ST + 5);
-  const uint32_t auxbar0 = smem_u32(bars + 2 * ST + 6);  // [warp][2]
+  const uint32_t auxbar0 = smem_u32(bars + 2 * ST + 6);  // [warp][MAX_NBA]
   const int ntiles = ((a.n * a.tiles_h * a.tiles_w + MS - 1) / MS) * a.tiles_n;
   // this CTA's tiles: t_first + i * t_step, i < my_tiles (a contiguous range in
   // the halo form, a grid-strided sequence otherwise)
@@ -561,9 +599,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull0 + 8 * b, 1);
-      mbar_init(tempty0 + 8 * b, EPI_WARPS);
+      mbar_init(tempty0 + 8 * b, SPLIT ? EPI_WARPS / 2 : EPI_WARPS);
     }
-    for (int b = 0; b < 2 * EPI_WARPS; ++b) mbar_init(auxbar0 + 8 * b, 1);
+    for (int b = 0; b < MAX_NBA * EPI_WARPS; ++b) mbar_init(auxbar0 + 8 * b, 1);
     mbar_init(drain, 1);
     mbar_init(bres, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -580,6 +618,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  // Programmatic dependent launch: the set-up above may overlap the tail of the
+  // previous kernel in the stream; every global access of this kernel comes after
+  // that kernel's results are complete and visible.  The next conv may start its
+  // own set-up as soon as this kernel's CTAs leave their SMs.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
   if (warp == 0) {
     if (lane == 0) {
@@ -602,7 +646,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
           mbar_expect_tx(full0 + 8 * s, STAGE_TX);
           for (int dy = 0; dy < 3; ++dy)
-            tma_load_4d(smem_u32(sA + s * A_STAGE + dy * HALO_BOX), &tmA, 0, tc.w0 - 1,
+            tma_load_4d(smem_u32(sA + s * A_STAGE + dy * HBOX), &tmA, 0, tc.w0 - 1,
                         tc.h0 + dy - 1, tc.img, full0 + 8 * s);
           ++g;
         }
@@ -662,7 +706,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
             for (int sub = 0; sub < MS; ++sub) {
               const TileCoord sc = sub == 0 ? tc : tile_coord(a, t, BN, MS, sub);
-              const uint32_t dAs = dA + sub * A_BYTES;
+              const uint32_t dAs = dA + sub * A_TILE;
               if (a.mode == CM_DOWN) {
                 const int k0 = kc * KCH;
                 const int di = k0 / (2 * a.Cin), rem = k0 - di * 2 * a.Cin;
@@ -718,10 +762,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll 1
           for (int tap = 0; tap < 9; ++tap) {
             const int dy = tap / 3, dx = tap - 3 * dy;
-            const uint64_t ad = umma_desc_sw128_rows(abase + dy * HALO_BOX, dx);
-            const uint64_t bd = umma_desc_sw128(smem_u32(sB + tap * B_BYTES));
+            const uint64_t ad = umma_desc_rows<NW>(abase + dy * HBOX, dx);
+            const uint64_t bd = umma_desc<NW>(smem_u32(sB + tap * B_BYTES));
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
+            for (int kk = 0; kk < KSTEPS; ++kk)
               umma<TA>(td, ad + 2 * kk, bd + 2 * kk, idesc, (tap | kk) != 0 ? 1u : 0u);
           }
           umma_commit(empty0 + 8 * s);
@@ -746,10 +790,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           for (int tap = 0; tap < 9; ++tap) {
             const int dy = tap / 3, dx = tap - 3 * dy;
             const uint64_t ad =
-                umma_desc_sw128_rows(smem_u32(sA + ((base + dy) % ST) * A_STAGE), dx);
-            const uint64_t bd = umma_desc_sw128(smem_u32(sB + tap * B_BYTES));
+                umma_desc_rows<NW>(smem_u32(sA + ((base + dy) % ST) * A_STAGE), dx);
+            const uint64_t bd = umma_desc<NW>(smem_u32(sB + tap * B_BYTES));
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
+            for (int kk = 0; kk < KSTEPS; ++kk)
               umma<TA>(td, ad + 2 * kk, bd + 2 * kk, idesc, (tap | kk) != 0 ? 1u : 0u);
           }
           umma_commit(tfull0 + 8 * b);
@@ -772,7 +816,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               const uint64_t ad = umma_desc_sw128_rows(abox, dx);
               const uint64_t bd = umma_desc_sw128(smem_u32(sB + s * B_STAGE + dx * B_BYTES));
 #pragma unroll
-              for (int kk = 0; kk < 4; ++kk)
+              for (int kk = 0; kk < KSTEPS; ++kk)
                 umma<TA>(td, ad + 2 * kk, bd + 2 * kk, idesc, (kc | dx | kk) != 0 ? 1u : 0u);
             }
             umma_commit(empty0 + 8 * s);
@@ -787,12 +831,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               break;
             }
             tc_fence_after();
-            const uint64_t bd = umma_desc_sw128(smem_u32(sB + s * B_STAGE));
+            const uint64_t bd = umma_desc<NW>(smem_u32(sB + s * B_STAGE));
 #pragma unroll
             for (int sub = 0; sub < MS; ++sub) {
-              const uint64_t ad = umma_desc_sw128(smem_u32(sA + s * A_STAGE + sub * A_BYTES));
+              const uint64_t ad = umma_desc<NW>(smem_u32(sA + s * A_STAGE + sub * A_TILE));
 #pragma unroll
-              for (int kk = 0; kk < 4; ++kk)
+              for (int kk = 0; kk < KSTEPS; ++kk)
                 umma<TA>(td + sub * BN, ad + 2 * kk, bd + 2 * kk, idesc,
                           (kc | kk) != 0 ? 1u : 0u);
             }
@@ -808,19 +852,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
     }
   } else if constexpr (IMG) {
-    // ---------------- image-side epilogue: the four warps of the first half own
-    // one TMEM quadrant each (one pixel row per lane), read the c valid columns
-    // and write out = aux + sign * acc to the f32 planar image, adding 1/2 out^2
-    // to the image's sum; the other four only hand the accumulator back.
+    // ---------------- image-side epilogue: half h of the warps takes the tiles
+    // of accumulator buffer h; each of its four warps owns one TMEM quadrant (one
+    // pixel row per lane), reads the c valid columns and writes out = aux + sign *
+    // acc to the f32 planar image, adding 1/2 out^2 to the image's sum.
     const int e = warp - 2, q = warp & 3, half = e >> 2;
     bool ok = true;
-    for (int lt = 0; lt < my_tiles && ok; ++lt) {
+    for (int lt = half; lt < my_tiles && ok; lt += 2) {
       const int t = t_first + lt * t_step;
       const int b = lt & 1, u = lt >> 1;
       ok = __all_sync(0xffffffffu, mbar_wait(tfull0 + 8 * b, u & 1, a.err, 4));
       if (!ok) break;
       tc_fence_after();
-      if (half == 0) {
+      {
         float v[16];
         tmem_ld16(tmem + (uint32_t)(b * TCOLS) + ((uint32_t)(q * 32) << 16), v);
         tc_fence_before();
@@ -846,92 +890,96 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           for (int off = 16; off > 0; off >>= 1) ssq += __shfl_xor_sync(0xffffffffu, ssq, off);
           if (lane == 0 && tc.img < a.n) atomicAdd(a.sumsq + tc.img, ssq);
         }
-      } else {
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(tempty0 + 8 * b);
       }
     }
   } else {
     // ---------------- epilogue warps 2..9, each on its own: warp e owns TMEM
     // lanes (rows) 32q .. 32q+31 (q = warp % 4, the quadrant it may read) and
-    // columns 32h .. 32h+31 (h = e / 4) of every 64-column panel, with its own
+    // columns 32h .. 32h+31 (h = e / 4) of every 64-column panel (of 32-column
+    // tiles: all columns of the tiles of accumulator buffer h), with its own
     // staging boxes, auxiliary barriers and bulk store groups.
     const int e = warp - 2, q = warp & 3, half = e >> 2;
-    const CUtensorMap* tmO[2] = {&tmO0, &tmO1};
-    const CUtensorMap* tmX[3] = {&tmX0, &tmX1, &tmX2};
-    const uint32_t sO = smem_u32(sOut) + (uint32_t)(e * a.nbo * a.nout * WBOX);
-    const uint32_t sX = smem_u32(sAux) + (uint32_t)(e * a.nba * a.naux * WBOX);
-    const uint32_t xbar = auxbar0 + 16 * e;
-    constexpr int TPANEL = MS * NPANEL;  // panels per tile
-    const int npc = my_tiles * TPANEL;  // panels this CTA processes
-    // auxiliary box of panel k -> buffer k % nba, loaded ahead by lane 0
-    auto aux_load = [&](int k) {
-      const int i = k / TPANEL, r = k - i * TPANEL, sub = r / NPANEL, p = r - sub * NPANEL;
-      const int t = t_first + i * t_step;
-      const TileCoord nc = HALO ? halo_coord(a, t) : tile_coord(a, t, BN, MS, sub);
-      const int buf = k % a.nba;
-      const uint32_t bar = xbar + 8 * buf;
-      mbar_expect_tx(bar, (uint32_t)(a.naux * WBOX));
-      for (int x = 0; x < a.naux; ++x)
-        epi_tma(false, a, tmX[x], sX + (uint32_t)((buf * a.naux + x) * WBOX), nc, q,
-                nc.n0 + 64 * p + 32 * half, bar);
-    };
-    int aux_issued = 0;
-    if (lane == 0 && a.naux > 0)
-      for (; aux_issued < a.nba && aux_issued < npc; ++aux_issued) aux_load(aux_issued);
-    int lt = 0, pc = 0;
-    bool ok = true;
-    for (; lt < my_tiles && ok; ++lt) {
-      const int t = t_first + lt * t_step;
-      const int b = lt & 1, u = lt >> 1;
-      ok = __all_sync(0xffffffffu, mbar_wait(tfull0 + 8 * b, u & 1, a.err, 4));
-      tc_fence_after();
-      for (int pp = 0; pp < TPANEL && ok; ++pp, ++pc) {
-        const int sub = pp / NPANEL, p = pp - sub * NPANEL;
-        const int sb = pc % a.nbo, ab = pc % a.nba;
-        if (lane == 0 && pc >= a.nbo) bulk_wait_read(a.nbo - 1);  // staging box sb read out
-        __syncwarp();
-        if (a.naux > 0) {
-          ok = __all_sync(0xffffffffu, mbar_wait(xbar + 8 * ab, (pc / a.nba) & 1, a.err, 7));
-          if (!ok) break;
-        }
-        float v[32];
-        tmem_ld32(tmem + (uint32_t)(b * TCOLS + sub * BN + 64 * p + 32 * half) +
-                      ((uint32_t)(q * 32) << 16),
-                  v);
-        if (pp == TPANEL - 1) {  // last read of this accumulator: hand it back
-          tc_fence_before();
+    {
+      // this warp's tiles: lt0 + j * lstep
+      const int lt0 = SPLIT ? half : 0, lstep = SPLIT ? 2 : 1;
+      const int my_n = SPLIT ? (my_tiles > half ? (my_tiles - half + 1) / 2 : 0) : my_tiles;
+      const int colh = SPLIT ? 0 : 32 * half;
+      const CUtensorMap* tmO[2] = {&tmO0, &tmO1};
+      const CUtensorMap* tmX[3] = {&tmX0, &tmX1, &tmX2};
+      const uint32_t sO = smem_u32(sOut) + (uint32_t)(e * a.nbo * a.nout * WBOX);
+      const uint32_t sX = smem_u32(sAux) + (uint32_t)(e * a.nba * a.naux * WBOX);
+      const uint32_t xbar = auxbar0 + 8 * MAX_NBA * e;
+      constexpr int TPANEL = MS * NPANEL;  // panels per tile
+      const int npc = my_n * TPANEL;  // panels this warp processes
+      // auxiliary box of panel k -> buffer k % nba, loaded ahead by lane 0
+      auto aux_load = [&](int k) {
+        const int i = k / TPANEL, r = k - i * TPANEL, sub = r / NPANEL, p = r - sub * NPANEL;
+        const int t = t_first + (lt0 + i * lstep) * t_step;
+        const TileCoord nc = HALO ? halo_coord(a, t) : tile_coord(a, t, BN, MS, sub);
+        const int buf = k % a.nba;
+        const uint32_t bar = xbar + 8 * buf;
+        mbar_expect_tx(bar, (uint32_t)(a.naux * WBOX));
+        for (int x = 0; x < a.naux; ++x)
+          epi_tma(false, a, tmX[x], sX + (uint32_t)((buf * a.naux + x) * WBOX), nc, q,
+                  nc.n0 + 64 * p + colh, bar);
+      };
+      int aux_issued = 0;
+      if (lane == 0 && a.naux > 0)
+        for (; aux_issued < a.nba && aux_issued < npc; ++aux_issued) aux_load(aux_issued);
+      int pc = 0;
+      bool ok = true;
+      for (int j = 0; j < my_n && ok; ++j) {
+        const int lt = lt0 + j * lstep;
+        const int t = t_first + lt * t_step;
+        const int b = lt & 1, u = lt >> 1;
+        ok = __all_sync(0xffffffffu, mbar_wait(tfull0 + 8 * b, u & 1, a.err, 4));
+        tc_fence_after();
+        for (int pp = 0; pp < TPANEL && ok; ++pp, ++pc) {
+          const int sub = pp / NPANEL, p = pp - sub * NPANEL;
+          const int sb = pc % a.nbo, ab = pc % a.nba;
+          if (lane == 0 && pc >= a.nbo) bulk_wait_read(a.nbo - 1);  // staging box sb read out
           __syncwarp();
-          if (lane == 0) mbar_arrive(tempty0 + 8 * b);
-        }
-        if constexpr (sizeof(TA) == 1) {  // FP8 operands: undo the two scales
-          const float sa = *a.a_scale;
-          const float* ws = a.w_scale + tile_coord(a, t, BN, MS, sub).n0 + 64 * p + 32 * half;
+          if (a.naux > 0) {
+            ok = __all_sync(0xffffffffu, mbar_wait(xbar + 8 * ab, (pc / a.nba) & 1, a.err, 7));
+            if (!ok) break;
+          }
+          float v[32];
+          tmem_ld32(tmem + (uint32_t)(b * TCOLS + sub * BN + 64 * p + colh) +
+                        ((uint32_t)(q * 32) << 16),
+                    v);
+          if (pp == TPANEL - 1) {  // last read of this accumulator: hand it back
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty0 + 8 * b);
+          }
+          if constexpr (sizeof(TA) == 1) {  // FP8 operands: undo the two scales
+            const float sa = *a.a_scale;
+            const float* ws = a.w_scale + tile_coord(a, t, BN, MS, sub).n0 + 64 * p + colh;
 #pragma unroll
-          for (int i = 0; i < 32; ++i) v[i] *= sa * __ldg(ws + i);
-        }
-        const uint32_t ob = sO + (uint32_t)(sb * a.nout * WBOX);
-        epi_apply<T>(a.epi, a.act, v, sX + (uint32_t)(ab * a.naux * WBOX), ob, lane);
-        fence_async_smem();
-        __syncwarp();
-        if (lane == 0) {
-          const TileCoord tc = HALO ? halo_coord(a, t) : tile_coord(a, t, BN, MS, sub);
-          for (int i = 0; i < a.nout; ++i)
-            epi_tma(true, a, tmO[i], ob + (uint32_t)(i * WBOX), tc, q,
-                    tc.n0 + 64 * p + 32 * half, 0);
-          bulk_commit();
-          if (a.naux > 0 && aux_issued < npc) aux_load(aux_issued++);  // into buffer ab
+            for (int i = 0; i < 32; ++i) v[i] *= sa * __ldg(ws + i);
+          }
+          const uint32_t ob = sO + (uint32_t)(sb * a.nout * WBOX);
+          epi_apply<T>(a.epi, a.act, v, sX + (uint32_t)(ab * a.naux * WBOX), ob, lane);
+          fence_async_smem();
+          __syncwarp();
+          if (lane == 0) {
+            const TileCoord tc = HALO ? halo_coord(a, t) : tile_coord(a, t, BN, MS, sub);
+            for (int i = 0; i < a.nout; ++i)
+              epi_tma(true, a, tmO[i], ob + (uint32_t)(i * WBOX), tc, q,
+                      tc.n0 + 64 * p + colh, 0);
+            bulk_commit();
+            if (a.naux > 0 && aux_issued < npc) aux_load(aux_issued++);  // into buffer ab
+          }
         }
       }
+      if (lane == 0) {
+        bulk_wait_all();
+        // on an early exit, let auxiliary loads still in flight land
+        for (int k = pc; k < aux_issued; ++k)
+          mbar_wait(xbar + 8 * (k % a.nba), (k / a.nba) & 1, a.err, 8);
+      }
+      __syncwarp();
     }
-    if (lane == 0) {
-      bulk_wait_all();
-      // on an early exit, let auxiliary loads still in flight land
-      for (int k = pc; k < aux_issued; ++k)
-        mbar_wait(xbar + 8 * (k % a.nba), (k / a.nba) & 1, a.err, 8);
-    }
-    __syncwarp();
   }
   tc_fence_before();
   __syncthreads();
@@ -968,6 +1016,7 @@ static bool image_side(const ConvArgs& a) {
 }
 
 static int pick_bn(int N) {
+  if (N % 64 != 0) return 32;
   // smallest N tiled 256 wide (measured: 256-wide tiles win from N = 256 up)
   const int n256 = tiling_override("IDEQ_TC_BN256_MIN", 256);
   if (N % 256 == 0 && N >= n256) return 256;
@@ -985,15 +1034,24 @@ static int epi_naux(int epi) {
   return 0;
 }
 
-static int k_chunk(int op_dt) { return op_dt == DT_FP8 ? 128 : 64; }  // K per 128-B row
+// narrow rows: 16-bit operands of 32 (not 64) channels per K chunk, for inputs
+// whose channel count is an odd multiple of 32
+static bool narrow_rows(const ConvArgs& a, int op_dt) {
+  return op_dt != DT_FP8 && a.Cin % 64 != 0 && a.Cin % 32 == 0;
+}
+
+// K elements per ring row: 128 B of e4m3 or 16-bit values, 64 B for narrow rows
+static int k_chunk(int op_dt, bool nw) { return op_dt == DT_FP8 ? 128 : (nw ? 32 : 64); }
 
 bool tc_supported(const ConvArgs& a, int op_dt) {
   if (image_side(a))  // weights padded to 16 rows [16][K] by the caller
-    return op_dt != DT_FP8 && a.Cin % 64 == 0 && a.aux0 && a.out;
+    return op_dt != DT_FP8 && a.Cin % 32 == 0 && a.aux0 && a.out;
   if (a.in_nchw || a.out_nchw || a.epi == EP_AXPY_NCHW) return false;
-  if (a.Cin % k_chunk(op_dt) != 0) return false;
+  if (a.Cin % k_chunk(op_dt, narrow_rows(a, op_dt)) != 0) return false;
   if (op_dt == DT_FP8 && (!a.a_scale || !a.w_scale)) return false;
-  if (a.N() % 64 != 0 || a.Cout % 64 != 0) return false;
+  // N tiles of 32, 64, 128 or 256 columns (e4m3: 64 up); epilogue boxes of 32 channels
+  const int nq = op_dt == DT_FP8 ? 64 : 32;
+  if (a.N() % nq != 0 || a.Cout % nq != 0) return false;
   if (a.mode == CM_DOWN && a.outmap != OM_IDENT) return false;
   if (epi_naux(a.epi) >= 1 && !a.aux0) return false;
   if (epi_naux(a.epi) >= 2 && (!a.aux1 || !a.aux2)) return false;
@@ -1002,7 +1060,8 @@ bool tc_supported(const ConvArgs& a, int op_dt) {
 }
 
 static size_t fixed_smem(int nout, int naux, int nbo, int nba, int stages) {
-  return 1024 + (size_t)(nbo * nout + nba * naux) * PANEL + (2 * stages + 6 + 2 * EPI_WARPS) * 8 + 16;
+  return 1024 + (size_t)(nbo * nout + nba * naux) * PANEL +
+         (2 * stages + 6 + MAX_NBA * EPI_WARPS) * 8 + 16;
 }
 
 constexpr size_t kMaxSmem = 227 * 1024;
@@ -1062,7 +1121,10 @@ TcPlan* tc_plan_create(const ConvArgs& a, int op_dt, int epi_dt, std::string* er
   TcPlan* p = new TcPlan();
   p->op_dt = op_dt;
   p->epi_dt = epi_dt;
-  const int KCH = k_chunk(op_dt);
+  p->nw = narrow_rows(a, op_dt);
+  p->pdl = tiling_override("IDEQ_TC_PDL", 1) != 0;
+  const int KCH = k_chunk(op_dt, p->nw);
+  const int RB = p->nw ? 64 : 128;  // bytes per ring row
   const bool img = image_side(a);
   const int N = img ? 16 : a.N();  // image side: weight rows padded to 16
   p->bn = img ? 16 : pick_bn(N);
@@ -1080,13 +1142,16 @@ TcPlan* tc_plan_create(const ConvArgs& a, int op_dt, int epi_dt, std::string* er
   p->tiles_n = N / p->bn;
   // halo form: 3x3 conv of 64 channels over whole 128-pixel row segments, with
   // the nine 64 x 64 weight taps resident in shared memory
-  const size_t bres = (size_t)p->nk * p->bn * 128;
-  p->halo = op_dt != DT_FP8 && a.mode == CM_CONV3 && p->Wt == 128 && p->Ht == 1 && p->tiles_n == 1 &&
-            p->cpt == 1 && bres <= 80 * 1024 && tiling_override("IDEQ_TC_HALO", 1) != 0;
-  p->slide = p->halo && tiling_override("IDEQ_TC_SLIDE", 0) != 0;
+  const size_t bres = (size_t)p->nk * p->bn * RB;
+  // (instantiated for N tiles of 16, 64 and 128 columns, narrow rows 16 to 64)
+  const bool halo_bn = p->nw ? p->bn <= 64 : (p->bn == 16 || p->bn == 64 || p->bn == 128);
+  p->halo = op_dt != DT_FP8 && a.mode == CM_CONV3 && p->Wt == 128 && p->Ht == 1 &&
+            p->tiles_n == 1 && p->cpt == 1 && halo_bn && bres <= 80 * 1024 &&
+            tiling_override("IDEQ_TC_HALO", 1) != 0;
+  p->slide = p->halo && !p->nw && tiling_override("IDEQ_TC_SLIDE", 0) != 0;
   // streamed halo: full-row 3x3 convs whose weights do not stay resident
-  p->stream = !p->halo && op_dt != DT_FP8 && a.mode == CM_CONV3 && p->Wt == 128 &&
-              p->Ht == 1 && p->tiles_n == 1 && p->bn <= 128 &&
+  p->stream = !p->halo && op_dt != DT_FP8 && !p->nw && a.mode == CM_CONV3 && p->Wt == 128 &&
+              p->Ht == 1 && p->tiles_n == 1 && p->bn <= 128 && p->bn != 32 &&
               tiling_override("IDEQ_TC_STREAM", 1) != 0;
   // Two 128-row sub-tiles can share each weight chunk (half the weight traffic
   // per FLOP), but measured on the U-Net layers the coarser tiles balance worse
@@ -1094,19 +1159,36 @@ TcPlan* tc_plan_create(const ConvArgs& a, int op_dt, int epi_dt, std::string* er
   p->ms = 1;
   {
     const int force_ms = tiling_override("IDEQ_TC_MS", 0);  // 2 forces two sub-tiles
-    if (!p->halo && !p->stream && p->bn <= 128 && force_ms == 2) p->ms = 2;
+    if (!p->halo && !p->stream && !p->nw && p->bn >= 64 && p->bn <= 128 && force_ms == 2)
+      p->ms = 2;
   }
   // shared memory: ring depth and staging buffers, preferring a deep ring
   // (halo: >= 5 row boxes, three in use and two in flight; else >= 3 stages),
   // then double-buffered staging
-  const size_t stage = p->halo     ? (size_t)(p->slide ? 1 : 3) * HALO_BOX
+  const size_t stage = p->halo     ? (size_t)(p->slide ? 1 : 3) * (p->nw ? HALO_BOX_NW : HALO_BOX)
                        : p->stream ? (size_t)HALO_BOX + 3 * (size_t)p->bn * 128
-                                   : (size_t)p->ms * A_BYTES + (size_t)p->bn * 128;
+                                   : ((size_t)p->ms * 128 + (size_t)p->bn) * RB;
   const size_t resident = p->halo ? bres : 0;
   p->stages = 0;
+  // short K (depth-to-space, stride-2 and 1x1 layers): the epilogue paces the
+  // kernel, so auxiliary boxes are fetched four panels ahead and the ring is
+  // held to two stages
+  if (p->naux > 0 && !p->halo && !p->stream && p->nk <= 4 &&
+      tiling_override("IDEQ_TC_NBA", MAX_NBA) == MAX_NBA) {
+    for (int st = 8; st >= 2 && !p->stages; --st) {
+      const size_t tot = fixed_smem(p->nout, p->naux, 2, MAX_NBA, st) + (size_t)st * stage;
+      if (tot <= kMaxSmem) {
+        p->stages = st;
+        p->nbo = 2;
+        p->nba = MAX_NBA;
+        p->smem = tot;
+      }
+    }
+  }
   const int min_stages[2] = {p->halo ? (p->slide ? 5 : 3) : (p->stream ? 2 : 3),
                              p->halo ? (p->slide ? 4 : 2) : 2};
   for (int min_st : min_stages) {
+    if (p->stages) break;
     for (int nbuf : {2, 1}) {
       int st = 8;
       auto total = [&](int k) {
@@ -1146,6 +1228,7 @@ TcPlan* tc_plan_create(const ConvArgs& a, int op_dt, int epi_dt, std::string* er
   };
   const CUtensorMapDataType dt = map_type(op_dt), edt = map_type(epi_dt);
   const cuuint64_t es = op_dt == DT_FP8 ? 1 : 2;  // operand element bytes
+  const CUtensorMapSwizzle swz = p->nw ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
   bool ok;
   if (a.mode == CM_DOWN) {
     const int Hi = 2 * a.H, Wi = 2 * a.W;
@@ -1154,7 +1237,7 @@ TcPlan* tc_plan_create(const ConvArgs& a, int op_dt, int epi_dt, std::string* er
     cuuint64_t strides[4] = {(cuuint64_t)2 * a.Cin * es, (cuuint64_t)Wi * a.Cin * es,
                              (cuuint64_t)2 * Wi * a.Cin * es, (cuuint64_t)Hi * Wi * a.Cin * es};
     cuuint32_t box[5] = {(cuuint32_t)KCH, (cuuint32_t)p->Wt, 1, (cuuint32_t)p->Ht, 1};
-    ok = encode(enc, &p->tmA, dt, 5, a.in, dims, strides, box);
+    ok = encode(enc, &p->tmA, dt, 5, a.in, dims, strides, box, swz);
   } else {
     cuuint64_t dims[4] = {(cuuint64_t)a.Cin, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.n};
     cuuint64_t strides[3] = {(cuuint64_t)a.Cin * es, (cuuint64_t)a.W * a.Cin * es,
@@ -1162,14 +1245,14 @@ TcPlan* tc_plan_create(const ConvArgs& a, int op_dt, int epi_dt, std::string* er
     cuuint32_t box[4] = {(cuuint32_t)KCH,
                          (cuuint32_t)((p->halo || p->stream) ? HALO_ROWS : p->Wt),
                          (cuuint32_t)p->Ht, 1};
-    ok = encode(enc, &p->tmA, dt, 4, a.in, dims, strides, box);
+    ok = encode(enc, &p->tmA, dt, 4, a.in, dims, strides, box, swz);
   }
   {
     const int K = a.K();
     cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)N};
     cuuint64_t strides[1] = {(cuuint64_t)K * es};
     cuuint32_t box[2] = {(cuuint32_t)KCH, (cuuint32_t)p->bn};
-    ok = ok && encode(enc, &p->tmB, dt, 2, a.wB, dims, strides, box);
+    ok = ok && encode(enc, &p->tmB, dt, 2, a.wB, dims, strides, box, swz);
   }
   const void* outs[2] = {a.out, a.out2};
   const void* auxs[3] = {a.aux0, a.aux1, a.aux2};
@@ -1192,19 +1275,28 @@ TcPlan* tc_plan_create(const ConvArgs& a, int op_dt, int epi_dt, std::string* er
 
 void tc_plan_destroy(TcPlan* p) { delete p; }
 
-template <typename TA, typename T, int BN, bool HALO, int MS>
+template <typename TA, typename T, int BN, bool HALO, int MS, bool NW = false>
 static cudaError_t launch_bn(const TcPlan* p, const TcArgs& ta, cudaStream_t st) {
   static bool attr_set = false;  // per instantiation; set before first launch
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<TA, T, BN, HALO, MS>,
+    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<TA, T, BN, HALO, MS, NW>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kMaxSmem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  conv_tc_kernel<TA, T, BN, HALO, MS><<<p->grid, TC_THREADS, p->smem, st>>>(
-      p->tmA, p->tmB, p->tmO[0], p->tmO[1], p->tmX[0], p->tmX[1], p->tmX[2], ta);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = p->grid;
+  cfg.blockDim = dim3(TC_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = p->smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = p->pdl ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, conv_tc_kernel<TA, T, BN, HALO, MS, NW>, p->tmA, p->tmB,
+                            p->tmO[0], p->tmO[1], p->tmX[0], p->tmX[1], p->tmX[2], ta);
 }
 
 template <typename T>
@@ -1216,6 +1308,23 @@ static cudaError_t launch_typed(const TcPlan* p, const TcArgs& t, cudaStream_t s
       default: return launch_bn<__nv_fp8_e4m3, T, 256, false, 1>(p, t, st);
     }
   }
+  if (p->nw && p->halo) {  // 32-channel K rows, halo form
+    switch (p->bn) {
+      case 16: return launch_bn<T, T, 16, true, 1, true>(p, t, st);
+      case 32: return launch_bn<T, T, 32, true, 1, true>(p, t, st);
+      default: return launch_bn<T, T, 64, true, 1, true>(p, t, st);
+    }
+  }
+  if (p->nw) {  // 32-channel K rows: plain tiles
+    switch (p->bn) {
+      case 16: return launch_bn<T, T, 16, false, 1, true>(p, t, st);
+      case 32: return launch_bn<T, T, 32, false, 1, true>(p, t, st);
+      case 64: return launch_bn<T, T, 64, false, 1, true>(p, t, st);
+      case 128: return launch_bn<T, T, 128, false, 1, true>(p, t, st);
+      default: return launch_bn<T, T, 256, false, 1, true>(p, t, st);
+    }
+  }
+  if (p->bn == 32) return launch_bn<T, T, 32, false, 1>(p, t, st);
   if (p->bn == 16) {
     if (p->halo) return launch_bn<T, T, 16, true, 1>(p, t, st);
     return launch_bn<T, T, 16, false, 1>(p, t, st);

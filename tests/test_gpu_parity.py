@@ -104,6 +104,13 @@ def test_operator_argument_errors():
     ("C1a", dict(n=1), "bf16", 1e-2),
     ("C1a", dict(n=1, h=136, w=200), "fp16", 2e-3),  # halo tiles with ragged row ends
     ("C3", dict(n=1, h=32, w=32), "fp32", 1e-5),
+    # half-width U-Net: 32-channel layers on 64-byte K rows and 32-wide N tiles
+    ("C3", dict(n=1, h=64, w=64), "fp16", 2e-3),
+    ("C3", dict(n=2, h=40, w=56), "bf16", 1e-2),
+    ("C3", dict(n=1), "fp16", 2e-3),
+    ("C3", dict(n=1), "bf16", 1e-2),
+    ("C3", dict(n=1, h=136, w=200), "fp16", 2e-3),  # 32-channel halo tiles, ragged rows
+    ("C5", dict(n=1), "fp16", 2e-3),            # 2-channel (complex) input and output
     # e4m3 operands (unit roundoff 2^-4) on the 256- and 512-channel convs, averaged
     # over K >= 1024 terms and damped by the 0.1 residual gains: measured 1.2e-2
     ("C1a", dict(n=1, h=64, w=64), "fp16_fp8", 3e-2),
@@ -300,6 +307,28 @@ def test_mri_solve_matches_oracle_fp32(prox):
     assert rel(to_np(x), xo) < 1e-5
     for i in range(2):
         assert abs(float(info.energy[i]) - infos[i]["energy"]) < 1e-5 * infos[i]["energy"]
+
+
+@pytest.mark.parametrize("prec,tol", [("fp16", 2e-3), ("bf16", 1e-2)])
+def test_mri_solve_half_precision_tensor_core_convs(prec, tol):
+    """30 inertial updates of the MRI problem with 16-bit convolutions, whose
+    32-channel layers run on the tensor cores: the iterate stays within the 16-bit
+    operand rounding (fp16 2^-11, bf16 2^-8, a few units after the U-Net) of the
+    FP64 iterate; the regulariser energy, quadratic in the residual z - N(z) (a
+    difference much smaller than z, so relatively less accurate), within 4x that."""
+    cfg, wl, net, ops, ys = setup("C5", n=2, h=64, w=64)
+    b = B()
+    x0 = np.stack([ops[i].AT(ys[i].astype(np.float64)) for i in range(2)])
+    xo, infos = solver.solve_batch(net, ops, ys.astype(np.float64), x0, cfg["lam"], cfg["tau"],
+                                   cfg["beta"], math.inf, 0.0, 30)
+    ctx = ctx_for(cfg, wl, PREC[prec]())
+    params = b.make_params(cfg["lam"], cfg["tau"], cfg["beta"], max_iter=30)
+    info = b.InfoBuffers(2)
+    x, st = b.ideq_solve(ctx, op_for(cfg, wl), torch.tensor(ys, device="cuda"), params,
+                         info=info, allow_maxiter=True)
+    assert rel(to_np(x), xo) < tol
+    for i in range(2):
+        assert abs(float(info.energy[i]) - infos[i]["energy"]) < 4 * tol * infos[i]["energy"]
 
 
 def test_rician_solve_matches_oracle_fp32():
