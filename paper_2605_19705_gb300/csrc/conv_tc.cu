@@ -53,6 +53,7 @@ struct TcArgs {
   const float* w_scale;  // FP8 operands: weight scale per GEMM column
   int slide;             // halo form: contiguous row runs per CTA reusing row boxes
   int stream;            // streamed halo: per stage one row box and the 3 dx taps of B
+  int split64;           // 64-column tiles: epilogue halves take alternate tiles
   // image-side output (BN = 16): out = aux + sign * acc, f32 planar, c <= 16 channels
   float sign;
   const float* img_aux;
@@ -66,7 +67,8 @@ struct TcPlan {
   int bn = 0, stages = 0, op_dt = DT_BF16, epi_dt = DT_BF16, nout = 1, naux = 0, nbo = 2,
       nba = 2, ms = 1;
   bool halo = false, slide = false, stream = false, nw = false;
-  bool pdl = true;  // launched with programmatic stream serialisation
+  bool pdl = true;       // launched with programmatic stream serialisation
+  bool split64 = false;  // 64-column tiles: epilogue halves on alternate tiles
   int Wt = 0, Ht = 0, tiles_w = 0, tiles_h = 0, tiles_n = 0, nk = 0, cpt = 0;
   dim3 grid;
   size_t smem = 0;
@@ -557,9 +559,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   constexpr int NPANEL = (IMG || BN < 64) ? 1 : BN / 64;  // 64-column epilogue panels
   constexpr int KCH = RB / (int)sizeof(TA);  // K elements per ring row
   static_assert(!HALO || sizeof(TA) == 2, "the halo form has 16-bit operands");
-  // tiles of <= 32 columns: the two halves of the epilogue warps take alternate
-  // tiles, half h the accumulator buffer h, so two tiles drain at once
+  // tiles of <= 32 (optionally 64) columns: the two halves of the epilogue warps
+  // take alternate tiles, half h the accumulator buffer h, so two tiles drain at once
   constexpr bool SPLIT = BN <= 32;
+  const bool spl = SPLIT || (BN == 64 && MS == 1 && a.split64 != 0);
   constexpr int TCOLS = MS * BN;  // TMEM columns of one accumulator buffer (2 x >= 32 allocated)
   const int ST = a.stages;
   extern __shared__ uint8_t smem_raw[];
@@ -599,7 +602,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull0 + 8 * b, 1);
-      mbar_init(tempty0 + 8 * b, SPLIT ? EPI_WARPS / 2 : EPI_WARPS);
+      mbar_init(tempty0 + 8 * b, spl ? EPI_WARPS / 2 : EPI_WARPS);
     }
     for (int b = 0; b < MAX_NBA * EPI_WARPS; ++b) mbar_init(auxbar0 + 8 * b, 1);
     mbar_init(drain, 1);
@@ -901,19 +904,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int e = warp - 2, q = warp & 3, half = e >> 2;
     {
       // this warp's tiles: lt0 + j * lstep
-      const int lt0 = SPLIT ? half : 0, lstep = SPLIT ? 2 : 1;
-      const int my_n = SPLIT ? (my_tiles > half ? (my_tiles - half + 1) / 2 : 0) : my_tiles;
-      const int colh = SPLIT ? 0 : 32 * half;
+      const int lt0 = spl ? half : 0, lstep = spl ? 2 : 1;
+      const int my_n = spl ? (my_tiles > half ? (my_tiles - half + 1) / 2 : 0) : my_tiles;
+      const int colh = spl ? 0 : 32 * half;
+      // panels: 32 columns each when split (all of the tile), else this half's 32
+      // columns of each 64-column panel
+      const int PW = spl ? 32 : 64;                // column step between panels
+      const int nper = spl ? BN / 32 : NPANEL;     // panels per 128-row sub-tile
+      const int npan = MS * nper;                  // panels per tile
       const CUtensorMap* tmO[2] = {&tmO0, &tmO1};
       const CUtensorMap* tmX[3] = {&tmX0, &tmX1, &tmX2};
       const uint32_t sO = smem_u32(sOut) + (uint32_t)(e * a.nbo * a.nout * WBOX);
       const uint32_t sX = smem_u32(sAux) + (uint32_t)(e * a.nba * a.naux * WBOX);
       const uint32_t xbar = auxbar0 + 8 * MAX_NBA * e;
-      constexpr int TPANEL = MS * NPANEL;  // panels per tile
-      const int npc = my_n * TPANEL;  // panels this warp processes
+      const int npc = my_n * npan;  // panels this warp processes
       // auxiliary box of panel k -> buffer k % nba, loaded ahead by lane 0
       auto aux_load = [&](int k) {
-        const int i = k / TPANEL, r = k - i * TPANEL, sub = r / NPANEL, p = r - sub * NPANEL;
+        const int i = k / npan, r = k - i * npan, sub = r / nper, p = r - sub * nper;
         const int t = t_first + (lt0 + i * lstep) * t_step;
         const TileCoord nc = HALO ? halo_coord(a, t) : tile_coord(a, t, BN, MS, sub);
         const int buf = k % a.nba;
@@ -921,7 +928,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         mbar_expect_tx(bar, (uint32_t)(a.naux * WBOX));
         for (int x = 0; x < a.naux; ++x)
           epi_tma(false, a, tmX[x], sX + (uint32_t)((buf * a.naux + x) * WBOX), nc, q,
-                  nc.n0 + 64 * p + colh, bar);
+                  nc.n0 + PW * p + colh, bar);
       };
       int aux_issued = 0;
       if (lane == 0 && a.naux > 0)
@@ -934,8 +941,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int b = lt & 1, u = lt >> 1;
         ok = __all_sync(0xffffffffu, mbar_wait(tfull0 + 8 * b, u & 1, a.err, 4));
         tc_fence_after();
-        for (int pp = 0; pp < TPANEL && ok; ++pp, ++pc) {
-          const int sub = pp / NPANEL, p = pp - sub * NPANEL;
+        for (int pp = 0; pp < npan && ok; ++pp, ++pc) {
+          const int sub = pp / nper, p = pp - sub * nper;
           const int sb = pc % a.nbo, ab = pc % a.nba;
           if (lane == 0 && pc >= a.nbo) bulk_wait_read(a.nbo - 1);  // staging box sb read out
           __syncwarp();
@@ -944,17 +951,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (!ok) break;
           }
           float v[32];
-          tmem_ld32(tmem + (uint32_t)(b * TCOLS + sub * BN + 64 * p + colh) +
+          tmem_ld32(tmem + (uint32_t)(b * TCOLS + sub * BN + PW * p + colh) +
                         ((uint32_t)(q * 32) << 16),
                     v);
-          if (pp == TPANEL - 1) {  // last read of this accumulator: hand it back
+          if (pp == npan - 1) {  // last read of this accumulator: hand it back
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(tempty0 + 8 * b);
           }
           if constexpr (sizeof(TA) == 1) {  // FP8 operands: undo the two scales
             const float sa = *a.a_scale;
-            const float* ws = a.w_scale + tile_coord(a, t, BN, MS, sub).n0 + 64 * p + colh;
+            const float* ws = a.w_scale + tile_coord(a, t, BN, MS, sub).n0 + PW * p + colh;
 #pragma unroll
             for (int i = 0; i < 32; ++i) v[i] *= sa * __ldg(ws + i);
           }
@@ -966,7 +973,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const TileCoord tc = HALO ? halo_coord(a, t) : tile_coord(a, t, BN, MS, sub);
             for (int i = 0; i < a.nout; ++i)
               epi_tma(true, a, tmO[i], ob + (uint32_t)(i * WBOX), tc, q,
-                      tc.n0 + 64 * p + colh, 0);
+                      tc.n0 + PW * p + colh, 0);
             bulk_commit();
             if (a.naux > 0 && aux_issued < npc) aux_load(aux_issued++);  // into buffer ab
           }
@@ -1123,6 +1130,9 @@ TcPlan* tc_plan_create(const ConvArgs& a, int op_dt, int epi_dt, std::string* er
   p->epi_dt = epi_dt;
   p->nw = narrow_rows(a, op_dt);
   p->pdl = tiling_override("IDEQ_TC_PDL", 1) != 0;
+  // measured on the 64-channel full-row layers: slower split (53.9 vs 56.1
+  // restorations/s on 8 x RGB 256^2), so 64-column tiles keep both halves per tile
+  p->split64 = tiling_override("IDEQ_TC_SPLIT64", 0) != 0;
   const int KCH = k_chunk(op_dt, p->nw);
   const int RB = p->nw ? 64 : 128;  // bytes per ring row
   const bool img = image_side(a);
@@ -1172,7 +1182,7 @@ TcPlan* tc_plan_create(const ConvArgs& a, int op_dt, int epi_dt, std::string* er
   p->stages = 0;
   // short K (depth-to-space, stride-2 and 1x1 layers): the epilogue paces the
   // kernel, so auxiliary boxes are fetched four panels ahead and the ring is
-  // held to two stages
+  // held to two stages (measured: 2% on the depth-to-space layers, 57 vs 58 us)
   if (p->naux > 0 && !p->halo && !p->stream && p->nk <= 4 &&
       tiling_override("IDEQ_TC_NBA", MAX_NBA) == MAX_NBA) {
     for (int st = 8; st >= 2 && !p->stages; --st) {
@@ -1374,6 +1384,7 @@ cudaError_t launch_conv_tc(const TcPlan* p, const ConvArgs& a, int* err_flag, cu
   t.nba = p->nba;
   t.slide = p->slide ? 1 : 0;
   t.stream = p->stream ? 1 : 0;
+  t.split64 = p->split64 ? 1 : 0;
   t.sign = a.sign;
   t.img_aux = (const float*)a.aux0;
   t.img_out = (float*)a.out;
