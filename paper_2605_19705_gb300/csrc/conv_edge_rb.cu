@@ -1,5 +1,5 @@
 // Register-blocked 3x3 convolutions between the image side (f32 planar NCHW,
-// c = 1 or 3 channels) and the feature side (NHWC, C = 32 or 64 channels, f32 /
+// c = 1, 2 or 3 channels) and the feature side (NHWC, C = 32 or 64 channels, f32 /
 // bf16 / f16): the regulariser's head and tail and their transposes.  Every
 // weight or input value a thread loads from shared memory feeds 8 to 24 FMAs,
 // so the FP32 pipes, not the shared-memory port, set the pace.
@@ -251,10 +251,10 @@ static bool rb_width(int C) { return C == 32 || C == 64; }
 bool edge_rb_supported(const ConvArgs& a) {
   if (a.mode != CM_CONV3 || a.outmap != OM_IDENT) return false;
   if (a.in_nchw && !a.out_nchw)
-    return (a.Cin == 1 || a.Cin == 3) && rb_width(a.Cout) &&
+    return a.Cin >= 1 && a.Cin <= 3 && rb_width(a.Cout) &&
            (a.epi == EP_STORE || a.epi == EP_ACT);
   if (a.out_nchw && !a.in_nchw)
-    return (a.Cout == 1 || a.Cout == 3) && rb_width(a.Cin) && a.epi == EP_AXPY_NCHW;
+    return a.Cout >= 1 && a.Cout <= 3 && rb_width(a.Cin) && a.epi == EP_AXPY_NCHW;
   return false;
 }
 
@@ -297,13 +297,15 @@ static cudaError_t i2f_c(const ConvArgs& a, cudaStream_t st) {
 
 template <typename T, int C>
 static cudaError_t f2i_c(const ConvArgs& a, cudaStream_t st) {
-  return a.Cout == 1 ? f2i<T, C, 1>(a, st) : f2i<T, C, 3>(a, st);
+  if (a.Cout == 1) return f2i<T, C, 1>(a, st);
+  return a.Cout == 2 ? f2i<T, C, 2>(a, st) : f2i<T, C, 3>(a, st);
 }
 
 template <typename T>
 static cudaError_t launch_rb_t(const ConvArgs& a, cudaStream_t st) {
   if (a.out_nchw) return a.Cin == 32 ? f2i_c<T, 32>(a, st) : f2i_c<T, 64>(a, st);
-  return a.Cin == 1 ? i2f_c<T, 1>(a, st) : i2f_c<T, 3>(a, st);
+  if (a.Cin == 1) return i2f_c<T, 1>(a, st);
+  return a.Cin == 2 ? i2f_c<T, 2>(a, st) : i2f_c<T, 3>(a, st);
 }
 
 cudaError_t launch_conv_edge_rb(const ConvArgs& a, int feat_dt, cudaStream_t st) {

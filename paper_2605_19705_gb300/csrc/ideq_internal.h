@@ -73,7 +73,7 @@ cudaError_t launch_conv_simt(const ConvArgs& a, int in_dt, int out_dt, cudaStrea
 // conv_edge.cu).  feat_dt is the element type of the NHWC side.
 bool edge_supported(const ConvArgs& a);
 cudaError_t launch_conv_edge(const ConvArgs& a, int feat_dt, cudaStream_t st);
-// register-blocked forms of the common edge shapes (c in {1, 3}, C in {32, 64})
+// register-blocked forms of the common edge shapes (c in {1, 2, 3}, C in {32, 64})
 bool edge_rb_supported(const ConvArgs& a);
 cudaError_t launch_conv_edge_rb(const ConvArgs& a, int feat_dt, cudaStream_t st);
 
