@@ -272,6 +272,10 @@ ideq_status ideq_prof_enable(ideq_ctx *ctx, int on);
 ideq_status ideq_prof_read(ideq_ctx *ctx, double *ms, int64_t *launches, double *flops);
 /* Number of kernels this context launched since the last call (host count). */
 ideq_status ideq_launch_count(ideq_ctx *ctx, int64_t *count);
+/* Whether the last ideq_solve on this context ran its iterations after the first
+ * two in the device-driven CUDA graph (*graphed = 1) or from the host (0: graphs
+ * off, profiler recording, max_iter <= 2, or the runtime refused to build one). */
+ideq_status ideq_solve_graphed(ideq_ctx *ctx, int *graphed);
 
 #ifdef __cplusplus
 }

@@ -85,6 +85,7 @@ _sig = {
     "ideq_prof_enable": [c_void_p, c_int],
     "ideq_prof_read": [c_void_p, P(c_double), P(ctypes.c_int64), P(c_double)],
     "ideq_launch_count": [c_void_p, P(ctypes.c_int64)],
+    "ideq_solve_graphed": [c_void_p, P(c_int)],
     "ideq_red_update_noalloc": [c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                 c_float, c_float, c_void_p, c_void_p, c_void_p],
 }
@@ -314,6 +315,13 @@ def ideq_launch_count(ctx: Context) -> int:
     n = ctypes.c_int64(0)
     ctx.check(_lib.ideq_launch_count(ctx.h, ctypes.byref(n)))
     return int(n.value)
+
+
+def ideq_solve_graphed(ctx: Context) -> bool:
+    """Whether the last ideq_solve on ctx ran its loop in the device-driven graph."""
+    g = c_int(0)
+    ctx.check(_lib.ideq_solve_graphed(ctx.h, ctypes.byref(g)))
+    return bool(g.value)
 
 
 def ideq_red_update_noalloc(z, grad_f, grad_g, x, x_new, lam, tau, step_sq=None, x_sq=None):

@@ -68,6 +68,10 @@ struct ideq_ctx {
     long long body_launches = 0;
   } sg;
   bool graph_ok = true;  // false once building a graph failed in this context
+  // private non-blocking stream the solve graph is captured on (the caller's
+  // stream may be the legacy default stream, which cannot be captured)
+  cudaStream_t cap_stream = nullptr;
+  bool last_graphed = false;  // the last solve ran its loop in the device graph
   void drop_graph() {
     if (sg.exec) cudaGraphExecDestroy(sg.exec);
     if (sg.g) cudaGraphDestroy(sg.g);
@@ -358,11 +362,32 @@ bool same_params(const ideq_params& a, const ideq_params& b) {
 bool build_solve_graph(ideq_ctx* ctx, const OpDev& od, const ideq_shape& s, const float* y,
                        const ideq_params* p) {
   ctx->drop_graph();
+  ctx->err.clear();
+  if (!ctx->cap_stream &&
+      cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    ctx->cap_stream = nullptr;
+    (void)cudaGetLastError();
+    ctx->graph_ok = false;
+    return false;
+  }
+  // iterate() launches on ctx->stream: point it at the capture stream until return
+  struct StreamSwap {
+    ideq_ctx* c;
+    cudaStream_t user;
+    ~StreamSwap() { c->stream = user; }
+  } swap{ctx, ctx->stream};
+  ctx->stream = ctx->cap_stream;
   cudaStream_t st = ctx->stream;
   cudaGraph_t g = nullptr;
   cudaGraphConditionalHandle h;
   bool capturing = false;
+  const char* step = "create";
   auto give_up = [&]() {
+    const cudaError_t why = cudaGetLastError();
+    const std::string before = ctx->err;  // set by a failing launch inside the capture
+    ctx->err = std::string("device-driven solve graph not built (") + step + ": " +
+               cudaGetErrorString(why) + (before.empty() ? "" : "; " + before) +
+               "); the loop runs from the host";
     if (capturing) {
       cudaGraph_t junk = nullptr;
       cudaStreamEndCapture(st, &junk);
@@ -375,6 +400,7 @@ bool build_solve_graph(ideq_ctx* ctx, const OpDev& od, const ideq_shape& s, cons
   };
   if (cudaGraphCreate(&g, 0) != cudaSuccess) return give_up();
   if (cudaGraphConditionalHandleCreate(&h, g, 0, 0) != cudaSuccess) return give_up();
+  step = "capture the condition";
   if (cudaStreamBeginCaptureToGraph(st, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) !=
       cudaSuccess)
     return give_up();
@@ -398,6 +424,7 @@ bool build_solve_graph(ideq_ctx* ctx, const OpDev& od, const ideq_shape& s, cons
   cudaGraphNode_t wnode;
   if (cudaGraphAddNode(&wnode, g, &first, nullptr, 1, &cp) != cudaSuccess) return give_up();
   cudaGraph_t body = cp.conditional.phGraph_out[0];
+  step = "capture the body";
   if (cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0,
                                     cudaStreamCaptureModeRelaxed) != cudaSuccess)
     return give_up();
@@ -411,8 +438,10 @@ bool build_solve_graph(ideq_ctx* ctx, const OpDev& od, const ideq_shape& s, cons
   const long long body_launches = ctx->launches - l0 + 1;
   ctx->launches = l0;
   capturing = false;
+  step = "end the body capture";
   if (cudaStreamEndCapture(st, &body) != cudaSuccess) return give_up();
   cudaGraphExec_t exec = nullptr;
+  step = "instantiate";
   if (cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) return give_up();
   ctx->sg.g = g;
   ctx->sg.exec = exec;
@@ -521,6 +550,7 @@ ideq_status ideq_destroy(ideq_ctx* ctx) {
   if (!ctx) return IDEQ_ERR_ARG;
   cudaStreamSynchronize(ctx->stream);
   ctx->drop_graph();
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   ctx->plan.reset();
   ctx->train.reset();
   ctx->warm_plan.reset();
@@ -684,6 +714,7 @@ ideq_status ideq_solve(ideq_ctx* ctx, const ideq_operator* op, ideq_shape shape,
   const int eager = use_graph ? std::min(2, p->max_iter) : p->max_iter;
   const int poll = p->tol > 0.0 ? 2 : 0;
   bool graphed = false;
+  ctx->last_graphed = false;
   for (int it = 0; it < eager; ++it) {
     if ((s = iterate(ctx, od, shape, y, p, it & 1, 1, avg)) != IDEQ_OK) return s;
     if (!use_graph && poll && ((it + 1) % poll == 0) && it + 1 < p->max_iter) {
@@ -709,6 +740,7 @@ ideq_status ideq_solve(ideq_ctx* ctx, const ideq_operator* op, ideq_shape shape,
       }
     }
   }
+  ctx->last_graphed = graphed;
   CK(launch_gather_parity(shape.n, ctx->sv_per, ctx->sv.parity, ctx->xb[0], ctx->xb[1], x_out, st));
   ctx->launches += 1;
   if (p->average) {
@@ -917,6 +949,12 @@ ideq_status ideq_launch_count(ideq_ctx* ctx, int64_t* count) {
   if (!ctx || !count) return IDEQ_ERR_ARG;
   *count = ctx->launches;
   ctx->launches = 0;
+  return IDEQ_OK;
+}
+
+ideq_status ideq_solve_graphed(ideq_ctx* ctx, int* graphed) {
+  if (!ctx || !graphed) return IDEQ_ERR_ARG;
+  *graphed = ctx->last_graphed ? 1 : 0;
   return IDEQ_OK;
 }
 

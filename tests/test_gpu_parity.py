@@ -249,6 +249,28 @@ def test_device_driven_loop_matches_host_loop(tol, max_iter):
         assert list(ig) == [max_iter, max_iter]
 
 
+def test_solve_graph_holds_tensor_core_convs():
+    """The 16-bit U-Net solve (tcgen05 convs launched with programmatic stream
+    serialisation) runs its loop in the device-driven graph and matches the
+    host-driven loop bit for bit."""
+    cfg, wl, net, ops, ys = setup("C1a", n=2, h=64, w=64)
+    b = B()
+    y = torch.tensor(ys, device="cuda")
+    out = []
+    for host in (False, True):
+        ctx = ctx_for(cfg, wl, b.IDEQ_FP16)
+        b.ideq_prof_enable(ctx, host)
+        params = b.make_params(cfg["lam"], cfg["tau"], cfg["beta"], tol=cfg["tol"], max_iter=60)
+        info = b.InfoBuffers(2)
+        x, st = b.ideq_solve(ctx, op_for(cfg, wl), y, params, info=info, allow_maxiter=True)
+        torch.cuda.synchronize()
+        assert b.ideq_solve_graphed(ctx) == (not host)
+        out.append((to_np(x), info.iters.cpu().numpy()))
+    (xg, ig), (xh, ih) = out
+    assert np.array_equal(ig, ih)
+    assert np.array_equal(xg, xh)
+
+
 def test_proximal_variant_matches_oracle_fp32():
     """i-DEQ-P (Algorithm 2): x^{k+1} = prox_{tau f}(z - tau lambda grad g(z)) with the
     closed-form inpainting prox, 30 updates on two masked images, against the oracle."""
