@@ -48,3 +48,17 @@ def test_num_params_matches_synth_layout():
         assert n == sum(int(np.prod(s)) for _, _, s, *_ in G.unet_layout(3, widths, 2))
     d = binding.net_desc({"type": "cnn", "chans": [1, 32, 32, 32, 1]}, 1)
     assert binding.ideq_num_params(d) == 19008
+
+
+def test_null_context_calls_are_argument_errors(lib):
+    """Context queries check their arguments before any CUDA call (no GPU needed)."""
+    from paper_2605_19705_gb300 import binding
+    lib.ideq_solve_graphed.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]
+    lib.ideq_launch_count.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]
+    lib.ideq_last_error.argtypes = [ctypes.c_void_p]
+    lib.ideq_last_error.restype = ctypes.c_char_p
+    g, n = ctypes.c_int(7), ctypes.c_int64(7)
+    assert lib.ideq_solve_graphed(None, ctypes.byref(g)) == binding.IDEQ_ERR_ARG
+    assert lib.ideq_launch_count(None, ctypes.byref(n)) == binding.IDEQ_ERR_ARG
+    assert g.value == 7 and n.value == 7  # outputs untouched on error
+    assert lib.ideq_last_error(None) == b"null context"
