@@ -256,7 +256,11 @@ ideq_status ideq_warm_get(ideq_ctx *ctx, float *weights);
  * looks up that array's device address (cudaGetSymbolAddress) with the device
  * current, so make it before any stream capture.  All calls share the array:
  * calls that overlap on the GPU (different streams, no ordering) race; calls on
- * one stream are safe.  Nothing in the array needs clearing between calls. */
+ * one stream are safe.  Nothing in the array needs clearing between calls.
+ * The looked-up address is kept for the life of the process, so a device reset
+ * (cudaDeviceReset, or a reset of the primary context) is not supported once the
+ * call has been made on that device.  Pointers need only 4-byte alignment; the
+ * vectorised path is taken when all five image pointers are 16-byte aligned. */
 ideq_status ideq_red_update_noalloc(int n, int per_img, const float *z, const float *grad_f,
                                     const float *grad_g, const float *x, float *x_new,
                                     float lambda, float tau, double *step_sq, double *x_sq,
@@ -270,6 +274,24 @@ ideq_status ideq_red_update_noalloc(int n, int per_img, const float *z, const fl
  * since the last read, and resets them (synchronises the stream). */
 ideq_status ideq_prof_enable(ideq_ctx *ctx, int on);
 ideq_status ideq_prof_read(ideq_ctx *ctx, double *ms, int64_t *launches, double *flops);
+/* Times `reps` back-to-back repetitions of the tensor-core convolution launches
+ * of one regulariser evaluation (forward list, then the input-gradient list) on
+ * the current plan's buffers, launched exactly as in a solve (programmatic
+ * dependent launch kept), with one pair of CUDA events on the context's stream
+ * around all of them.  *ms is the elapsed time (host double), *launches and
+ * *flops (nullable) the launch count and the summed algorithmic FLOPs (2 M N K
+ * per launch).  The plan's buffers hold whatever the last call left; the
+ * results written there are meaningless afterwards.  Synchronises the stream.
+ * Needs a plan (after a solve, step or ideq_grad_reg), else IDEQ_ERR_ARG. */
+ideq_status ideq_time_convs(ideq_ctx *ctx, int reps, double *ms, int64_t *launches,
+                            double *flops);
+/* Algorithmic FLOPs of every convolution (all kinds, all n images) of one
+ * iteration of the current plan: forward pass plus input-gradient pass. */
+ideq_status ideq_plan_flops(ideq_ctx *ctx, double *per_iteration);
+/* Measured FP32 FFMA throughput of this GPU (host double, TFLOP/s counting 2
+ * FLOPs per FMA): a kernel of independent FMA chains on every SM, timed with
+ * CUDA events on `stream` (synchronises it); the roofline of the plain FP32 form. */
+ideq_status ideq_fp32_fma_peak(void *stream, double *tflops);
 /* Number of kernels this context launched since the last call (host count). */
 ideq_status ideq_launch_count(ideq_ctx *ctx, int64_t *count);
 /* Whether the last ideq_solve on this context ran its iterations after the first

@@ -61,8 +61,12 @@ def averaging_step(zs, steps):
 
 
 def solve_image(net, op, y, x0, lam, tau, beta, B=math.inf, tol=0.0, max_iter=50,
-                keep_history=False, average=False, prox=False):
-    """Run the iteration on one image.  Returns (x_hat, info dict)."""
+                keep_history=False, average=False, prox=False, on_update=None):
+    """Run the iteration on one image.  Returns (x_hat, info dict).
+
+    on_update(total, x_new, rel), when given, is called after every update with
+    the update count, the new iterate and its relative step (read-only hook for
+    recording; it does not change the iteration)."""
     if average and (tol > 0.0 or B < math.inf):
         raise ValueError("the averaging step needs a fixed run: tol = 0 and no restart")
     x = np.asarray(x0, dtype=np.float64).copy()
@@ -86,6 +90,8 @@ def solve_image(net, op, y, x0, lam, tau, beta, B=math.inf, tol=0.0, max_iter=50
         total += 1
         S += s
         rel = math.sqrt(s) / math.sqrt(nx) if nx > 0 else math.inf
+        if on_update is not None:
+            on_update(total, x, rel)
         if keep_history:
             info["steps"].append(math.sqrt(s))
             info["rel"].append(rel)

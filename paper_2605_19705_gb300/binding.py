@@ -85,6 +85,9 @@ _sig = {
     "ideq_prof_enable": [c_void_p, c_int],
     "ideq_prof_read": [c_void_p, P(c_double), P(ctypes.c_int64), P(c_double)],
     "ideq_launch_count": [c_void_p, P(ctypes.c_int64)],
+    "ideq_time_convs": [c_void_p, c_int, P(c_double), P(ctypes.c_int64), P(c_double)],
+    "ideq_plan_flops": [c_void_p, P(c_double)],
+    "ideq_fp32_fma_peak": [c_void_p, P(c_double)],
     "ideq_solve_graphed": [c_void_p, P(c_int)],
     "ideq_red_update_noalloc": [c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                 c_float, c_float, c_void_p, c_void_p, c_void_p],
@@ -309,6 +312,31 @@ def ideq_prof_read(ctx: Context):
     ms, n, fl = c_double(0), ctypes.c_int64(0), c_double(0)
     ctx.check(_lib.ideq_prof_read(ctx.h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(fl)))
     return ms.value, int(n.value), fl.value
+
+
+def ideq_time_convs(ctx: Context, reps: int):
+    """(ms, launches, flops) of `reps` back-to-back repetitions of the plan's
+    tensor-core conv launches, timed with CUDA events on the context's stream."""
+    ms, n, fl = c_double(0), ctypes.c_int64(0), c_double(0)
+    ctx.check(_lib.ideq_time_convs(ctx.h, int(reps), ctypes.byref(ms), ctypes.byref(n),
+                                   ctypes.byref(fl)))
+    return ms.value, int(n.value), fl.value
+
+
+def ideq_plan_flops(ctx: Context) -> float:
+    """Algorithmic FLOPs of all convolutions of one iteration of the current plan."""
+    v = c_double(0)
+    ctx.check(_lib.ideq_plan_flops(ctx.h, ctypes.byref(v)))
+    return v.value
+
+
+def ideq_fp32_fma_peak() -> float:
+    """Measured FP32 FFMA throughput of the current GPU, TFLOP/s."""
+    v = c_double(0)
+    st = _lib.ideq_fp32_fma_peak(_stream(), ctypes.byref(v))
+    if st != IDEQ_OK:
+        raise IdeqError(st, "ideq_fp32_fma_peak failed")
+    return v.value
 
 
 def ideq_launch_count(ctx: Context) -> int:

@@ -53,9 +53,10 @@ struct ideq_ctx {
   // scratch for the stand-alone operator calls
   float* scratch = nullptr;
   size_t scratch_bytes = 0;
-  // Device-driven solve loop: one CUDA graph whose while node repeats two
-  // iterations (body captured once) for as long as an image is running, so the
-  // solve needs no host round trip per iteration.  Rebuilt when the plan, the
+  // Device-driven solve loop: one CUDA graph whose while node repeats a body of
+  // two iterations (the second inside an IF node, so the condition is checked
+  // after every iteration) for as long as an image is running, so the solve
+  // needs no host round trip per iteration.  Rebuilt when the plan, the
   // operator, y or the parameters change; a graph that cannot be built falls back
   // to the host-driven loop.
   struct SolveGraph {
@@ -192,6 +193,7 @@ ideq_status ensure_plan(ideq_ctx* ctx, const ideq_shape& s) {
   v.best = dp + 5 * n;
   v.k0 = ip + 5 * n;
   v.snap = ip + 6 * n;
+  v.skip = ip + 7 * n;
   v.zsum = (double*)(m + o_zs);
   v.zsnap = (double*)(m + o_zn);
   v.part_s = (double*)(m + o_p);
@@ -211,7 +213,7 @@ ideq_status ensure_plan(ideq_ctx* ctx, const ideq_shape& s) {
   CK(cudaMemsetAsync(m, 0, off, ctx->stream));
   std::unique_ptr<NetPlan> np(new NetPlan());
   std::string e;
-  if (!np->build(ctx->w.get(), s.n, s.h, s.w, ctx->precision, v.gsum, &e))
+  if (!np->build(ctx->w.get(), s.n, s.h, s.w, ctx->precision, v.gsum, &e, v.skip))
     return fail(ctx, IDEQ_ERR_UNSUPPORTED, "plan: " + e);
   ctx->plan = std::move(np);
   return IDEQ_OK;
@@ -343,9 +345,13 @@ bool graph_enabled() {
   return on;
 }
 
+// Everything of the operator that iterate() bakes into the captured graph by
+// value: the kind and kernel size pick the kernels, the pointers and the scalars
+// (saturation gain, Rician sigma) are launch arguments.  Kernel and mask contents
+// are read at run time and may change between solves.
 bool same_op(const OpDev& a, const OpDev& b) {
   return a.kind == b.kind && a.kh == b.kh && a.kw == b.kw && a.kernel == b.kernel &&
-         a.mask == b.mask && a.gain == b.gain;
+         a.mask == b.mask && a.gain == b.gain && a.sigma == b.sigma;
 }
 
 bool same_params(const ideq_params& a, const ideq_params& b) {
@@ -423,23 +429,64 @@ bool build_solve_graph(ideq_ctx* ctx, const OpDev& od, const ideq_shape& s, cons
   cp.conditional.size = 1;
   cudaGraphNode_t wnode;
   if (cudaGraphAddNode(&wnode, g, &first, nullptr, 1, &cp) != cudaSuccess) return give_up();
+  // body: iteration (parity 0); an IF node holding iteration (parity 1) that runs
+  // only while an image is still running; the while condition.  The loop thus
+  // checks after every iteration and never computes an iteration past the last
+  // running image.
   cudaGraph_t body = cp.conditional.phGraph_out[0];
+  cudaGraphConditionalHandle h_if;
+  step = "create the inner condition";
+  if (cudaGraphConditionalHandleCreate(&h_if, body, 0, 0) != cudaSuccess) return give_up();
   step = "capture the body";
   if (cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0,
                                     cudaStreamCaptureModeRelaxed) != cudaSuccess)
     return give_up();
   capturing = true;
   const long long l0 = ctx->launches;
-  for (int par = 0; par < 2; ++par)
-    if (iterate(ctx, od, s, y, p, par, 1, p->average != 0) != IDEQ_OK) return give_up();
-  if (launch_loop_cond(h, ctx->sv.n_running, ctx->sv.loop_count, 0, max_bodies, ctx->d_err,
-                       st) != cudaSuccess)
-    return give_up();
-  const long long body_launches = ctx->launches - l0 + 1;
+  if (iterate(ctx, od, s, y, p, 0, 1, p->average != 0) != IDEQ_OK) return give_up();
+  const long long iter_launches = ctx->launches - l0;
   ctx->launches = l0;
+  if (launch_if_cond(h_if, ctx->sv.n_running, st) != cudaSuccess) return give_up();
+  cudaStreamCaptureStatus cs;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  if (cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, nullptr, &ndeps) != cudaSuccess ||
+      ndeps != 1)
+    return give_up();
+  cudaGraphNode_t cond_node = deps[0];
   capturing = false;
   step = "end the body capture";
   if (cudaStreamEndCapture(st, &body) != cudaSuccess) return give_up();
+  cudaGraphNodeParams ip = {};
+  ip.type = cudaGraphNodeTypeConditional;
+  ip.conditional.handle = h_if;
+  ip.conditional.type = cudaGraphCondTypeIf;
+  ip.conditional.size = 1;
+  cudaGraphNode_t if_node;
+  step = "add the inner condition";
+  if (cudaGraphAddNode(&if_node, body, &cond_node, nullptr, 1, &ip) != cudaSuccess)
+    return give_up();
+  cudaGraph_t inner = ip.conditional.phGraph_out[0];
+  step = "capture the inner iteration";
+  if (cudaStreamBeginCaptureToGraph(st, inner, nullptr, nullptr, 0,
+                                    cudaStreamCaptureModeRelaxed) != cudaSuccess)
+    return give_up();
+  capturing = true;
+  if (iterate(ctx, od, s, y, p, 1, 1, p->average != 0) != IDEQ_OK) return give_up();
+  ctx->launches = l0;
+  capturing = false;
+  if (cudaStreamEndCapture(st, &inner) != cudaSuccess) return give_up();
+  step = "capture the loop condition";
+  if (cudaStreamBeginCaptureToGraph(st, body, &if_node, nullptr, 1,
+                                    cudaStreamCaptureModeRelaxed) != cudaSuccess)
+    return give_up();
+  capturing = true;
+  if (launch_loop_cond(h, ctx->sv.n_running, ctx->sv.loop_count, 0, max_bodies, ctx->d_err,
+                       st) != cudaSuccess)
+    return give_up();
+  capturing = false;
+  if (cudaStreamEndCapture(st, &body) != cudaSuccess) return give_up();
+  const long long body_launches = iter_launches;  // per iteration run in the graph
   cudaGraphExec_t exec = nullptr;
   step = "instantiate";
   if (cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) return give_up();
@@ -643,6 +690,7 @@ ideq_status ideq_grad_reg(ideq_ctx* ctx, ideq_shape shape, const float* z, float
   const size_t bytes = (size_t)shape.n * shape.c * shape.h * shape.w * 4;
   CK(cudaMemcpyAsync(P->z, z, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
   CK(launch_zero_d(shape.n, ctx->gsum, ctx->stream));
+  CK(cudaMemsetAsync(ctx->sv.skip, 0, shape.n * sizeof(int), ctx->stream));  // every image
   CK(run_steps(P->fwd, ctx->d_err, ctx->stream, &ctx->prof, &ctx->launches));
   CK(run_steps(P->vjp, ctx->d_err, ctx->stream, &ctx->prof, &ctx->launches));
   CK(cudaMemcpyAsync(grad, P->grad, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -752,10 +800,12 @@ ideq_status ideq_solve(ideq_ctx* ctx, const ideq_operator* op, ideq_shape shape,
   // overall status (stream already synchronised by check_timeout)
   std::vector<int> hs(shape.n), ht(shape.n);
   CK(cudaMemcpy(hs.data(), ctx->sv.status, shape.n * 4, cudaMemcpyDeviceToHost));
-  if (graphed) {  // launches the graph ran: one condition kernel, then bodies of two iterations
+  if (graphed) {  // launches the graph ran: one condition kernel, then per body up to two
+                  // iterations and two condition kernels
     CK(cudaMemcpy(ht.data(), ctx->sv.total, shape.n * 4, cudaMemcpyDeviceToHost));
     const int last = *std::max_element(ht.begin(), ht.end());
-    ctx->launches += 1 + (long long)std::max(0, (last - 2 + 1) / 2) * ctx->sg.body_launches;
+    const long long in_graph = std::max(0, last - 2), bodies = (in_graph + 1) / 2;
+    ctx->launches += 1 + in_graph * ctx->sg.body_launches + 2 * bodies;
   }
   bool div = false, maxit = false;
   for (int v : hs) {
@@ -942,6 +992,50 @@ ideq_status ideq_prof_read(ideq_ctx* ctx, double* ms, int64_t* launches, double*
   ctx->prof.used = 0;
   ctx->prof.launches = 0;
   ctx->prof.flops = 0;
+  return IDEQ_OK;
+}
+
+ideq_status ideq_time_convs(ideq_ctx* ctx, int reps, double* ms, int64_t* launches,
+                            double* flops) {
+  clear_stale_cuda_error();
+  if (!ctx || reps < 1 || !ms) return fail(ctx, IDEQ_ERR_ARG, "bad arguments");
+  NetPlan* P = ctx->plan.get();
+  if (!P) return fail(ctx, IDEQ_ERR_ARG, "no plan yet: run a solve, step or grad_reg first");
+  cudaStream_t st = ctx->stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  long long nl = 0;
+  double fl = 0;
+  cudaError_t e = cudaMemsetAsync(ctx->sv.skip, 0, P->n * sizeof(int), st);  // every image
+  if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+  for (int r = 0; r < reps && e == cudaSuccess; ++r)
+    for (const std::vector<Step>* list : {&P->fwd, &P->vjp})
+      for (const Step& s : *list) {
+        if (!s.tc || s.quant_n > 0 || e != cudaSuccess) continue;
+        e = launch_conv_tc(s.tc, s.a, ctx->d_err, st);
+        nl += 1;
+        fl += s.a.flops();
+      }
+  if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "ideq_time_convs");
+  ctx->launches += nl;
+  *ms = t;
+  if (launches) *launches = nl;
+  if (flops) *flops = fl;
+  return check_timeout(ctx);
+}
+
+ideq_status ideq_plan_flops(ideq_ctx* ctx, double* per_iteration) {
+  if (!ctx || !per_iteration) return IDEQ_ERR_ARG;
+  NetPlan* P = ctx->plan.get();
+  if (!P) return fail(ctx, IDEQ_ERR_ARG, "no plan yet: run a solve, step or grad_reg first");
+  *per_iteration = P->fwd_flops + P->vjp_flops;
   return IDEQ_OK;
 }
 

@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(256) feat2img_kernel(ConvArgs a) {
   float* wsm = sm + F2_E * F2_E * F2_CP;  // [c][9][C]
   const int C = a.Cin, c = a.Cout;
   const int b = blockIdx.z;
+  if (a.skip && a.skip[b]) return;  // frozen image of a solve: not needed
   const int y0 = blockIdx.y * F2_T, x0 = blockIdx.x * F2_T;
   const TIn* in = (const TIn*)a.in;
   const float* w = (const float*)a.wB;  // [c][9*C], k = t*C + ci
@@ -157,6 +158,7 @@ __global__ void __launch_bounds__(256) img2feat_kernel(ConvArgs a) {
   TOut* stg = (TOut*)(dsm + C * 9 * CIN);          // [256 px][C + 8]
   const int SP = C + 8;                            // padded pixel stride (elements)
   const int b = blockIdx.z;
+  if (a.skip && a.skip[b]) return;  // frozen image of a solve: not needed
   const int y0 = blockIdx.y * ET, x0 = blockIdx.x * ET;
   const float* in = (const float*)a.in;
   for (int e = threadIdx.x; e < CIN * EH * EH; e += 256) {

@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(C * 4) img2feat_rb_kernel(ConvArgs a) {
   __shared__ __align__(16) float wsm[9 * CIN][C + I2_WP];  // k-major
   extern __shared__ uint4 stg[];                   // [nout][256 px][CH]
   const int b = blockIdx.z, y0 = blockIdx.y * I2_TY, x0 = blockIdx.x * I2_TX;
+  if (a.skip && a.skip[b]) return;  // frozen image of a solve: not needed
   const float* in = (const float*)a.in;
   for (int e = threadIdx.x; e < CIN * I2_EY * I2_EX; e += NT) {
     const int ci = e / (I2_EY * I2_EX), p = e % (I2_EY * I2_EX);
@@ -168,6 +169,7 @@ __global__ void __launch_bounds__(256) feat2img_rb_kernel(ConvArgs a) {
   float* wsm = (float*)(tile + EY * EX * PS);  // [dy][e][g][12]: (o, dx) at 3 o + dx
   __shared__ double red[32];
   const int b = blockIdx.z, y0 = blockIdx.y * 8, x0 = blockIdx.x * TX;
+  if (a.skip && a.skip[b]) return;  // frozen image of a solve: not needed
   const uint4* in = (const uint4*)a.in;
   for (int e = threadIdx.x; e < EY * EX * G; e += 256) {
     const int g = e % G, p = e / G;

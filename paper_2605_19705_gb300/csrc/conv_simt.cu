@@ -26,6 +26,12 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
   const long long m0 = (long long)blockIdx.x * BM;
   const int n0 = blockIdx.y * BN;
   const int HW = a.H * a.W;
+  if (a.skip) {  // every image this block touches is frozen in a solve: nothing needed
+    const long long m_last = (m0 + BM < M ? m0 + BM : M) - 1;
+    bool any = false;
+    for (long long i = m0 / HW; i <= m_last / HW; ++i) any |= a.skip[i] == 0;
+    if (!any) return;
+  }
   const TIn* __restrict__ in = (const TIn*)a.in;
   const float* __restrict__ inf = (const float*)a.in;
   const float* __restrict__ wf = (const float*)a.wB;
@@ -188,6 +194,12 @@ __global__ void __launch_bounds__(256) conv_simt_f32_kernel(ConvArgs a) {
   const long long m0 = (long long)blockIdx.x * BM;
   const int n0 = blockIdx.y * BN;
   const int HW = a.H * a.W;
+  if (a.skip) {  // every image this block touches is frozen in a solve: nothing needed
+    const long long m_last = (m0 + BM < M ? m0 + BM : M) - 1;
+    bool any = false;
+    for (long long i = m0 / HW; i <= m_last / HW; ++i) any |= a.skip[i] == 0;
+    if (!any) return;
+  }
   const int SH = a.mode == CM_DOWN ? 2 * a.H : a.H;
   const int SW = a.mode == CM_DOWN ? 2 * a.W : a.W;
   const float* __restrict__ in = (const float*)a.in;

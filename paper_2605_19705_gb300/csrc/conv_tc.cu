@@ -59,6 +59,7 @@ struct TcArgs {
   const float* img_aux;
   float* img_out;
   double* sumsq;
+  const int* skip;  // per image, nonzero: frozen, its tiles are not computed (nullable)
   int* err;
 };
 
@@ -455,17 +456,28 @@ struct TileCoord {
   int img, h0, w0, n0;
 };
 
-// Tile t covers MS consecutive 128-row M-tiles (sub-tiles) and BN columns.
-// An M-tile index past the last one maps to an image index >= n, which the
-// TMA loads fill with zeros and the TMA stores clip.
-IDEQ_DEV TileCoord tile_coord(const TcArgs& a, int t, int bn, int ms, int sub) {
+// The images a launch computes: all n, or, when the caller passes per-image skip
+// flags (frozen images of a solve), the nrun images not skipped, in increasing
+// order (list[j] = image of the j-th computed image; null = identity).
+struct ImgMap {
+  int nrun;
+  const int* list;
+  IDEQ_DEV int img(int j) const { return list ? list[j] : j; }
+};
+constexpr int kMaxListImages = 128;  // images of a launch that the skip list can hold
+
+// Tile t covers MS consecutive 128-row M-tiles (sub-tiles) and BN columns of the
+// computed images.  An M-tile index past the last one maps to an image index >= n,
+// which the TMA loads fill with zeros and the TMA stores clip.
+IDEQ_DEV TileCoord tile_coord(const TcArgs& a, const ImgMap& im, int t, int bn, int ms, int sub) {
   const int per_img = a.tiles_h * a.tiles_w;
-  const int tiles_m = a.n * per_img;
+  const int tiles_m = im.nrun * per_img;
   const int groups = (tiles_m + ms - 1) / ms;
   const int nidx = t / groups, m = (t - nidx * groups) * ms + sub;
   TileCoord c;
-  c.img = m / per_img;
-  const int rr = m - c.img * per_img;
+  const int j = m / per_img;
+  c.img = j < im.nrun ? im.img(j) : a.n;
+  const int rr = m - j * per_img;
   c.h0 = (rr / a.tiles_w) * a.Ht;
   c.w0 = (rr % a.tiles_w) * a.Wt;
   c.n0 = nidx * bn;
@@ -517,12 +529,12 @@ constexpr int HALO_PF = 4;       // rows prefetched into L2 ahead of the row bei
 // CTA need them), or, in the sliding form, each CTA runs a contiguous range of
 // rows and a tile that continues its run loads only row y+1, reusing y-1 and y
 // (measured slower on the U-Net's 64-channel layers: 90 vs 60 us).
-IDEQ_DEV TileCoord halo_coord(const TcArgs& a, int t) {
+IDEQ_DEV TileCoord halo_coord(const TcArgs& a, const ImgMap& im, int t) {
   const int strip = t / a.tiles_h;
   TileCoord c;
   c.h0 = t - strip * a.tiles_h;
   c.w0 = (strip % a.tiles_w) * 128;
-  c.img = strip / a.tiles_w;
+  c.img = im.img(strip / a.tiles_w);
   c.n0 = 0;
   return c;
 }
@@ -573,6 +585,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint8_t* sAux = sOut + a.nbo * a.nout * PANEL;                 // [warp][nba][naux][WBOX]
   uint64_t* bars = (uint64_t*)(sAux + a.nba * a.naux * PANEL);
   uint32_t* tmem_slot = (uint32_t*)(bars + 2 * ST + 6 + MAX_NBA * EPI_WARPS);
+  int* s_list = (int*)(tmem_slot + 4);  // [kMaxListImages] computed images, then their count
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + ST);
@@ -581,20 +594,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t drain = smem_u32(bars + 2 * ST + 4);
   const uint32_t bres = smem_u32(bars + 2 * ST + 5);
   const uint32_t auxbar0 = smem_u32(bars + 2 * ST + 6);  // [warp][MAX_NBA]
-  const int ntiles = ((a.n * a.tiles_h * a.tiles_w + MS - 1) / MS) * a.tiles_n;
-  // this CTA's tiles: t_first + i * t_step, i < my_tiles (a contiguous range in
-  // the halo form, a grid-strided sequence otherwise)
-  int t_first, t_step, my_tiles;
-  if (HALO && a.slide) {
-    t_first = (int)(((long long)blockIdx.x * ntiles) / gridDim.x);
-    my_tiles = (int)(((long long)(blockIdx.x + 1) * ntiles) / gridDim.x) - t_first;
-    t_step = 1;
-  } else {
-    t_first = blockIdx.x;
-    t_step = gridDim.x;
-    my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-  }
-
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
       mbar_init(full0 + 8 * s, 1);
@@ -627,6 +626,35 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   // own set-up as soon as this kernel's CTAs leave their SMs.
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  // the images to compute (the skip flags were written by an earlier kernel of the
+  // stream, complete after the wait above)
+  const bool use_list = a.skip != nullptr && a.n <= kMaxListImages;
+  if (warp == 0 && use_list) {
+    int cnt = 0;
+    for (int base = 0; base < a.n; base += 32) {
+      const int b = base + lane;
+      const bool on = b < a.n && a.skip[b] == 0;
+      const unsigned bal = __ballot_sync(0xffffffffu, on);
+      if (on) s_list[cnt + __popc(bal & ((1u << lane) - 1u))] = b;
+      cnt += __popc(bal);
+    }
+    if (lane == 0) s_list[kMaxListImages] = cnt;
+  }
+  __syncthreads();
+  const ImgMap im{use_list ? s_list[kMaxListImages] : a.n, use_list ? s_list : nullptr};
+  const int ntiles = ((im.nrun * a.tiles_h * a.tiles_w + MS - 1) / MS) * a.tiles_n;
+  // this CTA's tiles: t_first + i * t_step, i < my_tiles (a contiguous range in
+  // the halo form, a grid-strided sequence otherwise)
+  int t_first, t_step, my_tiles;
+  if (HALO && a.slide) {
+    t_first = (int)(((long long)blockIdx.x * ntiles) / gridDim.x);
+    my_tiles = (int)(((long long)(blockIdx.x + 1) * ntiles) / gridDim.x) - t_first;
+    t_step = 1;
+  } else {
+    t_first = blockIdx.x;
+    t_step = gridDim.x;
+    my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  }
 
   if (warp == 0) {
     if (lane == 0) {
@@ -641,7 +669,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       bool ok = true;
       if (HALO && !a.slide) {  // one slot of three row boxes per tile
         for (int i = 0; i < my_tiles && ok; ++i) {
-          const TileCoord tc = halo_coord(a, t_first + i * t_step);
+          const TileCoord tc = halo_coord(a, im, t_first + i * t_step);
           const int s = g % ST, j = g / ST;
           if (j > 0 && !mbar_wait(empty0 + 8 * s, (j - 1) & 1, a.err, 1)) {
             ok = false;
@@ -656,7 +684,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       } else if (HALO) {  // sliding: single row boxes, reused across consecutive rows
         for (int i = 0; i < my_tiles && ok; ++i) {
           const int t = t_first + i * t_step;
-          const TileCoord tc = halo_coord(a, t);
+          const TileCoord tc = halo_coord(a, im, t);
           const bool fresh = i == 0 || t % a.tiles_h == 0;  // three new boxes
           // rows loaded a few tiles from now are pulled into L2 first: each row is
           // read by this CTA alone, so its load would otherwise wait on DRAM
@@ -676,7 +704,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
       }
       for (int i = 0; i < my_tiles && ok && STREAM; ++i) {  // streamed halo
-        const TileCoord tc = tile_coord(a, t_first + i * t_step, BN, MS, 0);
+        const TileCoord tc = tile_coord(a, im, t_first + i * t_step, BN, MS, 0);
         for (int kc = 0; kc < 3 * a.cpt; ++kc) {  // (row dy, channel chunk c)
           const int s = g % ST, j = g / ST;
           if (j > 0 && !mbar_wait(empty0 + 8 * s, (j - 1) & 1, a.err, 1)) {
@@ -695,7 +723,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
       for (int i = 0; i < my_tiles && ok && !HALO && !STREAM; ++i) {
         const int t = t_first + i * t_step;
-        const TileCoord tc = tile_coord(a, t, BN, MS, 0);
+        const TileCoord tc = tile_coord(a, im, t, BN, MS, 0);
         for (int kc = 0; kc < a.nk; ++kc) {
           const int s = g % ST, j = g / ST;
           if (j > 0 && !mbar_wait(empty0 + 8 * s, (j - 1) & 1, a.err, 1)) {
@@ -708,7 +736,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const uint32_t dB = smem_u32(sB + s * B_STAGE);
 #pragma unroll
             for (int sub = 0; sub < MS; ++sub) {
-              const TileCoord sc = sub == 0 ? tc : tile_coord(a, t, BN, MS, sub);
+              const TileCoord sc = sub == 0 ? tc : tile_coord(a, im, t, BN, MS, sub);
               const uint32_t dAs = dA + sub * A_TILE;
               if (a.mode == CM_DOWN) {
                 const int k0 = kc * KCH;
@@ -873,7 +901,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(tempty0 + 8 * b);
-        const TileCoord tc = HALO ? halo_coord(a, t) : tile_coord(a, t, BN, MS, 0);
+        const TileCoord tc = HALO ? halo_coord(a, im, t) : tile_coord(a, im, t, BN, MS, 0);
         const int m = 32 * q + lane;
         const int x = tc.w0 + m % a.Wt, y = tc.h0 + m / a.Wt;
         double ssq = 0.0;
@@ -922,7 +950,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       auto aux_load = [&](int k) {
         const int i = k / npan, r = k - i * npan, sub = r / nper, p = r - sub * nper;
         const int t = t_first + (lt0 + i * lstep) * t_step;
-        const TileCoord nc = HALO ? halo_coord(a, t) : tile_coord(a, t, BN, MS, sub);
+        const TileCoord nc = HALO ? halo_coord(a, im, t) : tile_coord(a, im, t, BN, MS, sub);
         const int buf = k % a.nba;
         const uint32_t bar = xbar + 8 * buf;
         mbar_expect_tx(bar, (uint32_t)(a.naux * WBOX));
@@ -961,7 +989,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
           if constexpr (sizeof(TA) == 1) {  // FP8 operands: undo the two scales
             const float sa = *a.a_scale;
-            const float* ws = a.w_scale + tile_coord(a, t, BN, MS, sub).n0 + PW * p + colh;
+            const float* ws = a.w_scale + tile_coord(a, im, t, BN, MS, sub).n0 + PW * p + colh;
 #pragma unroll
             for (int i = 0; i < 32; ++i) v[i] *= sa * __ldg(ws + i);
           }
@@ -970,7 +998,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           fence_async_smem();
           __syncwarp();
           if (lane == 0) {
-            const TileCoord tc = HALO ? halo_coord(a, t) : tile_coord(a, t, BN, MS, sub);
+            const TileCoord tc = HALO ? halo_coord(a, im, t) : tile_coord(a, im, t, BN, MS, sub);
             for (int i = 0; i < a.nout; ++i)
               epi_tma(true, a, tmO[i], ob + (uint32_t)(i * WBOX), tc, q,
                       tc.n0 + PW * p + colh, 0);
@@ -1068,7 +1096,7 @@ bool tc_supported(const ConvArgs& a, int op_dt) {
 
 static size_t fixed_smem(int nout, int naux, int nbo, int nba, int stages) {
   return 1024 + (size_t)(nbo * nout + nba * naux) * PANEL +
-         (2 * stages + 6 + MAX_NBA * EPI_WARPS) * 8 + 16;
+         (2 * stages + 6 + MAX_NBA * EPI_WARPS) * 8 + 16 + 4 * (kMaxListImages + 1);
 }
 
 constexpr size_t kMaxSmem = 227 * 1024;
@@ -1389,6 +1417,7 @@ cudaError_t launch_conv_tc(const TcPlan* p, const ConvArgs& a, int* err_flag, cu
   t.img_aux = (const float*)a.aux0;
   t.img_out = (float*)a.out;
   t.sumsq = a.sumsq;
+  t.skip = a.skip;
   t.a_scale = a.a_scale;
   t.w_scale = a.w_scale;
   t.err = err_flag;

@@ -59,6 +59,9 @@ struct ConvArgs {
   double* sumsq = nullptr;     // per-image accumulator of 1/2 sum(out^2), or null
   const float* a_scale = nullptr;  // FP8 operands: activation scale (device scalar)
   const float* w_scale = nullptr;  // FP8 operands: weight scale per output column [N]
+  // per-image flags (device, n ints; nullable): nonzero = the image is frozen in a
+  // solve and its outputs are not needed, so the launch may skip its work
+  const int* skip = nullptr;
   IDEQ_HD int N() const { return outmap == OM_D2S ? 4 * Cout : Cout; }
   IDEQ_HD int K() const { return mode == CM_CONV3 ? 9 * Cin : (mode == CM_DOWN ? 4 * Cin : Cin); }
   IDEQ_HD long long M() const { return (long long)n * H * W; }
@@ -92,6 +95,16 @@ enum WForm { WF_CONV3_FWD = 0, WF_CONV3_DGRAD, WF_DOWN_FWD, WF_DOWN_DGRAD, WF_UP
 cudaError_t launch_weight_form(int form, int cin, int cout, const float* src, float* dst_f32,
                                void* dst_bf16, void* dst_f16, cudaStream_t st);
 void weight_form_dims(int form, int cin, int cout, int* N, int* K);  // the form's [N][K]
+// 3x3 forms over padded channel counts (pcin >= cin, pcout >= cout; zero weights on
+// the padded rows and columns); the other forms ignore the padding
+void weight_form_dims_padded(int form, int cin, int cout, int pcin, int pcout, int* N, int* K);
+cudaError_t launch_weight_form_padded(int form, int cin, int cout, int pcin, int pcout,
+                                      const float* src, float* dst_f32, void* dst_bf16,
+                                      void* dst_f16, cudaStream_t st);
+// dst (PyTorch layout) += scale * g, g a padded GEMM-form gradient [N][K]
+cudaError_t launch_weight_unform_padded(int form, int cin, int cout, int pcin, int pcout,
+                                        const float* g, float scale, float* dst,
+                                        cudaStream_t st);
 // FP8 e4m3 weight form: w8[n][k] = e4m3(w32[n][k] / s[n]), s[n] = max_k |w32[n][k]| / 448.
 cudaError_t launch_weight_fp8(const float* w32, int N, int K, uint8_t* w8, float* scale,
                               cudaStream_t st);
@@ -174,6 +187,7 @@ struct SolverDev {
   double* energy;
   double* part_s;  // [n][nblk] partial sums of ||x_new - x||^2
   double* part_x;  // [n][nblk] partial sums of ||x||^2
+  int* skip;       // 1 once the image is frozen (its convolutions are skipped), else 0
   int* n_running;
   int* loop_count;  // bodies run by the device-driven solve loop
   // averaging step of Algorithm 1 (used when the solve asks for it)
@@ -219,6 +233,8 @@ cudaError_t launch_solver_init(int n, const SolverDev& s, float beta, cudaStream
 // raises *err (code 10) instead.
 cudaError_t launch_loop_cond(cudaGraphConditionalHandle h, const int* n_running, int* counter,
                              int first, int max_bodies, int* err, cudaStream_t st);
+// IF-node condition inside the loop body: (*n_running > 0).
+cudaError_t launch_if_cond(cudaGraphConditionalHandle h, const int* n_running, cudaStream_t st);
 cudaError_t launch_fill_info(int n, const SolverDev& s, ideq_info info, cudaStream_t st);
 int update_blocks_per_image(int per_img);
 

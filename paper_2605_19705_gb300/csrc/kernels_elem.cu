@@ -306,7 +306,7 @@ __global__ void extrapolate4_kernel(int per4, long long total4, const float4* __
 cudaError_t launch_extrapolate(int n, int per_img, const float* x, const float* xp,
                                const float* beta_eff, float* z, cudaStream_t st) {
   const long long total = (long long)n * per_img;
-  if (per_img % 4 == 0) {
+  if (per_img % 4 == 0 && (((uintptr_t)x | (uintptr_t)xp | (uintptr_t)z) & 15) == 0) {
     const long long t4 = total / 4;
     const int blocks = (int)std::min<long long>((t4 + 255) / 256, 152 * 8);
     extrapolate4_kernel<<<blocks, 256, 0, st>>>(per_img / 4, t4, (const float4*)x,
@@ -532,7 +532,7 @@ __global__ void __launch_bounds__(256) red_update_kernel(
     int per_img, const float* __restrict__ z, const float* __restrict__ gf,
     const float* __restrict__ gg, const float* __restrict__ x, float* __restrict__ xn,
     float lam, float tau, const int* __restrict__ status, double* __restrict__ part_s,
-    double* __restrict__ part_x, const float* __restrict__ addv) {
+    double* __restrict__ part_x, const float* __restrict__ addv, int vec4) {
   __shared__ double red[32];
   const int b = blockIdx.y;
   const int nblk = gridDim.x;
@@ -540,7 +540,7 @@ __global__ void __launch_bounds__(256) red_update_kernel(
   double ss = 0.0, sx = 0.0;
   const size_t base = (size_t)b * per_img;
   if (run) {
-    if ((per_img & 3) == 0 && addv == nullptr) {
+    if (vec4) {
       const int n4 = per_img >> 2;
       const float4* z4 = (const float4*)(z + base);
       const float4* f4 = (const float4*)(gf + base);
@@ -585,8 +585,13 @@ cudaError_t launch_red_update(int n, int per_img, int nblk, const float* z, cons
                               const int* status, double* part_s, double* part_x,
                               cudaStream_t st, const float* addv) {
   dim3 grid(nblk, n);
+  // float4 path only where every image starts on a 16-byte boundary: a caller's
+  // sub-allocation or offset view may be only 4-byte aligned
+  const uintptr_t align = (uintptr_t)z | (uintptr_t)gf | (uintptr_t)gg | (uintptr_t)x |
+                          (uintptr_t)xn;
+  const int vec4 = (per_img & 3) == 0 && addv == nullptr && (align & 15) == 0;
   red_update_kernel<<<grid, 256, 0, st>>>(per_img, z, gf, gg, x, xn, lam, tau, status, part_s,
-                                          part_x, addv);
+                                          part_x, addv, vec4);
   return cudaGetLastError();
 }
 
@@ -649,6 +654,7 @@ __global__ void finalize_kernel(int n, int nblk, SolverDev s, int parity_new, fl
             be = 0.f;
           }
           s.status[b] = st;
+          s.skip[b] = st == IDEQ_IMG_RUNNING ? 0 : 1;  // frozen: later convs skip it
           s.beta_eff[b] = st == IDEQ_IMG_RUNNING ? be : 0.f;
           if (st == IDEQ_IMG_RUNNING) my_run += 1;
         }
@@ -692,6 +698,7 @@ __global__ void solver_init_kernel(int n, SolverDev s, float beta) {
     s.best[b] = INFINITY;
     s.k0[b] = -1;
     s.snap[b] = 0;
+    s.skip[b] = 0;
   }
   if (b == 0) *s.n_running = n;
 }
@@ -705,6 +712,17 @@ __global__ void loop_cond_kernel(cudaGraphConditionalHandle h, const int* n_runn
   const bool running = *n_running > 0;
   if (running && c >= max_bodies) atomicCAS(err, 0, 10);
   cudaGraphSetConditional(h, (running && c < max_bodies) ? 1u : 0u);
+}
+
+// Condition of the IF node inside the solve loop's body: the body's second
+// iteration runs only while an image is running.
+__global__ void if_cond_kernel(cudaGraphConditionalHandle h, const int* n_running) {
+  cudaGraphSetConditional(h, *n_running > 0 ? 1u : 0u);
+}
+
+cudaError_t launch_if_cond(cudaGraphConditionalHandle h, const int* n_running, cudaStream_t st) {
+  if_cond_kernel<<<1, 1, 0, st>>>(h, n_running);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_loop_cond(cudaGraphConditionalHandle h, const int* n_running, int* counter,
@@ -786,11 +804,16 @@ cudaError_t launch_zero_d(long long n, double* p, cudaStream_t st) {
 //   down dgrad   B[q*Cin+ci][co]        = W[co][ci][q]           (pixelwise, D2S)
 //   up fwd       B[q*Cout+co][ci]       = U[ci][co][q]           (pixelwise, D2S)
 //   up dgrad     B[ci][q*Cout+co]       = U[ci][co][q]           (stride-2 gather)
-__device__ __forceinline__ long long wform_src(int form, int cin, int cout, int nn, int kk) {
+// 3x3 forms may store padded channel counts pcin >= cin, pcout >= cout (zero
+// weights on the padded rows and columns); -1 marks a padded entry.
+__device__ __forceinline__ long long wform_src(int form, int cin, int cout, int pcin, int pcout,
+                                               int nn, int kk) {
   switch (form) {
-    case WF_CONV3_FWD: { const int t = kk / cin, ci = kk % cin;
+    case WF_CONV3_FWD: { const int t = kk / pcin, ci = kk % pcin;
+      if (nn >= cout || ci >= cin) return -1;
       return ((long long)nn * cin + ci) * 9 + t; }
-    case WF_CONV3_DGRAD: { const int t = kk / cout, co = kk % cout;
+    case WF_CONV3_DGRAD: { const int t = kk / pcout, co = kk % pcout;
+      if (nn >= cin || co >= cout) return -1;
       return ((long long)co * cin + nn) * 9 + (8 - t); }
     case WF_DOWN_FWD: { const int q = kk / cin, ci = kk % cin;
       return ((long long)nn * cin + ci) * 4 + q; }
@@ -804,6 +827,20 @@ __device__ __forceinline__ long long wform_src(int form, int cin, int cout, int 
 }
 
 void weight_form_dims(int form, int cin, int cout, int* N, int* K) {
+  weight_form_dims_padded(form, cin, cout, cin, cout, N, K);
+}
+
+void weight_form_dims_padded(int form, int cin, int cout, int pcin, int pcout, int* N, int* K) {
+  if (form == WF_CONV3_FWD) {
+    *N = pcout;
+    *K = 9 * pcin;
+    return;
+  }
+  if (form == WF_CONV3_DGRAD) {
+    *N = pcin;
+    *K = 9 * pcout;
+    return;
+  }
   switch (form) {
     case WF_CONV3_FWD: *N = cout; *K = 9 * cin; break;
     case WF_CONV3_DGRAD: *N = cin; *K = 9 * cout; break;
@@ -814,49 +851,64 @@ void weight_form_dims(int form, int cin, int cout, int* N, int* K) {
   }
 }
 
-__global__ void wform_kernel(int form, int cin, int cout, int N, int K,
+__global__ void wform_kernel(int form, int cin, int cout, int pcin, int pcout, int N, int K,
                              const float* __restrict__ src, float* __restrict__ d32,
                              __nv_bfloat16* __restrict__ d16, __half* __restrict__ dh) {
   const long long tot = (long long)N * K;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
        e += (long long)gridDim.x * blockDim.x) {
     const int nn = (int)(e / K), kk = (int)(e % K);
-    const float v = src[wform_src(form, cin, cout, nn, kk)];
+    const long long si = wform_src(form, cin, cout, pcin, pcout, nn, kk);
+    const float v = si < 0 ? 0.f : src[si];
     if (d32) d32[e] = v;
     if (d16) d16[e] = __float2bfloat16_rn(v);
     if (dh) dh[e] = __float2half_rn(v);
   }
 }
 
-__global__ void wunform_kernel(int form, int cin, int cout, int N, int K,
+__global__ void wunform_kernel(int form, int cin, int cout, int pcin, int pcout, int N, int K,
                                const float* __restrict__ g, float scale, float* __restrict__ dst) {
   const long long tot = (long long)N * K;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
        e += (long long)gridDim.x * blockDim.x) {
     const int nn = (int)(e / K), kk = (int)(e % K);
-    dst[wform_src(form, cin, cout, nn, kk)] += scale * g[e];
+    const long long di = wform_src(form, cin, cout, pcin, pcout, nn, kk);
+    if (di >= 0) dst[di] += scale * g[e];
   }
+}
+
+cudaError_t launch_weight_form_padded(int form, int cin, int cout, int pcin, int pcout,
+                                      const float* src, float* dst_f32, void* dst_bf16,
+                                      void* dst_f16, cudaStream_t st) {
+  int N, K;
+  weight_form_dims_padded(form, cin, cout, pcin, pcout, &N, &K);
+  const long long tot = (long long)N * K;
+  const int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
+  wform_kernel<<<blocks, 256, 0, st>>>(form, cin, cout, pcin, pcout, N, K, src, dst_f32,
+                                       (__nv_bfloat16*)dst_bf16, (__half*)dst_f16);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_weight_form(int form, int cin, int cout, const float* src, float* dst_f32,
                                void* dst_bf16, void* dst_f16, cudaStream_t st) {
+  return launch_weight_form_padded(form, cin, cout, cin, cout, src, dst_f32, dst_bf16, dst_f16,
+                                   st);
+}
+
+cudaError_t launch_weight_unform_padded(int form, int cin, int cout, int pcin, int pcout,
+                                        const float* g, float scale, float* dst,
+                                        cudaStream_t st) {
   int N, K;
-  weight_form_dims(form, cin, cout, &N, &K);
+  weight_form_dims_padded(form, cin, cout, pcin, pcout, &N, &K);
   const long long tot = (long long)N * K;
   const int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
-  wform_kernel<<<blocks, 256, 0, st>>>(form, cin, cout, N, K, src, dst_f32,
-                                       (__nv_bfloat16*)dst_bf16, (__half*)dst_f16);
+  wunform_kernel<<<blocks, 256, 0, st>>>(form, cin, cout, pcin, pcout, N, K, g, scale, dst);
   return cudaGetLastError();
 }
 
 cudaError_t launch_weight_unform_scaled(int form, int cin, int cout, const float* g, float scale,
                                         float* dst, cudaStream_t st) {
-  int N, K;
-  weight_form_dims(form, cin, cout, &N, &K);
-  const long long tot = (long long)N * K;
-  const int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
-  wunform_kernel<<<blocks, 256, 0, st>>>(form, cin, cout, N, K, g, scale, dst);
-  return cudaGetLastError();
+  return launch_weight_unform_padded(form, cin, cout, cin, cout, g, scale, dst, st);
 }
 
 cudaError_t launch_weight_unform(int form, int cin, int cout, const float* g, float* dst,

@@ -25,11 +25,13 @@ bool net_param_count(const ideq_net_desc& d, long long* count, std::vector<Layer
                      std::string* err) {
   std::vector<Layer> L;
   long long off = 0;
-  auto add = [&](int kind, int cin, int cout) {
+  auto add = [&](int kind, int cin, int cout, int pcin = -1, int pcout = -1) {
     Layer l;
     l.kind = kind;
     l.cin = cin;
     l.cout = cout;
+    l.pcin = pcin < 0 ? cin : pcin;
+    l.pcout = pcout < 0 ? cout : pcout;
     l.off = off;
     l.numel = (long long)cin * cout * (kind == LK_CONV3 ? 9 : 4);
     l.fwd_form = conv_form(kind, false);
@@ -81,7 +83,11 @@ bool net_param_count(const ideq_net_desc& d, long long* count, std::vector<Layer
       *err = "CNN widths[0] and widths[depth] must equal in_ch";
       return false;
     }
-    for (int i = 0; i < d.depth; ++i) add(LK_CONV3, d.widths[i], d.widths[i + 1]);
+    // hidden widths stored as multiples of 32 channels (the image sides as they are)
+    auto pad = [](int c) { return (c + 31) / 32 * 32; };
+    for (int i = 0; i < d.depth; ++i)
+      add(LK_CONV3, d.widths[i], d.widths[i + 1], i == 0 ? d.widths[i] : pad(d.widths[i]),
+          i == d.depth - 1 ? d.widths[i + 1] : pad(d.widths[i + 1]));
   } else {
     *err = "unknown network kind";
     return false;
@@ -113,11 +119,11 @@ bool NetWeights::build(const ideq_net_desc& d, std::string* err) {
     // 16-bit forms keep at least 16 rows (zero rows past N): the tensor-core conv
     // that writes c <= 16 image channels runs a 16-wide N tile
     int Nf, Kf, Nd, Kd;
-    weight_form_dims(l.fwd_form, l.cin, l.cout, &Nf, &Kf);
-    weight_form_dims(l.dg_form, l.cin, l.cout, &Nd, &Kd);
+    weight_form_dims_padded(l.fwd_form, l.cin, l.cout, l.pcin, l.pcout, &Nf, &Kf);
+    weight_form_dims_padded(l.dg_form, l.cin, l.cout, l.pcin, l.pcout, &Nd, &Kd);
     const size_t f16n = (size_t)std::max(Nf, 16) * Kf, d16n = (size_t)std::max(Nd, 16) * Kd;
-    l.fwd32 = (float*)al(l.numel * 4);
-    l.dg32 = (float*)al(l.numel * 4);
+    l.fwd32 = (float*)al((size_t)Nf * Kf * 4);
+    l.dg32 = (float*)al((size_t)Nd * Kd * 4);
     l.fwd16 = (__nv_bfloat16*)al(f16n * 2);
     l.dg16 = (__nv_bfloat16*)al(d16n * 2);
     l.fwdh = (__half*)al(f16n * 2);
@@ -158,10 +164,11 @@ bool NetWeights::build(const ideq_net_desc& d, std::string* err) {
 
 cudaError_t NetWeights::reform(cudaStream_t st) {
   for (auto& l : layers) {
-    cudaError_t e = launch_weight_form(l.fwd_form, l.cin, l.cout, master + l.off, l.fwd32,
-                                       l.fwd16, l.fwdh, st);
+    cudaError_t e = launch_weight_form_padded(l.fwd_form, l.cin, l.cout, l.pcin, l.pcout,
+                                              master + l.off, l.fwd32, l.fwd16, l.fwdh, st);
     if (e != cudaSuccess) return e;
-    e = launch_weight_form(l.dg_form, l.cin, l.cout, master + l.off, l.dg32, l.dg16, l.dgh, st);
+    e = launch_weight_form_padded(l.dg_form, l.cin, l.cout, l.pcin, l.pcout, master + l.off,
+                                  l.dg32, l.dg16, l.dgh, st);
     if (e != cudaSuccess) return e;
     int N, K;
     if (l.fwd8) {
@@ -241,6 +248,7 @@ struct Builder {
     a.aux1 = aux1;
     a.aux2 = aux2;
     a.sumsq = sumsq;
+    a.skip = P->skip;
     const int prec = P->prec;
     const int adt = prec == IDEQ_FP32
                         ? DT_F32
@@ -303,8 +311,9 @@ struct Builder {
 }  // namespace
 
 bool NetPlan::build(NetWeights* wts, int n_, int H_, int W_, int prec_, double* gsum_,
-                    std::string* err) {
+                    std::string* err, const int* skip_) {
   w = wts;
+  skip = skip_;
   n = n_;
   c = wts->desc.in_ch;
   H = H_;
@@ -329,8 +338,8 @@ bool NetPlan::build(NetWeights* wts, int n_, int H_, int W_, int prec_, double* 
     const int D = d.depth;
     std::vector<void*> a(D), s(D);
     for (int i = 0; i + 1 < D; ++i) {
-      a[i] = B.act(H, W, d.widths[i + 1]);
-      s[i] = B.act(H, W, d.widths[i + 1]);
+      a[i] = B.act(H, W, Ls[i].pcout);
+      s[i] = B.act(H, W, Ls[i].pcout);
     }
     // forward
     for (int i = 0; i < D; ++i) {
@@ -338,24 +347,24 @@ bool NetPlan::build(NetWeights* wts, int n_, int H_, int W_, int prec_, double* 
       const bool first = i == 0, last = i == D - 1;
       const void* in = first ? (const void*)z : a[i - 1];
       if (last)
-        B.conv(fwd, L, false, CM_CONV3, OM_IDENT, H, W, L.cin, L.cout, in, r, EP_AXPY_NCHW, z,
+        B.conv(fwd, L, false, CM_CONV3, OM_IDENT, H, W, L.pcin, L.pcout, in, r, EP_AXPY_NCHW, z,
                nullptr, first, true, -1.f, gsum);
       else
-        B.conv(fwd, L, false, CM_CONV3, OM_IDENT, H, W, L.cin, L.cout, in, a[i], EP_ACT, nullptr,
-               s[i], first);
+        B.conv(fwd, L, false, CM_CONV3, OM_IDENT, H, W, L.pcin, L.pcout, in, a[i], EP_ACT,
+               nullptr, s[i], first);
     }
     // reverse: d_h(i-1) = s(i-1) . conv_i^T(d_h(i)); the first conv's transpose forms grad
     std::vector<void*> dh(D);
-    for (int i = 0; i + 1 < D; ++i) dh[i] = B.act(H, W, d.widths[i + 1]);
+    for (int i = 0; i + 1 < D; ++i) dh[i] = B.act(H, W, Ls[i].pcout);
     for (int i = D - 1; i >= 0; --i) {
       const Layer& L = Ls[i];
       const bool last = i == D - 1, first = i == 0;
       const void* in = last ? (const void*)r : dh[i];
       if (first)
-        B.conv(vjp, L, true, CM_CONV3, OM_IDENT, H, W, L.cout, L.cin, in, grad, EP_AXPY_NCHW, r,
-               nullptr, last, true, -1.f, nullptr);
+        B.conv(vjp, L, true, CM_CONV3, OM_IDENT, H, W, L.pcout, L.pcin, in, grad, EP_AXPY_NCHW,
+               r, nullptr, last, true, -1.f, nullptr);
       else
-        B.conv(vjp, L, true, CM_CONV3, OM_IDENT, H, W, L.cout, L.cin, in, dh[i - 1], EP_MUL,
+        B.conv(vjp, L, true, CM_CONV3, OM_IDENT, H, W, L.pcout, L.pcin, in, dh[i - 1], EP_MUL,
                s[i - 1], nullptr, last, false);
     }
   } else {

@@ -15,6 +15,10 @@ enum LayerKind { LK_CONV3 = 0, LK_DOWN = 1, LK_UP = 2 };
 
 struct Layer {
   int kind, cin, cout;  // cin/cout of the layer as written in PyTorch
+  // stored channel counts of its input and output activations: cin/cout, or for a
+  // plain CNN's hidden layers rounded up to a multiple of 32 (zero weights on the
+  // padded channels) so that they fit the tensor-core conv's 32-channel rows
+  int pcin, pcout;
   long long off;        // offset in the flat weight vector
   long long numel;
   int fwd_form, dg_form;
@@ -76,11 +80,13 @@ struct NetPlan {
   float* r = nullptr;
   float* grad = nullptr;
   double* gsum = nullptr;  // per-image 1/2||r||^2, accumulated by the forward pass
+  const int* skip = nullptr;  // per-image skip flags of the solver (nullable)
   std::vector<Step> fwd, vjp;
   std::vector<void*> allocs;
   double fwd_flops = 0, vjp_flops = 0;
   ~NetPlan();
-  bool build(NetWeights* w, int n, int H, int W, int prec, double* gsum, std::string* err);
+  bool build(NetWeights* w, int n, int H, int W, int prec, double* gsum, std::string* err,
+             const int* skip = nullptr);
   void* alloc(size_t bytes);
 };
 

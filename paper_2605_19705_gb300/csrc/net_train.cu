@@ -163,7 +163,7 @@ bool TrainPlan::build(NetWeights* wts, int n_, int H_, int W_, int prec_, double
     // ta/tc: t-chain raw / scaled cotangent, pa/pc: p-chain raw / scaled cotangent
     std::vector<void*> a(D), s(D), ad(D), hd(D), ta(D), tcv(D), pa(D), pcv(D);
     for (int i = 0; i + 1 < D; ++i) {
-      const int C = d.widths[i + 1];
+      const int C = Ls[i].pcout;  // stored (padded) channels
       a[i] = B.act(H, W, C);
       s[i] = B.act(H, W, C);
       ad[i] = B.act(H, W, C);
@@ -180,15 +180,15 @@ bool TrainPlan::build(NetWeights* wts, int n_, int H_, int W_, int prec_, double
       const void* in = first ? (const void*)z : a[i - 1];
       const void* tin = first ? (const void*)zd : ad[i - 1];
       if (last) {
-        fsteps[i] = B.make(L, false, CM_CONV3, OM_IDENT, H, W, L.cin, L.cout, in, out_img,
+        fsteps[i] = B.make(L, false, CM_CONV3, OM_IDENT, H, W, L.pcin, L.pcout, in, out_img,
                            EP_AXPY_NCHW, z, nullptr, first, true, warm ? 1.f : -1.f,
                            warm ? nullptr : gsum);
-        jvp.push_back(B.make(L, false, CM_CONV3, OM_IDENT, H, W, L.cin, L.cout, tin, rd,
+        jvp.push_back(B.make(L, false, CM_CONV3, OM_IDENT, H, W, L.pcin, L.pcout, tin, rd,
                              EP_AXPY_NCHW, zd, nullptr, first, true, -1.f, nullptr));
       } else {
-        fsteps[i] = B.make(L, false, CM_CONV3, OM_IDENT, H, W, L.cin, L.cout, in, a[i], EP_ACT,
+        fsteps[i] = B.make(L, false, CM_CONV3, OM_IDENT, H, W, L.pcin, L.pcout, in, a[i], EP_ACT,
                            nullptr, s[i], first);
-        jvp.push_back(B.make(L, false, CM_CONV3, OM_IDENT, H, W, L.cin, L.cout, tin, ad[i],
+        jvp.push_back(B.make(L, false, CM_CONV3, OM_IDENT, H, W, L.pcin, L.pcout, tin, ad[i],
                              EP_MUL_KEEP, s[i], hd[i], first));
       }
       fwd.push_back(fsteps[i]);
@@ -204,14 +204,14 @@ bool TrainPlan::build(NetWeights* wts, int n_, int H_, int W_, int prec_, double
       if (first && warm) {
         // the warm start needs no input gradient: the chain ends at layer 1
       } else if (first) {
-        tchain.push_back(B.make(L, true, CM_CONV3, OM_IDENT, H, W, L.cout, L.cin, tin, grad,
+        tchain.push_back(B.make(L, true, CM_CONV3, OM_IDENT, H, W, L.pcout, L.pcin, tin, grad,
                                 EP_AXPY_NCHW, r, nullptr, last, true, -1.f, nullptr));
-        pchain.push_back(B.make(L, true, CM_CONV3, OM_IDENT, H, W, L.cout, L.cin, pin, hvp,
+        pchain.push_back(B.make(L, true, CM_CONV3, OM_IDENT, H, W, L.pcout, L.pcin, pin, hvp,
                                 EP_AXPY_NCHW, rd, nullptr, last, true, -1.f, nullptr));
       } else {
-        tchain.push_back(B.make(L, true, CM_CONV3, OM_IDENT, H, W, L.cout, L.cin, tin, tcv[i - 1],
+        tchain.push_back(B.make(L, true, CM_CONV3, OM_IDENT, H, W, L.pcout, L.pcin, tin, tcv[i - 1],
                                 EP_MUL_KEEP, s[i - 1], ta[i - 1], last, false));
-        pchain.push_back(B.make(L, true, CM_CONV3, OM_IDENT, H, W, L.cout, L.cin, pin, pcv[i - 1],
+        pchain.push_back(B.make(L, true, CM_CONV3, OM_IDENT, H, W, L.pcout, L.pcin, pin, pcv[i - 1],
                                 EP_DUAL, s[i - 1], nullptr, last, false, -1.f, nullptr, hd[i - 1],
                                 ta[i - 1]));
       }
@@ -409,7 +409,8 @@ cudaError_t TrainPlan::run_wgrad(float* dst, float scale, bool dual, cudaStream_
       if (e != cudaSuccess) return e;
     }
     // accumulate the [N][K] forward-form gradient into the PyTorch layout
-    e = launch_weight_unform_scaled(L.fwd_form, L.cin, L.cout, wg_acc, scale, dst + L.off, st);
+    e = launch_weight_unform_padded(L.fwd_form, L.cin, L.cout, L.pcin, L.pcout, wg_acc, scale,
+                                    dst + L.off, st);
     if (e != cudaSuccess) return e;
     if (launches) *launches += dual ? 5 : 3;
   }

@@ -172,10 +172,18 @@ def test_solve_c0_restart_and_stopping_fp32(B_, tol):
     xo, infos = _oracle_solve(cfg, net, ops, ys, B=B_, tol=tol, max_iter=400)
     xg, info, st = _gpu_solve(cfg, wl, ys, B().IDEQ_FP32, B=B_, tol=tol, max_iter=400)
     for i in range(2):
-        assert abs(int(info.iters[i]) - infos[i]["iters"]) <= 1
+        it = int(info.iters[i])
+        assert abs(it - infos[i]["iters"]) <= 1
         assert int(info.restarts[i]) == infos[i]["restarts"]
         assert int(info.status[i]) == infos[i]["status"]
-    assert rel(xg, xo) < 1e-5 or all(int(info.iters[i]) != infos[i]["iters"] for i in range(2))
+        # the FP32 iterate against the oracle run for exactly the GPU's number of
+        # updates (same restarts; the stopping test may flip by one update between
+        # FP32 and FP64, so the oracle's own stopping iterate is not the reference)
+        xo_i, inf_i = solver.solve_image(net, ops[i], ys[i].astype(np.float64),
+                                         ops[i].AT(ys[i].astype(np.float64)), cfg["lam"],
+                                         cfg["tau"], cfg["beta"], B_, 0.0, it)
+        assert inf_i["restarts"] == int(info.restarts[i])
+        assert rel(xg[i], xo_i) < 1e-5, (i, rel(xg[i], xo_i))
     if B_ < math.inf:
         assert min(int(v) for v in info.restarts.cpu()) >= 1
 
@@ -505,3 +513,144 @@ def test_step_at_full_size_sampled_images(prec, tol):
         # (unit roundoff u = 2^-11 f16, 2^-8 bf16) move g by up to ~2u relative
         e_tol = {"fp32": 1e-4, "bf16": 2 * 2.0 ** -8, "fp16": 2 * 2.0 ** -11}[prec]
         assert abs(float(info.energy[i]) - (fval + cfg["lam"] * gval)) < e_tol * (fval + cfg["lam"] * gval)
+
+
+# ---------------------------------------------------------------- saturation model in a solve
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("fp16", 2e-3)])
+def test_saturation_solve_matches_oracle(prec, tol):
+    """The nonlinear forward model A(x) = tanh(2 k*x)/tanh 2 (15x15 Gaussian k) inside
+    a solve: 30 inertial updates of two RGB 64^2 images, data gradient J_A(z)^T(A(z) - y)
+    at every extrapolated point, against the oracle (FP32 1e-5, FP16 convs 2e-3)."""
+    cfg, wl, net, ops, ys = setup("C4", n=2, h=64, w=64)
+    xo, infos = _oracle_solve(cfg, net, ops, ys, tol=0.0, max_iter=30)
+    xg, info, st = _gpu_solve(cfg, wl, ys, PREC[prec](), tol=0.0, max_iter=30)
+    assert list(info.iters.cpu().numpy()) == [30, 30]
+    assert rel(xg, xo) < tol, rel(xg, xo)
+    for i in range(2):
+        assert abs(float(info.energy[i]) - infos[i]["energy"]) < 4 * tol * abs(infos[i]["energy"])
+
+
+# ---------------------------------------------------------------- full-size solves
+
+
+def _c1a_golden():
+    import os
+    p = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "c1a_oracle_samples.npz")
+    return np.load(p)
+
+
+@pytest.mark.parametrize("prec,tol,it_slack", [("fp32", 1e-5, 1), ("fp16", 2e-3, 3)])
+def test_full_size_c1a_solve_matches_oracle(prec, tol, it_slack):
+    """Images 0 and 1 of the 8 x RGB 256^2 motion-blur workload solved to the 1e-4
+    relative step (App. D.1.3) in the launch configuration of the benchmark (device-
+    driven solve graph, spectral data step, halo/streamed tcgen05 convs for FP16).
+    The stored FP64 oracle trajectory (tests/golden/oracle_c1a_samples.py) gives the
+    iteration count and, at the GPU's own count, x^k at 512 sampled pixels and the
+    PSNR of the whole image."""
+    g = _c1a_golden()
+    cfg, wl, net, ops, ys = setup("C1a", n=2)
+    xg, info, st = _gpu_solve(cfg, wl, ys, PREC[prec]())
+    idx, ks = g["idx"], list(g["k"])
+    for i in range(2):
+        it = int(info.iters[i])
+        assert int(info.status[i]) == solver.CONVERGED
+        assert abs(it - int(g["stop"][i])) <= it_slack, (i, it, int(g["stop"][i]))
+        j = ks.index(it)
+        xs = xg[i].ravel()[idx]
+        assert rel(xs, g["samples"][i, j]) < tol, (i, rel(xs, g["samples"][i, j]))
+        p_gpu = solver.psnr(xg[i], wl["x_true"][i])
+        assert abs(p_gpu - float(g["psnr"][i, j])) < 0.05
+        # and against the oracle's own stopping iterate
+        j0 = ks.index(int(g["stop"][i]))
+        assert abs(p_gpu - float(g["psnr"][i, j0])) < 0.05
+
+
+# ---------------------------------------------------------------- failure detection
+
+
+def _solve_status(ctx, op, y, params, info):
+    b = B()
+    try:
+        x, st = b.ideq_solve(ctx, op, y, params, info=info, allow_maxiter=True)
+    except b.IdeqError as e:
+        return None, e.status
+    return x, st
+
+
+@pytest.mark.parametrize("name,prec", [("C0", "fp32"), ("C1a", "fp16")])
+def test_nan_observation_marks_only_that_image_diverged(name, prec):
+    """A NaN in image 0's observation makes its first step non-finite: the solve
+    returns IDEQ_DIVERGED with image 0 DIVERGED and image 1 CONVERGED, image 1's
+    restoration is bit-identical to the one from a clean batch (images never
+    interact), and the context solves normally afterwards."""
+    cfg, wl, net, ops, ys = setup(name, n=2, h=48, w=64)
+    b = B()
+    op = op_for(cfg, wl)
+    params = b.make_params(cfg["lam"], cfg["tau"], cfg["beta"], tol=1e-4, max_iter=400)
+    clean = torch.tensor(ys, device="cuda")
+    bad = clean.clone()
+    bad[0, 0, 5, 7] = float("nan")
+    ctx = ctx_for(cfg, wl, PREC[prec]())
+    info = b.InfoBuffers(2)
+    out = torch.zeros_like(clean)
+    st = b._lib.ideq_solve(ctx.h, ctypes_ref(op), b._shape(bad), bad.data_ptr(), None,
+                           out.data_ptr(), ctypes_ref(params), ctypes_ref(info.s))
+    assert st == b.IDEQ_DIVERGED
+    assert int(info.status[0]) == b.IDEQ_IMG_DIVERGED
+    assert int(info.status[1]) == b.IDEQ_IMG_CONVERGED
+    assert int(info.iters[0]) == 1  # frozen at its first (non-finite) update
+    ref_ctx = ctx_for(cfg, wl, PREC[prec]())
+    info2 = b.InfoBuffers(2)
+    x_ref, st2 = b.ideq_solve(ref_ctx, op, clean, params, info=info2)
+    assert torch.equal(out[1], x_ref[1])
+    assert int(info.iters[1]) == int(info2.iters[1])
+    # the context that saw the failure still solves the clean batch identically
+    x_again, st3 = b.ideq_solve(ctx, op, clean, params, info=info)
+    assert torch.equal(x_again, x_ref)
+
+
+def test_step_size_far_above_1_over_L_diverges_every_image():
+    """tau = 200 (about 200 x 1/L): the iterates grow geometrically until a step
+    norm overflows; every image is reported DIVERGED before max_iter, the solve
+    returns IDEQ_DIVERGED, and the context then solves a valid problem normally."""
+    cfg, wl, net, ops, ys = setup("C0", n=2, h=40, w=48)
+    b = B()
+    op = op_for(cfg, wl)
+    y = torch.tensor(ys, device="cuda")
+    ctx = ctx_for(cfg, wl, b.IDEQ_FP32)
+    info = b.InfoBuffers(2)
+    x, st = _solve_status(ctx, op, y, b.make_params(cfg["lam"], 200.0, cfg["beta"], tol=1e-4,
+                                                    max_iter=400), info)
+    assert st == b.IDEQ_DIVERGED
+    assert [int(v) for v in info.status.cpu()] == [b.IDEQ_IMG_DIVERGED] * 2
+    assert max(int(v) for v in info.iters.cpu()) < 400
+    good = b.make_params(cfg["lam"], cfg["tau"], cfg["beta"], max_iter=20)
+    x1, _ = b.ideq_solve(ctx, op, y, good, allow_maxiter=True)
+    x2, _ = b.ideq_solve(ctx_for(cfg, wl, b.IDEQ_FP32), op, y, good, allow_maxiter=True)
+    assert torch.equal(x1, x2)
+
+
+# ---------------------------------------------------------------- solve-graph cache
+
+
+def test_graph_cache_tracks_rician_sigma():
+    """Two device-graph Rician solves on one context and one y buffer that differ
+    only in the noise level sigma of the data term: each matches the host-driven
+    loop bit for bit (the captured graph must not be reused across sigmas)."""
+    cfg, wl, net, ops, ys = setup("C6", n=2, h=64, w=64)
+    b = B()
+    y = torch.tensor(ys, device="cuda")
+    ctx_g = ctx_for(cfg, wl, b.IDEQ_FP32)
+    ctx_h = ctx_for(cfg, wl, b.IDEQ_FP32)
+    b.ideq_prof_enable(ctx_h, True)  # per-launch events keep this one on the host loop
+    params = b.make_params(cfg["lam"], 0.002, cfg["beta"], max_iter=12)  # tau < 0.9 sigma^2
+    for sigma in (0.1, 0.05):
+        op = b.make_operator(b.IDEQ_OP_RICIAN, sigma=sigma)
+        xg, _ = b.ideq_solve(ctx_g, op, y, params, allow_maxiter=True)
+        assert b.ideq_solve_graphed(ctx_g)
+        xh, _ = b.ideq_solve(ctx_h, op, y, params, allow_maxiter=True)
+        assert not b.ideq_solve_graphed(ctx_h)
+        torch.cuda.synchronize()
+        assert torch.equal(xg, xh), sigma

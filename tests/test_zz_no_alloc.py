@@ -59,3 +59,54 @@ def test_noalloc_update_matches_step_on_two_calls():
         assert torch.allclose(x_sq, ref_x_sq, rtol=1e-9), call
         # advance to the next step's state
         xp, x = x, xk
+
+
+def test_noalloc_nullable_outputs_size_limit_and_unaligned_views():
+    """The step norms are optional; a request larger than the static array is an
+    argument error that leaves x_new untouched; and tensors that start 4 bytes past a
+    16-byte boundary (a sub-allocation or an offset view of a caller's buffer) take
+    the scalar path and give the same update as aligned ones."""
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2605_19705_gb300 import build
+    build.build()
+    from paper_2605_19705_gb300 import binding as B
+
+    g = torch.Generator(device="cpu").manual_seed(5)
+    shape = (3, 3, 40, 56)
+    numel = 3 * 3 * 40 * 56
+    z, gf, gg, x = (torch.randn(shape, generator=g).cuda() for _ in range(4))
+    lam, tau = 0.1, 0.75
+    ref = torch.empty_like(x)
+    s_ref = torch.zeros(3, dtype=torch.float64, device="cuda")
+    x_ref = torch.zeros(3, dtype=torch.float64, device="cuda")
+    B.ideq_red_update_noalloc(z, gf, gg, x, ref, lam, tau, s_ref, x_ref)
+    # no norms requested
+    out = torch.empty_like(x)
+    B.ideq_red_update_noalloc(z, gf, gg, x, out, lam, tau, None, None)
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    # unaligned: every tensor viewed one float into a larger buffer
+    def shifted(t):
+        buf = torch.empty(numel + 1, device="cuda")
+        v = buf[1:].view(shape)
+        v.copy_(t)
+        assert v.data_ptr() % 16 == 4
+        return v
+    zu, fu, gu, xu = shifted(z), shifted(gf), shifted(gg), shifted(x)
+    ou = shifted(torch.zeros_like(x))
+    s_u = torch.zeros(3, dtype=torch.float64, device="cuda")
+    x_u = torch.zeros(3, dtype=torch.float64, device="cuda")
+    B.ideq_red_update_noalloc(zu, fu, gu, xu, ou, lam, tau, s_u, x_u)
+    torch.cuda.synchronize()
+    assert torch.allclose(ou, ref, rtol=1e-6, atol=1e-6)
+    assert torch.allclose(s_u, s_ref, rtol=1e-9) and torch.allclose(x_u, x_ref, rtol=1e-9)
+    # 2 * n * blocks > 65536 partial sums: refused before any launch
+    n_big = 32769  # one block per one-value image
+    t = torch.zeros(n_big, 1, 1, 1, device="cuda")
+    sentinel = torch.full_like(t, 7.0)
+    with pytest.raises(B.IdeqError) as e:
+        B.ideq_red_update_noalloc(t, t, t, t, sentinel, lam, tau)
+    assert e.value.status == B.IDEQ_ERR_ARG
+    torch.cuda.synchronize()
+    assert bool((sentinel == 7.0).all())
