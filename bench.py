@@ -39,7 +39,15 @@ WORKLOADS = {
           "k-space sigma 0.01, 2-channel U-Net 32/64/128/256, lambda 0.1, tau 0.75, beta 0.8, tol 1e-4",
     "C6": "C6: 4 x grey 256x256 Rician denoising, sigma 0.1, U-Net 32/64/128/256, "
           "lambda 0.1, tau 0.009, beta 0.8, tol 1e-4",
+    "C4": "C4: 32 x RGB 256x256, A(x) = tanh(2 k*x)/tanh 2 with 15x15 Gaussian k (sigma 2), "
+          "sigma 0.01, U-Net 64/128/256/512, lambda 0.1, tau 0.2, beta 0.8, tol 1e-4; "
+          "warm start 3-48-48-48-48-48-3 ReLU CNN trained on FP16-solver equilibria",
 }
+WORKLOADS["C3"] = ("C3: DEQ training step on 16 x RGB 128x128 patches, 9x9 Gaussian blur "
+                   "sigma U[0.5,3], noise U[0.005,0.05], U-Net 32/64/128/256 (4.25M params); "
+                   "forward solve to 1e-3, implicit adjoint to 1e-3, one Adam step")
+WARM_TRAIN_IMAGES = 512   # held-out equilibria the warm start is trained on
+WARM_TRAIN_STEPS = 600    # Adam steps (batch 8, lr 1e-3)
 WORKLOAD = WORKLOADS["C1a"]
 CONV_REPS = 20  # repetitions of the conv launch sequence in the roofline timing
 
@@ -469,10 +477,228 @@ def run_reference(args):
     print(json.dumps(res), flush=True)
 
 
+def run_warm(args):
+    """C4: the learned warm start on the saturation workload.  Trains W_phi with the
+    library's own kernels on equilibria that the plain FP16 solver produces for
+    WARM_TRAIN_IMAGES held-out images (seeds disjoint from the benchmark batch),
+    then solves the 32-image benchmark batch from A^T y (plain) and from the warm
+    start, both to the same relative step 1e-4, and reports restorations/s,
+    iterations and PSNR of both (and of the plain FP32 form)."""
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_2605_19705_gb300 import build as pbuild
+    pbuild.build()
+    from paper_2605_19705_gb300 import binding as B
+    from paper_2605_19705_gb300 import warmstart as W
+    from synth import get_config, workload
+    cfg, wl, _ = load_workload(name="C4")
+    n = cfg["n"]
+    dev = torch.device("cuda", local)
+    desc = B.net_desc(cfg["net"], cfg["c"])
+    ctx = B.Context(desc, torch.tensor(wl["weights"], device=dev), B.IDEQ_FP16)
+    wdesc = B.net_desc(cfg["warm"], cfg["c"])
+    W.warm_set(ctx, wdesc, torch.tensor(wl["warm_weights"], device=dev))
+    params = B.make_params(cfg["lam"], cfg["tau"], cfg["beta"], cfg["B"], cfg["tol"],
+                           cfg["max_iter"])
+    # ---- training set: equilibria of the plain FP16 solver on held-out images
+    t0 = time.perf_counter()
+    atys, xbars, it_tr = [], [], []
+    for b in range(WARM_TRAIN_IMAGES // n):
+        tc = get_config("C4", seeds=dict(img=20000 + n * b, noise=21000 + n * b, weights=2001,
+                                        kernel=0, mask=0, warm=2004))
+        twl = workload(tc)
+        op_b = B.make_operator(B.IDEQ_OP_SATBLUR, torch.tensor(twl["kern"], device=dev),
+                               sat_gain=tc["sat_gain"])
+        y_b = B.ideq_apply_A(ctx, op_b, torch.tensor(twl["x_true"], device=dev)) + \
+            torch.tensor(twl["noise"], device=dev)
+        info_b = B.InfoBuffers(n, dev)
+        x_b, _ = B.ideq_solve(ctx, op_b, y_b, params, info=info_b)
+        atys.append(B.ideq_apply_AT(ctx, op_b, y_b))
+        xbars.append(x_b.clone())
+        it_tr.append(info_b.iters.float().mean().item())
+    atys, xbars = torch.cat(atys), torch.cat(xbars)
+    torch.cuda.synchronize()
+    t_eq = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    hist = W.train(ctx, atys, xbars, steps=WARM_TRAIN_STEPS, lr=1e-3, batch=8)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del atys, xbars
+    # ---- the benchmark batch: plain vs warm start at equal residual
+    x_true = torch.tensor(wl["x_true"], device=dev)
+    op = B.make_operator(B.IDEQ_OP_SATBLUR, torch.tensor(wl["kern"], device=dev),
+                         sat_gain=cfg["sat_gain"])
+    y = B.ideq_apply_A(ctx, op, x_true) + torch.tensor(wl["noise"], device=dev)
+    st = torch.cuda.current_stream()
+
+    def psnr(x):
+        mse = ((x.double() - x_true.double()) ** 2).mean(dim=(1, 2, 3))
+        return (10 * torch.log10(1.0 / mse)).cpu().numpy()
+
+    res = {}
+    for name, init in (("plain", B.IDEQ_INIT_ATY), ("warm", B.IDEQ_INIT_WARM)):
+        p = B.make_params(cfg["lam"], cfg["tau"], cfg["beta"], cfg["B"], cfg["tol"],
+                          cfg["max_iter"], init)
+        info = B.InfoBuffers(n, dev)
+        out = torch.empty_like(y)
+        for _ in range(args.warmup):
+            B.ideq_solve(ctx, op, y, p, out=out, info=info)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        its = []
+        e0.record(st)
+        for _ in range(args.steps):
+            B.ideq_solve(ctx, op, y, p, out=out, info=info)
+            its.append(info.iters.clone())
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        it = torch.stack(its).float()
+        res[name] = {"value": n / (ms / 1e3), "unit": "restorations/s", "ms_per_solve": ms,
+                     "mean_iters": it.mean().item(), "max_iters": int(it.max().item()),
+                     "max_rel_res": float(info.rel_res.max().item()),
+                     "psnr_db_mean": float(psnr(out).mean()), "x": out.clone()}
+    aty = B.ideq_apply_AT(ctx, op, y)
+    x0w = W.warm_forward(ctx, aty)
+    xp = res["plain"]["x"]
+    e_aty = float((aty - xp).norm() / xp.norm())
+    e_warm = float((x0w - xp).norm() / xp.norm())
+    dpsnr = float(np.max(np.abs(psnr(res["warm"]["x"]) - psnr(xp))))
+    # plain FP32 form, one solve
+    ctx32 = B.Context(desc, torch.tensor(wl["weights"], device=dev), B.IDEQ_FP32)
+    info32 = B.InfoBuffers(n, dev)
+    out32 = torch.empty_like(y)
+    B.ideq_solve(ctx32, op, y, params, out=out32, info=info32)
+    torch.cuda.synchronize()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(st)
+    B.ideq_solve(ctx32, op, y, params, out=out32, info=info32)
+    a1.record(st)
+    torch.cuda.synchronize()
+    pms = a0.elapsed_time(a1)
+    for r in res.values():
+        r.pop("x")
+    line = {
+        "metric": "256² RGB restorations/s at equal residual, FP16 + learned warm start vs "
+                  "FP16 from A^T y vs plain FP32",
+        "value": res["warm"]["value"], "unit": "restorations/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["warm"]["ms_per_solve"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16",
+        "data": "synthetic (seeded images, noise; random-init U-Net and warm-start weights)",
+        "config": {"workload": WORKLOADS["C4"], "batch_per_gpu": n, "image": "3x256x256"},
+        "warm_start": {"train_images": WARM_TRAIN_IMAGES, "train_steps": WARM_TRAIN_STEPS,
+                       "train_loss_first_last": [hist[0], hist[-1]],
+                       "train_mean_iters": float(np.mean(it_tr)),
+                       "seconds_equilibria": t_eq, "seconds_training": t_train,
+                       "x0_rel_err_aty": e_aty, "x0_rel_err_warm": e_warm,
+                       "iterations_saved_mean": res["plain"]["mean_iters"] - res["warm"]["mean_iters"],
+                       "max_abs_psnr_delta_db": dpsnr},
+        "fp16_plain": res["plain"], "fp16_warm": res["warm"],
+        "plain_fp32": {"value": n / (pms / 1e3), "unit": "restorations/s", "ms_per_solve": pms,
+                       "mean_iters": float(info32.iters.float().mean().item()),
+                       "psnr_db_mean": float(psnr(out32).mean())},
+        "speedup_vs_plain_fp32": res["warm"]["value"] / (n / (pms / 1e3)),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_train(args):
+    """C3: DEQ training steps of the regulariser (App. D.1.2-D.1.3) through
+    ideq_train_step -- forward solve to 1e-3, MSE loss against the ground truth,
+    implicit adjoint solve to 1e-3, parameter gradient (tcgen05 weight gradients),
+    one Adam step -- timed with CUDA events; then the weight-gradient pass alone
+    (ideq_time_wgrad) for its roofline."""
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_2605_19705_gb300 import build as pbuild
+    pbuild.build()
+    from paper_2605_19705_gb300 import binding as B
+    cfg, wl, _ = load_workload(name="C3")
+    n = cfg["n"]
+    dev = torch.device("cuda", local)
+    ctx = B.Context(B.net_desc(cfg["net"], cfg["c"]), torch.tensor(wl["weights"], device=dev),
+                    B.IDEQ_FP16)
+    op = B.make_operator(B.IDEQ_OP_BLUR, torch.tensor(wl["kern"], device=dev))
+    x_true = torch.tensor(wl["x_true"], device=dev)
+    y = B.ideq_apply_A(ctx, op, x_true) + torch.tensor(wl["noise"], device=dev)
+    params = B.make_params(cfg["lam"], cfg["tau"], cfg["beta"], cfg["B"], cfg["tol"],
+                           cfg["max_iter"])
+    adj = B.make_adj(B.IDEQ_ADJ_IMPLICIT, cfg["adj_tol"], 3000, 0.0)
+    lr = 1e-5
+    info = B.InfoBuffers(n, dev)
+    binfo_iters = []
+    x = torch.empty_like(y)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    for _ in range(args.warmup):
+        B.ideq_train_step(ctx, op, y, x_true, params, adj, lr, x_out=x, loss=loss, info=info)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fw_iters, losses = [], []
+    e0.record(st)
+    for _ in range(args.steps):
+        B.ideq_train_step(ctx, op, y, x_true, params, adj, lr, x_out=x, loss=loss, info=info)
+        fw_iters.append(info.iters.clone())
+        losses.append(loss.clone())
+    e1.record(st)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    # the backward alone (adjoint iterations per image from its info) and the
+    # weight-gradient pass alone
+    binfo = B.InfoBuffers(n, dev)
+    v = (2.0 * (x - x_true) / x.numel()).contiguous()
+    g = torch.zeros(wl["weights"].size, device=dev)
+    dl = torch.zeros(1, device=dev)
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b0.record(st)
+    B.ideq_solve_backward(ctx, op, y, x, v, params, adj, g, dl, binfo)
+    b1.record(st)
+    torch.cuda.synchronize()
+    bwd_ms = b0.elapsed_time(b1)
+    wg_ms, wg_flops, wg_tc = B.ideq_time_wgrad(ctx, 10)
+    peaks, src = measured_peaks()
+    peak = float(peaks.get("bf16_tflops", peaks.get("bf16_tflops_sustained")))
+    wg_tflops = wg_flops / (wg_ms / 1e3) / 1e12
+    line = {
+        "metric": "DEQ training steps/s (forward solve + implicit adjoint + Adam), 16 x RGB 128^2",
+        "value": 1e3 / ms, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f16",
+        "data": "synthetic (seeded patches, kernels, noise; random-init U-Net weights)",
+        "config": {"workload": WORKLOADS["C3"], "batch_per_gpu": n, "image": "3x128x128",
+                   "lr": lr, "adjoint": "implicit, u <- J_R^T u + v, tol 1e-3"},
+        "images_per_s": n * 1e3 / ms,
+        "forward_mean_iters": float(torch.stack(fw_iters).float().mean().item()),
+        "adjoint_mean_iters": float(binfo.iters.float().mean().item()),
+        "backward_ms": bwd_ms,
+        "loss_first_last": [float(losses[0].item()), float(losses[-1].item())],
+        "wgrad": {"bound": "tensor", "achieved": wg_tflops, "peak": peak, "unit": "TFLOP/s",
+                  "frac": wg_tflops / peak, "ms_per_pass": wg_ms / 10,
+                  "tensor_core_convs": wg_tc,
+                  "timing": "CUDA events around 10 weight-gradient passes of the last backward"
+                            f" (both products per conv); peak: bf16_tflops burst ({src})"},
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.ncu_steps > 0:
         run_profile_steps(a)
+    elif a.impl == "ours" and a.workload == "C4":
+        run_warm(a)
+    elif a.impl == "ours" and a.workload == "C3":
+        run_train(a)
     elif a.impl == "reference":
         run_reference(a)
     else:

@@ -222,6 +222,23 @@ ideq_status ideq_solve_backward(ideq_ctx *ctx, const ideq_operator *op, ideq_sha
                                 const ideq_params *p, const ideq_adj_params *ap,
                                 float *dl_dtheta, float *dl_dlambda, ideq_info *info);
 
+/* One training step of the regulariser on a batch with ground truth x_true
+ * (App. D.1.2-D.1.3): x_out = x_hat from ideq_solve (x0 = A^T y), the loss
+ * l = mean((x_hat - x_true)^2) (device double *loss, nullable), the implicit
+ * backward of ideq_solve_backward with `ap`, and one Adam step (beta1 0.9, beta2
+ * 0.999, eps 1e-8, learning rate lr; Adam state kept in the context) on theta,
+ * after which the context's weights are the updated ones.  dl_dtheta (device,
+ * ideq_num_params floats) and dl_dlambda (device, 1 float) receive the gradient
+ * of this step (nullable); lambda itself is a parameter of the call and is not
+ * updated.  A forward solve that returns IDEQ_MAXITER / IDEQ_DIVERGED, or an
+ * adjoint solve that returns IDEQ_ADJ_MAXITER, ends the step with that status
+ * before theta changes.  info (nullable) receives the forward solve's results.
+ * Linear operators only (as ideq_solve_backward). */
+ideq_status ideq_train_step(ideq_ctx *ctx, const ideq_operator *op, ideq_shape shape,
+                            const float *y, const float *x_true, const ideq_params *p,
+                            const ideq_adj_params *ap, float lr, float *x_out,
+                            float *dl_dtheta, float *dl_dlambda, double *loss, ideq_info *info);
+
 /* ---- learned warm start x0 = A^T y + W(A^T y) ----------------------------- */
 /* Not in the paper, which leaves x^0 free (Algorithm 1).  W is an
  * IDEQ_NET_CNN network with its own weights and Adam state in the context. */
@@ -285,6 +302,15 @@ ideq_status ideq_prof_read(ideq_ctx *ctx, double *ms, int64_t *launches, double 
  * Needs a plan (after a solve, step or ideq_grad_reg), else IDEQ_ERR_ARG. */
 ideq_status ideq_time_convs(ideq_ctx *ctx, int reps, double *ms, int64_t *launches,
                             double *flops);
+/* Times `reps` repetitions of the weight-gradient pass of the last implicit
+ * backward (both products of every conv, the same kernels as in
+ * ideq_solve_backward) with one pair of CUDA events on the context's stream.
+ * *ms: elapsed time; *flops (nullable): the algorithmic FLOPs of the timed
+ * passes (2 x 2 M N K per conv and pass); *tc_convs (nullable): how many convs
+ * run on the tensor cores (the others on the SIMT kernel).  Needs a training
+ * plan (after ideq_solve_backward), else IDEQ_ERR_ARG.  Synchronises the stream. */
+ideq_status ideq_time_wgrad(ideq_ctx *ctx, int reps, double *ms, double *flops,
+                            int64_t *tc_convs);
 /* Algorithmic FLOPs of every convolution (all kinds, all n images) of one
  * iteration of the current plan: forward pass plus input-gradient pass. */
 ideq_status ideq_plan_flops(ideq_ctx *ctx, double *per_iteration);

@@ -78,6 +78,9 @@ _sig = {
                    P(Info)],
     "ideq_solve_backward": [c_void_p, P(Operator), Shape, c_void_p, c_void_p, c_void_p,
                             P(Params), P(AdjParams), c_void_p, c_void_p, P(Info)],
+    "ideq_train_step": [c_void_p, P(Operator), Shape, c_void_p, c_void_p, P(Params),
+                        P(AdjParams), c_float, c_void_p, c_void_p, c_void_p, c_void_p, P(Info)],
+    "ideq_time_wgrad": [c_void_p, c_int, P(c_double), P(c_double), P(ctypes.c_int64)],
     "ideq_warm_set": [c_void_p, P(NetDesc), c_void_p],
     "ideq_warm_forward": [c_void_p, Shape, c_void_p, c_void_p],
     "ideq_warm_train_step": [c_void_p, Shape, c_void_p, c_void_p, c_float, c_void_p],
@@ -296,6 +299,29 @@ def ideq_solve_backward(ctx: Context, op: Operator, y, x_bar, dl_dx, params: Par
     if st == IDEQ_ADJ_MAXITER and allow_maxiter:
         return st
     return ctx.check(st)
+
+
+def ideq_train_step(ctx: Context, op: Operator, y, x_true, params: Params, adj: AdjParams,
+                    lr: float, x_out=None, dl_dtheta=None, dl_dlambda=None, loss=None, info=None):
+    """One training step (solve, MSE loss, implicit backward, Adam on theta); returns
+    x_hat.  Raises IdeqError when the forward or the adjoint solve did not converge."""
+    import torch
+    x_out = torch.empty_like(y) if x_out is None else x_out
+    ctx.check(_lib.ideq_train_step(
+        ctx.h, ctypes.byref(op), _shape(y), _ptr(y, torch.float32), _ptr(x_true, torch.float32),
+        ctypes.byref(params), ctypes.byref(adj), float(lr), _ptr(x_out, torch.float32),
+        _ptr(dl_dtheta, torch.float32), _ptr(dl_dlambda, torch.float32),
+        _ptr(loss, torch.float64), ctypes.byref(info.s) if info is not None else None))
+    return x_out
+
+
+def ideq_time_wgrad(ctx: Context, reps: int):
+    """(ms, flops, tensor-core convs) of `reps` weight-gradient passes of the last
+    implicit backward, timed with CUDA events on the context's stream."""
+    ms, fl, n = c_double(0), c_double(0), ctypes.c_int64(0)
+    ctx.check(_lib.ideq_time_wgrad(ctx.h, int(reps), ctypes.byref(ms), ctypes.byref(fl),
+                                   ctypes.byref(n)))
+    return ms.value, fl.value, int(n.value)
 
 
 def make_adj(mode=IDEQ_ADJ_IMPLICIT, tol=1e-3, max_iter=500, beta=0.0) -> AdjParams:

@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "net.cu", "kernels_elem.cu", "conv_simt.cu", "conv_tc.cu", "conv_edge.cu",
            "conv_edge_rb.cu", "fft.cu", "wgrad.cu",
-           "net_train.cu", "noalloc.cu", "instr.cu"]
+           "net_train.cu", "noalloc.cu", "instr.cu", "wgrad_tc.cu"]
 
 
 def nvcc() -> str:

@@ -28,6 +28,16 @@ struct ideq_ctx {
   float* warm_v = nullptr;
   float* warm_g = nullptr;
   int warm_t = 0;
+  // training of the regulariser (ideq_train_step): Adam state of theta, the
+  // parameter gradient, the loss cotangent dl/dx_hat and the loss
+  float* reg_m = nullptr;
+  float* reg_v = nullptr;
+  float* reg_g = nullptr;
+  float* reg_cot = nullptr;
+  size_t reg_cot_bytes = 0;
+  double* reg_loss = nullptr;
+  float* reg_dlam = nullptr;
+  int reg_t = 0;
   std::string err;
   int* d_err = nullptr;       // device error flag of bounded waits
   int* h_running = nullptr;   // pinned
@@ -602,8 +612,10 @@ ideq_status ideq_destroy(ideq_ctx* ctx) {
   ctx->train.reset();
   ctx->warm_plan.reset();
   ctx->warm_w.reset();
-  for (float* p : {ctx->warm_m, ctx->warm_v, ctx->warm_g})
+  for (float* p : {ctx->warm_m, ctx->warm_v, ctx->warm_g, ctx->reg_m, ctx->reg_v, ctx->reg_g,
+                   ctx->reg_cot, ctx->reg_dlam})
     if (p) cudaFree(p);
+  if (ctx->reg_loss) cudaFree(ctx->reg_loss);
   ctx->w.reset();
   if (ctx->sv_mem) cudaFree(ctx->sv_mem);
   if (ctx->scratch) cudaFree(ctx->scratch);
@@ -890,7 +902,7 @@ ideq_status ideq_solve_backward(ideq_ctx* ctx, const ideq_operator* op, ideq_sha
   CK(run_steps(T->jvp, ctx->d_err, st, &ctx->prof, &ctx->launches));
   CK(run_steps(T->pchain, ctx->d_err, st, &ctx->prof, &ctx->launches));
   CK(cudaMemsetAsync(dl_dtheta, 0, ctx->w->nparams * 4, st));
-  CK(T->run_wgrad(dl_dtheta, p->tau * p->lambda, true, st, &ctx->launches));
+  CK(T->run_wgrad(dl_dtheta, p->tau * p->lambda, true, st, &ctx->launches, ctx->d_err));
   ctx->launches += 2;
   if (info) CK(launch_fill_info(n, ctx->sv, *info, st));
   if ((s = check_timeout(ctx)) != IDEQ_OK) return s;
@@ -901,6 +913,91 @@ ideq_status ideq_solve_backward(ideq_ctx* ctx, const ideq_operator* op, ideq_sha
       if (v != IDEQ_IMG_CONVERGED) return fail(ctx, IDEQ_ADJ_MAXITER, "adjoint solve did not converge");
   }
   return IDEQ_OK;
+}
+
+ideq_status ideq_train_step(ideq_ctx* ctx, const ideq_operator* op, ideq_shape shape,
+                            const float* y, const float* x_true, const ideq_params* p,
+                            const ideq_adj_params* ap, float lr, float* x_out,
+                            float* dl_dtheta, float* dl_dlambda, double* loss, ideq_info* info) {
+  clear_stale_cuda_error();
+  if (!ctx || !y || !x_true || !x_out || !ap || !shape_ok(shape) || !(lr >= 0.f))
+    return fail(ctx, IDEQ_ERR_ARG, "bad arguments");
+  const long long np = ctx->w->nparams;
+  const size_t bytes = (size_t)shape.n * shape.c * shape.h * shape.w * 4;
+  if (!ctx->reg_m) {
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMalloc((void**)&ctx->reg_m, np * 4));
+    CK(cudaMalloc((void**)&ctx->reg_v, np * 4));
+    CK(cudaMalloc((void**)&ctx->reg_g, np * 4));
+    CK(cudaMalloc((void**)&ctx->reg_loss, 16));
+    CK(cudaMalloc((void**)&ctx->reg_dlam, 16));
+    CK(cudaMemsetAsync(ctx->reg_m, 0, np * 4, ctx->stream));
+    CK(cudaMemsetAsync(ctx->reg_v, 0, np * 4, ctx->stream));
+    ctx->reg_t = 0;
+  }
+  if (ctx->reg_cot_bytes < bytes) {
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->reg_cot) cudaFree(ctx->reg_cot);
+    ctx->reg_cot = nullptr;
+    ctx->reg_cot_bytes = 0;
+    CK(cudaMalloc((void**)&ctx->reg_cot, bytes));
+    ctx->reg_cot_bytes = bytes;
+  }
+  // forward: x_hat, the fixed point (Algorithm 1); a solve that did not converge
+  // stops the step before any weight changes
+  ideq_status s = ideq_solve(ctx, op, shape, y, nullptr, x_out, p, info);
+  if (s != IDEQ_OK) return s;
+  cudaStream_t st = ctx->stream;
+  // l = mean((x_hat - x*)^2) and dl/dx_hat
+  double* lp = loss ? loss : ctx->reg_loss;
+  CK(launch_mse_grad((long long)bytes / 4, x_out, x_true, ctx->reg_cot, ctx->dot_part, lp, st));
+  ctx->launches += 2;
+  // implicit backward (App. D.1.2): dl/dtheta, dl/dlambda
+  float* dl = dl_dlambda ? dl_dlambda : ctx->reg_dlam;
+  s = ideq_solve_backward(ctx, op, shape, y, x_out, ctx->reg_cot, p, ap, ctx->reg_g, dl, nullptr);
+  if (s != IDEQ_OK) return s;
+  if (dl_dtheta) CK(cudaMemcpyAsync(dl_dtheta, ctx->reg_g, np * 4, cudaMemcpyDeviceToDevice, st));
+  // one Adam step on theta, then the weight forms of the convolutions
+  ctx->reg_t += 1;
+  CK(launch_adam(np, ctx->w->master, ctx->reg_g, ctx->reg_m, ctx->reg_v, ctx->reg_t, lr, 0.9f,
+                 0.999f, 1e-8f, st));
+  CK(ctx->w->reform(st));
+  ctx->launches += 1 + 2 * (long long)ctx->w->layers.size();
+  return IDEQ_OK;
+}
+
+ideq_status ideq_time_wgrad(ideq_ctx* ctx, int reps, double* ms, double* flops,
+                            int64_t* tc_convs) {
+  clear_stale_cuda_error();
+  if (!ctx || reps < 1 || !ms) return fail(ctx, IDEQ_ERR_ARG, "bad arguments");
+  TrainPlan* T = ctx->train.get();
+  if (!T) return fail(ctx, IDEQ_ERR_ARG, "no training plan yet: run ideq_solve_backward first");
+  float* dst = ensure_scratch(ctx, (size_t)ctx->w->nparams * 4);
+  if (!dst) return fail(ctx, IDEQ_ERR_NOMEM, "scratch");
+  cudaStream_t st = ctx->stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  cudaError_t e = cudaEventRecord(e0, st);
+  for (int r = 0; r < reps && e == cudaSuccess; ++r)
+    e = T->run_wgrad(dst, 1.f, true, st, &ctx->launches, ctx->d_err);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "ideq_time_wgrad");
+  double fl = 0;
+  long long ntc = 0;
+  for (const WgStep& g : T->wg) {
+    fl += 2.0 * g.a.flops();  // the dual form: two products per conv
+    ntc += g.tc[0] != nullptr;
+  }
+  *ms = t;
+  if (flops) *flops = fl * reps;
+  if (tc_convs) *tc_convs = ntc;
+  return check_timeout(ctx);
 }
 
 ideq_status ideq_warm_set(ideq_ctx* ctx, const ideq_net_desc* net, const float* weights) {
@@ -952,7 +1049,7 @@ ideq_status ideq_warm_train_step(ideq_ctx* ctx, ideq_shape shape, const float* a
   CK(launch_mse_grad(numel, T->out_img, target, T->cot_img, part, loss, st));
   CK(run_steps(T->tchain, ctx->d_err, st, &ctx->prof, &ctx->launches));
   CK(cudaMemsetAsync(ctx->warm_g, 0, W->nparams * 4, st));
-  CK(T->run_wgrad(ctx->warm_g, 1.f, false, st, &ctx->launches));
+  CK(T->run_wgrad(ctx->warm_g, 1.f, false, st, &ctx->launches, ctx->d_err));
   ctx->warm_t += 1;
   CK(launch_adam(W->nparams, W->master, ctx->warm_g, ctx->warm_m, ctx->warm_v, ctx->warm_t, lr,
                  0.9f, 0.999f, 1e-8f, st));

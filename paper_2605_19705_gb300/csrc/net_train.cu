@@ -17,6 +17,7 @@
 // Every pass has its own buffers (nothing is overwritten), so the weight
 // gradients can run after all reverse passes.
 #include <algorithm>
+#include <cstdlib>
 
 #include "net.h"
 #include "net_train.h"
@@ -27,6 +28,9 @@ TrainPlan::~TrainPlan() {
   for (auto* L : {&fwd, &tchain, &jvp, &pchain})
     for (auto& s : *L)
       if (s.tc) tc_plan_destroy(s.tc);
+  for (auto& g : wg)
+    for (WgTcPlan* p : g.tc)
+      if (p) wgrad_tc_plan_destroy(p);
   for (void* p : allocs) cudaFree(p);
 }
 
@@ -375,10 +379,15 @@ bool TrainPlan::build(NetWeights* wts, int n_, int H_, int W_, int prec_, double
     if (err->empty()) *err = "cudaMalloc(train activations) failed";
     return false;
   }
-  // weight-gradient workspace: splits x N x K partials and a GEMM-form accumulator
+  // weight-gradient workspace: splits x N x K partials and a GEMM-form accumulator;
+  // tensor-core forms for the 16-bit convs that fit them (IDEQ_WGRAD_TC=0: SIMT only)
+  const char* tcv = std::getenv("IDEQ_WGRAD_TC");
+  const bool use_tc = !(tcv && tcv[0] == '0');
   size_t part = 0, acc = 0;
   for (auto& g : wg) {
-    part = std::max(part, (size_t)wgrad_splits(g.a) * g.a.N() * g.a.K());
+    const bool tc = use_tc && wgrad_tc_supported(g.a, g.in_dt, g.cot_dt);
+    const int sp = std::max(wgrad_splits(g.a), tc ? wgrad_tc_splits(g.a) : 1);
+    part = std::max(part, (size_t)sp * g.a.N() * g.a.K());
     acc = std::max(acc, (size_t)g.a.N() * g.a.K());
   }
   wg_part = (float*)alloc(part * 4);
@@ -387,6 +396,19 @@ bool TrainPlan::build(NetWeights* wts, int n_, int H_, int W_, int prec_, double
     *err = "cudaMalloc(wgrad workspace) failed";
     return false;
   }
+  for (auto& g : wg) {
+    if (!use_tc || !wgrad_tc_supported(g.a, g.in_dt, g.cot_dt)) continue;
+    const void* ins[3] = {g.a.in, g.tin, g.a.in};
+    const void* cots[3] = {g.pcot, g.tcot, g.tcot};
+    for (int j = 0; j < 3; ++j) {
+      if ((warm && j < 2) || (!warm && j == 2) || !ins[j] || !cots[j]) continue;
+      g.tc[j] = wgrad_tc_plan_create(g.a, g.in_dt, ins[j], cots[j], wg_part);
+      if (!g.tc[j]) {
+        *err = "tensor-core weight-gradient plan failed";
+        return false;
+      }
+    }
+  }
   return true;
 }
 
@@ -394,18 +416,26 @@ bool TrainPlan::build(NetWeights* wts, int n_, int H_, int W_, int prec_, double
 // <pcot, out(primal)> + <tcot, out(tangent)> over every conv (dual), or of
 // <tcot, out(primal)> alone (plain reverse chain, e.g. the warm start).
 cudaError_t TrainPlan::run_wgrad(float* dst, float scale, bool dual, cudaStream_t st,
-                                 long long* launches) {
+                                 long long* launches, int* err) {
   for (const WgStep& g : wg) {
     const Layer& L = w->layers[g.layer];
     const long long nk = (long long)g.a.N() * g.a.K();
     cudaError_t e = cudaMemsetAsync(wg_acc, 0, nk * 4, st);
     if (e != cudaSuccess) return e;
-    e = launch_wgrad(g.a, g.in_dt, g.cot_dt, dual ? g.pcot : g.tcot, 1.f, wg_part, wg_acc, st);
+    const WgTcPlan* t0 = dual ? g.tc[0] : g.tc[2];
+    if (t0)
+      e = launch_wgrad_tc(t0, 1.f, wg_acc, err, st);
+    else
+      e = launch_wgrad(g.a, g.in_dt, g.cot_dt, dual ? g.pcot : g.tcot, 1.f, wg_part, wg_acc, st);
     if (e != cudaSuccess) return e;
     if (dual) {
-      ConvArgs t = g.a;
-      t.in = g.tin;
-      e = launch_wgrad(t, g.in_dt, g.cot_dt, g.tcot, 1.f, wg_part, wg_acc, st);
+      if (g.tc[1]) {
+        e = launch_wgrad_tc(g.tc[1], 1.f, wg_acc, err, st);
+      } else {
+        ConvArgs t = g.a;
+        t.in = g.tin;
+        e = launch_wgrad(t, g.in_dt, g.cot_dt, g.tcot, 1.f, wg_part, wg_acc, st);
+      }
       if (e != cudaSuccess) return e;
     }
     // accumulate the [N][K] forward-form gradient into the PyTorch layout

@@ -9,6 +9,7 @@
 // order (deterministic), scales and adds into a [N][K] f32 accumulator.
 #include "common.cuh"
 #include "ideq_internal.h"
+#include "net_train.h"
 
 namespace ideq {
 
@@ -158,7 +159,11 @@ cudaError_t launch_wgrad(const ConvArgs& a, int in_dt, int cot_dt, const void* c
     wgrad_kernel<float><<<grid, 256, 0, st>>>(a, cot, mps, part);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const long long nk = (long long)a.N() * a.K();
+  return launch_wgrad_reduce((long long)a.N() * a.K(), splits, part, scale, dst, st);
+}
+
+cudaError_t launch_wgrad_reduce(long long nk, int splits, const float* part, float scale,
+                                float* dst, cudaStream_t st) {
   const int blocks = (int)std::min<long long>((nk + 255) / 256, 2048);
   wgrad_reduce_kernel<<<blocks, 256, 0, st>>>(nk, splits, part, scale, dst);
   return cudaGetLastError();

@@ -9,7 +9,7 @@ same point.  Tolerances: FP32 convolutions 1e-4 relative on the parameter gradie
 import numpy as np
 import pytest
 
-from gpu_common import ctx_for, op_for, rel, setup
+from gpu_common import ctx_for, op_for, rel, setup, to_np
 from oracle import adjoint, solver
 
 torch = pytest.importorskip("torch")
@@ -175,3 +175,96 @@ def test_autograd_function_backward_equals_direct_call():
     b.ideq_solve_backward(ctx, op, ty, x.detach().contiguous(), v, params, adj, dth, dlam)
     assert torch.allclose(gw, dth, rtol=1e-5, atol=1e-12)
     assert abs(float(gl) - float(dlam)) <= 1e-5 * abs(float(dlam))
+
+
+@pytest.mark.parametrize("name,over", [("C1a", dict(n=2, h=64, w=64)),
+                                       ("C1a", dict(n=1, h=40, w=56)),
+                                       ("C3", dict(n=2, h=64, w=64))])
+def test_tensor_core_weight_gradient_matches_simt(name, over):
+    """The tcgen05 weight gradient (3x3 and stride-2 2x2 convs with 64k input and
+    output channels, MN-major operands, split-K with a fixed-order reduction) against
+    the SIMT weight-gradient kernel on the same FP16 activations and cotangents
+    (IDEQ_WGRAD_TC=0 keeps a context on the SIMT kernel): both accumulate in FP32
+    over the pixels, so only the summation order differs.  JFB mode, the dual
+    (pcot x input + tcot x tangent) form of App. D.1.2's parameter gradient.  The
+    ragged 40 x 56 case has partial 64-pixel boxes and levels narrower than a box."""
+    import os
+    cfg, wl, net, ops, ys = setup(name, **over)
+    b = B()
+    rng = np.random.default_rng(9)
+    xbar = np.clip(ys + 0.05 * rng.standard_normal(ys.shape), 0, 1).astype(np.float32)
+    v = (2.0 * (xbar - wl["x_true"]) / xbar.size).astype(np.float64)
+    out = []
+    for simt in (False, True):
+        if simt:
+            os.environ["IDEQ_WGRAD_TC"] = "0"
+        try:
+            out.append(_gpu_backward(cfg, wl, ys, xbar, v, b.IDEQ_FP16, b.IDEQ_ADJ_JFB))
+        finally:
+            os.environ.pop("IDEQ_WGRAD_TC", None)
+    (d_tc, l_tc, _, _), (d_simt, l_simt, _, _) = out
+    assert np.isfinite(d_tc).all()
+    assert rel(d_tc, d_simt) < 1e-4, rel(d_tc, d_simt)
+    assert l_tc == l_simt  # dl/dlambda does not involve the weight gradient
+
+
+def test_train_step_is_solve_backward_and_adam():
+    """ideq_train_step = ideq_solve + MSE loss + ideq_solve_backward + one Adam step
+    on theta: its gradient equals the direct calls' on a fresh context with the same
+    weights, its loss equals mean((x_hat - x*)^2), and the new weights equal
+    torch.optim.Adam's step on that gradient."""
+    cfg, wl, net, ops, ys = setup("C3", n=2, h=32, w=32)
+    b = B()
+    op = op_for(cfg, wl)
+    ty = torch.tensor(ys, device="cuda")
+    xt = torch.tensor(wl["x_true"], device="cuda")
+    params = b.make_params(cfg["lam"], cfg["tau"], cfg["beta"], tol=1e-5, max_iter=3000)
+    adj = b.make_adj(b.IDEQ_ADJ_IMPLICIT, 1e-5, 3000, 0.0)
+    w0 = torch.tensor(wl["weights"], device="cuda")
+    ctx = ctx_for(cfg, wl, b.IDEQ_FP32)
+    g = torch.zeros_like(w0)
+    dlam = torch.zeros(1, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    lr = 1e-3
+    x = b.ideq_train_step(ctx, op, ty, xt, params, adj, lr, dl_dtheta=g, dl_dlambda=dlam,
+                          loss=loss)
+    # the same gradient from the direct calls on a fresh context
+    ref = ctx_for(cfg, wl, b.IDEQ_FP32)
+    xr, _ = b.ideq_solve(ref, op, ty, params)
+    v = (2.0 * (xr - xt) / xr.numel()).contiguous()
+    gr = torch.zeros_like(w0)
+    lr_ = torch.zeros(1, device="cuda")
+    b.ideq_solve_backward(ref, op, ty, xr, v, params, adj, gr, lr_)
+    torch.cuda.synchronize()
+    assert torch.equal(x, xr)
+    assert abs(float(loss) - float(((xr.double() - xt.double()) ** 2).mean())) < 1e-12
+    assert torch.allclose(g, gr, rtol=1e-5, atol=1e-12)
+    assert abs(float(dlam) - float(lr_)) <= 1e-5 * abs(float(lr_))
+    # weights after the step: torch's Adam on the same gradient
+    p = w0.clone().requires_grad_(True)
+    opt = torch.optim.Adam([p], lr=lr, betas=(0.9, 0.999), eps=1e-8)
+    p.grad = gr.clone()
+    opt.step()
+    # the context now solves with the updated weights: compare through a solve
+    ctx_new = b.Context(b.net_desc(cfg["net"], cfg["c"]), p.detach().contiguous(), b.IDEQ_FP32)
+    x1, _ = b.ideq_solve(ctx, op, ty, params)
+    x2, _ = b.ideq_solve(ctx_new, op, ty, params)
+    assert rel(to_np(x1), to_np(x2)) < 1e-5
+
+
+def test_autograd_raises_on_unconverged_adjoint():
+    """A capped implicit adjoint solve is reported, not silently differentiated."""
+    from paper_2605_19705_gb300 import autograd as IA
+    cfg, wl, net, ops, ys = setup("C3", n=1, h=32, w=32)
+    b = B()
+    ctx = ctx_for(cfg, wl, b.IDEQ_FP32)
+    op = op_for(cfg, wl)
+    w = torch.tensor(wl["weights"], device="cuda", requires_grad=True)
+    lam = torch.tensor(cfg["lam"], device="cuda", requires_grad=True)
+    params = b.make_params(cfg["lam"], cfg["tau"], cfg["beta"], tol=1e-6, max_iter=3000)
+    adj = IA.make_adj(b.IDEQ_ADJ_IMPLICIT, 1e-12, 2)  # two adjoint iterations at most
+    x = IA.ideq_restore(w, lam, torch.tensor(ys, device="cuda"), ctx, op, params, adj)
+    loss = ((x - torch.tensor(wl["x_true"], device="cuda")) ** 2).mean()
+    with pytest.raises(b.IdeqError) as e:
+        torch.autograd.grad(loss, [w, lam])
+    assert e.value.status == b.IDEQ_ADJ_MAXITER
