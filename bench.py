@@ -50,6 +50,7 @@ WARM_TRAIN_IMAGES = 512   # held-out equilibria the warm start is trained on
 WARM_TRAIN_STEPS = 600    # Adam steps (batch 8, lr 1e-3)
 WORKLOAD = WORKLOADS["C1a"]
 CONV_REPS = 20  # repetitions of the conv launch sequence in the roofline timing
+UPDATE_REPS = 60  # timed calls of the update pass
 
 
 def make_op_and_y(B, cfg, wl, ctx, x_true, dev):
@@ -298,6 +299,26 @@ def run_ours(args):
     per_image_iter_flops = B.ideq_plan_flops(ctx) / n
     algo_flops_per_step = float(iters_t.sum()) / args.steps * per_image_iter_flops
 
+    # ---- the fused update pass alone (x_new = z - tau (grad f + lambda grad g) with the
+    # FP64 step norms), through the allocation-free entry point on buffers of this
+    # batch's size; six buffer sets in rotation exceed L2, so every call reads HBM
+    sets = [[torch.rand_like(y) for _ in range(5)] for _ in range(6)]
+    nrm = torch.zeros(2, n, dtype=torch.float64, device=dev)
+    for k in range(6):
+        z_, f_, g_, x_, o_ = sets[k]
+        B.ideq_red_update_noalloc(z_, f_, g_, x_, o_, 0.1, 0.75, nrm[0], nrm[1])
+    torch.cuda.synchronize()
+    u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    u0.record(st)
+    for k in range(UPDATE_REPS):
+        z_, f_, g_, x_, o_ = sets[k % 6]
+        B.ideq_red_update_noalloc(z_, f_, g_, x_, o_, 0.1, 0.75, nrm[0], nrm[1])
+    u1.record(st)
+    torch.cuda.synchronize()
+    upd_ms = u0.elapsed_time(u1) / UPDATE_REPS
+    upd_bytes = 5 * y.numel() * 4
+    del sets
+
     # ---- end to end through the C ABI: pinned host y in, x_hat out, every step
     y_host = y.cpu().pin_memory()
     x_host = torch.empty_like(y_host).pin_memory()
@@ -382,6 +403,13 @@ def run_ours(args):
                      "step_work": "sum over images of their iterations x conv FLOPs per image "
                                   "iteration (frozen images' work not counted), per timed step"},
         "clocks": clk,
+        "update_pass": {"bound": "hbm", "achieved": upd_bytes / (upd_ms / 1e3) / 1e9,
+                        "peak": float(peaks.get("hbm_gbs", 6800.0)), "unit": "GB/s",
+                        "frac": upd_bytes / (upd_ms / 1e3) / 1e9 / float(peaks.get("hbm_gbs", 6800.0)),
+                        "us_per_pass": upd_ms * 1e3, "bytes_per_pass": upd_bytes,
+                        "timing": f"CUDA events around {UPDATE_REPS} calls of "
+                                  "ideq_red_update_noalloc (red_update_kernel + per-image "
+                                  "norm sums) rotating over 6 buffer sets (> L2)"},
     }
     if plain:
         res["plain_fp32"] = plain
@@ -628,7 +656,10 @@ def run_train(args):
     y = B.ideq_apply_A(ctx, op, x_true) + torch.tensor(wl["noise"], device=dev)
     params = B.make_params(cfg["lam"], cfg["tau"], cfg["beta"], cfg["B"], cfg["tol"],
                            cfg["max_iter"])
-    adj = B.make_adj(B.IDEQ_ADJ_IMPLICIT, cfg["adj_tol"], 3000, 0.0)
+    # the adjoint iteration u <- J_R^T u + v with the forward's heavy-ball inertia
+    # (its fixed point is the implicit gradient's; plain iteration crawls along the
+    # directions the blur removes, where J_R's eigenvalues approach 1)
+    adj = B.make_adj(B.IDEQ_ADJ_IMPLICIT, cfg["adj_tol"], 3000, cfg["beta"])
     lr = 1e-5
     info = B.InfoBuffers(n, dev)
     binfo_iters = []
@@ -674,7 +705,8 @@ def run_train(args):
         "vs_baseline": None, "dtype": "f16",
         "data": "synthetic (seeded patches, kernels, noise; random-init U-Net weights)",
         "config": {"workload": WORKLOADS["C3"], "batch_per_gpu": n, "image": "3x128x128",
-                   "lr": lr, "adjoint": "implicit, u <- J_R^T u + v, tol 1e-3"},
+                   "lr": lr, "adjoint": "implicit, u <- J_R^T u + v with heavy-ball beta "
+                                        f"{cfg['beta']}, tol 1e-3"},
         "images_per_s": n * 1e3 / ms,
         "forward_mean_iters": float(torch.stack(fw_iters).float().mean().item()),
         "adjoint_mean_iters": float(binfo.iters.float().mean().item()),

@@ -147,6 +147,15 @@ ideq_status check_op(ideq_ctx* ctx, const ideq_operator* op, const ideq_shape& s
   return IDEQ_OK;
 }
 
+// IDEQ_SKIP_FROZEN=0 computes frozen images too (for comparisons).
+bool skip_frozen_enabled() {
+  static const bool on = [] {
+    const char* v = std::getenv("IDEQ_SKIP_FROZEN");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
+
 ideq_status ensure_plan(ideq_ctx* ctx, const ideq_shape& s) {
   if (s.c != ctx->w->desc.in_ch) return fail(ctx, IDEQ_ERR_ARG, "channels differ from the network's in_ch");
   NetPlan* p = ctx->plan.get();
@@ -223,7 +232,8 @@ ideq_status ensure_plan(ideq_ctx* ctx, const ideq_shape& s) {
   CK(cudaMemsetAsync(m, 0, off, ctx->stream));
   std::unique_ptr<NetPlan> np(new NetPlan());
   std::string e;
-  if (!np->build(ctx->w.get(), s.n, s.h, s.w, ctx->precision, v.gsum, &e, v.skip))
+  if (!np->build(ctx->w.get(), s.n, s.h, s.w, ctx->precision, v.gsum, &e,
+                 skip_frozen_enabled() ? v.skip : nullptr))
     return fail(ctx, IDEQ_ERR_UNSUPPORTED, "plan: " + e);
   ctx->plan = std::move(np);
   return IDEQ_OK;

@@ -266,11 +266,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   // form one row box and the three horizontal taps of B of one (row, channel chunk)
   const bool STREAM = !HALO && !NW && a.stream;
   const int A_STAGE =
-      HALO ? (a.slide ? HBOX : 3 * HBOX) : (STREAM ? HALO_BOX : MS * A_TILE);
+      HALO ? (a.slide ? HBOX : 3 * HBOX) : (STREAM ? MS * HALO_BOX : MS * A_TILE);
   const int B_STAGE = STREAM ? 3 * B_BYTES : B_BYTES;
   const uint32_t STAGE_TX =
       HALO ? (a.slide ? 1u : 3u) * HALO_ROWS * (uint32_t)RB
-           : (STREAM ? HALO_ROWS * 128u + 3u * B_BYTES : (uint32_t)(MS * A_TILE + B_BYTES));
+           : (STREAM ? MS * HALO_ROWS * 128u + 3u * B_BYTES
+                     : (uint32_t)(MS * A_TILE + B_BYTES));
   constexpr bool IMG = BN == 16;  // image-side output: c <= 16 planar f32 channels
   constexpr int NPANEL = (IMG || BN < 64) ? 1 : BN / 64;  // 64-column epilogue panels
   constexpr int KCH = RB / (int)sizeof(TA);  // K elements per ring row
@@ -280,6 +281,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   constexpr bool SPLIT = BN <= 32;
   const bool spl = SPLIT || (BN == 64 && MS == 1 && a.split64 != 0);
   constexpr int TCOLS = MS * BN;  // TMEM columns of one accumulator buffer (2 x >= 32 allocated)
+  // accumulator buffers: two (the epilogue of one tile overlaps the MMAs of the
+  // next) while they fit the 512 TMEM columns, else one (M = 256 x N = 256 tiles)
+  constexpr int NACC = TCOLS <= 256 ? 2 : 1;
   const int ST = a.stages;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -315,25 +319,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"((uint32_t)(2 * TCOLS))
+                 "r"((uint32_t)(NACC * TCOLS))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
+  // The images to compute: every warp reads the per-image skip flags into a
+  // bitmask.  The flags are written only by kernels that are not convolutions (the
+  // solver's bookkeeping) or by copies, after which the first convolution starts
+  // only once they have completed; convolutions never write them.  So they are
+  // read before the wait below, overlapping the previous convolution's tail.
+  const bool masked = a.skip != nullptr && a.n <= kMaxMaskImages;
+  uint32_t run = 0u;
+  if (masked) run = __ballot_sync(0xffffffffu, lane < a.n && a.skip[lane] == 0);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   // Programmatic dependent launch: the set-up above may overlap the tail of the
-  // previous kernel in the stream; every global access of this kernel comes after
-  // that kernel's results are complete and visible.  The next conv may start its
-  // own set-up as soon as this kernel's CTAs leave their SMs.
+  // previous kernel in the stream; every global access of this kernel to data a
+  // convolution writes comes after that kernel's results are complete and visible.
+  // The next conv may start its own set-up as soon as this kernel's CTAs leave
+  // their SMs.
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  // the images to compute: every warp reads the skip flags (written by an earlier
-  // kernel of the stream, complete after the wait above) into a bitmask
-  const bool masked = a.skip != nullptr && a.n <= kMaxMaskImages;
-  uint32_t run = 0u;
-  if (masked) run = __ballot_sync(0xffffffffu, lane < a.n && a.skip[lane] == 0);
   const ImgMap im{masked ? __popc(run) : a.n, run, masked};
   const int ntiles = ((im.nrun * a.tiles_h * a.tiles_w + MS - 1) / MS) * a.tiles_n;
   // this CTA's tiles: t_first + i * t_step, i < my_tiles (a contiguous range in
@@ -397,7 +405,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
       }
       for (int i = 0; i < my_tiles && ok && STREAM; ++i) {  // streamed halo
-        const TileCoord tc = tile_coord(a, im, t_first + i * t_step, BN, MS, 0);
+        const int t = t_first + i * t_step;
         for (int kc = 0; kc < 3 * a.cpt; ++kc) {  // (row dy, channel chunk c)
           const int s = g % ST, j = g / ST;
           if (j > 0 && !mbar_wait(empty0 + 8 * s, (j - 1) & 1, a.err, 1)) {
@@ -406,8 +414,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
           mbar_expect_tx(full0 + 8 * s, STAGE_TX);
           const int dy = kc / a.cpt, c = kc - dy * a.cpt;
-          tma_load_4d(smem_u32(sA + s * A_STAGE), &tmA, c * KCH, tc.w0 - 1, tc.h0 + dy - 1, tc.img,
-                      full0 + 8 * s);
+#pragma unroll
+          for (int sub = 0; sub < MS; ++sub) {  // one row box per 128-pixel sub-tile
+            const TileCoord sc = tile_coord(a, im, t, BN, MS, sub);
+            tma_load_4d(smem_u32(sA + s * A_STAGE + sub * HALO_BOX), &tmA, c * KCH, sc.w0 - 1,
+                        sc.h0 + dy - 1, sc.img, full0 + 8 * s);
+          }
+          const TileCoord tc = tile_coord(a, im, t, BN, MS, 0);
           for (int dx = 0; dx < 3; ++dx)
             tma_load_2d(smem_u32(sB + s * B_STAGE + dx * B_BYTES), &tmB,
                         ((3 * dy + dx) * a.cpt + c) * KCH, tc.n0, full0 + 8 * s);
@@ -468,7 +481,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       int g = 0, base = 0;  // base: ring position of the tile's row y-1 box (HALO)
       for (int lt = 0; lt < my_tiles && ok; ++lt) {
         const int t = t_first + lt * t_step;
-        const int b = lt & 1, u = lt >> 1;
+        const int b = lt % NACC, u = lt / NACC;
         if (u > 0 && !mbar_wait(tempty0 + 8 * b, (u - 1) & 1, a.err, 5)) {
           ok = false;
           break;
@@ -537,11 +550,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const uint32_t abox = smem_u32(sA + s * A_STAGE);
 #pragma unroll 1
             for (int dx = 0; dx < 3; ++dx) {
-              const uint64_t ad = umma_desc_sw128_rows(abox, dx);
               const uint64_t bd = umma_desc_sw128(smem_u32(sB + s * B_STAGE + dx * B_BYTES));
 #pragma unroll
-              for (int kk = 0; kk < KSTEPS; ++kk)
-                umma<TA>(td, ad + 2 * kk, bd + 2 * kk, idesc, (kc | dx | kk) != 0 ? 1u : 0u);
+              for (int sub = 0; sub < MS; ++sub) {
+                const uint64_t ad = umma_desc_sw128_rows(abox + sub * HALO_BOX, dx);
+#pragma unroll
+                for (int kk = 0; kk < KSTEPS; ++kk)
+                  umma<TA>(td + sub * BN, ad + 2 * kk, bd + 2 * kk, idesc,
+                           (kc | dx | kk) != 0 ? 1u : 0u);
+              }
             }
             umma_commit(empty0 + 8 * s);
             ++g;
@@ -659,7 +676,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int j = 0; j < my_n && ok; ++j) {
         const int lt = lt0 + j * lstep;
         const int t = t_first + lt * t_step;
-        const int b = lt & 1, u = lt >> 1;
+        const int b = lt % NACC, u = lt / NACC;
         ok = __all_sync(0xffffffffu, mbar_wait(tfull0 + 8 * b, u & 1, a.err, 4));
         tc_fence_after();
         for (int pp = 0; pp < npan && ok; ++pp, ++pc) {
@@ -714,7 +731,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"((uint32_t)(2 * TCOLS))
+                 "r"((uint32_t)(NACC * TCOLS))
                  : "memory");
   }
 }
@@ -864,64 +881,81 @@ TcPlan* tc_plan_create(const ConvArgs& a, int op_dt, int epi_dt, std::string* er
   const size_t bres = (size_t)p->nk * p->bn * RB;
   // (instantiated for N tiles of 16, 64 and 128 columns, narrow rows 16 to 64)
   const bool halo_bn = p->nw ? p->bn <= 64 : (p->bn == 16 || p->bn == 64 || p->bn == 128);
-  p->halo = op_dt != DT_FP8 && a.mode == CM_CONV3 && p->Wt == 128 && p->Ht == 1 &&
-            p->tiles_n == 1 && p->cpt == 1 && halo_bn && bres <= 80 * 1024 &&
-            tiling_override("IDEQ_TC_HALO", 1) != 0;
-  p->slide = p->halo && !p->nw && tiling_override("IDEQ_TC_SLIDE", 0) != 0;
-  // streamed halo: full-row 3x3 convs whose weights do not stay resident
-  p->stream = !p->halo && op_dt != DT_FP8 && !p->nw && a.mode == CM_CONV3 && p->Wt == 128 &&
-              p->Ht == 1 && p->tiles_n == 1 && p->bn <= 128 && p->bn != 32 &&
-              tiling_override("IDEQ_TC_STREAM", 1) != 0;
-  // Two 128-row sub-tiles can share each weight chunk (half the weight traffic
-  // per FLOP), but measured on the U-Net layers the coarser tiles balance worse
-  // over the SMs than they save, so M = 256 is used only when forced.
-  p->ms = 1;
-  {
-    const int force_ms = tiling_override("IDEQ_TC_MS", 0);  // 2 forces two sub-tiles
-    if (!p->halo && !p->stream && !p->nw && p->bn >= 64 && p->bn <= 128 && force_ms == 2)
-      p->ms = 2;
-  }
-  // shared memory: ring depth and staging buffers, preferring a deep ring
-  // (halo: >= 5 row boxes, three in use and two in flight; else >= 3 stages),
-  // then double-buffered staging
-  const size_t stage = p->halo     ? (size_t)(p->slide ? 1 : 3) * (p->nw ? HALO_BOX_NW : HALO_BOX)
-                       : p->stream ? (size_t)HALO_BOX + 3 * (size_t)p->bn * 128
-                                   : ((size_t)p->ms * 128 + (size_t)p->bn) * RB;
-  const size_t resident = p->halo ? bres : 0;
+  // the form with resident weights (halo) is tried first; where its staging does
+  // not fit (epilogues with three auxiliary inputs), the layer runs without it
   p->stages = 0;
-  // short K (depth-to-space, stride-2 and 1x1 layers): the epilogue paces the
-  // kernel, so auxiliary boxes are fetched four panels ahead and the ring is
-  // held to two stages (measured: 2% on the depth-to-space layers, 57 vs 58 us)
-  if (p->naux > 0 && !p->halo && !p->stream && p->nk <= 4 &&
-      tiling_override("IDEQ_TC_NBA", MAX_NBA) == MAX_NBA) {
-    for (int st = 8; st >= 2 && !p->stages; --st) {
-      const size_t tot = fixed_smem(p->nout, p->naux, 2, MAX_NBA, st) + (size_t)st * stage;
-      if (tot <= kMaxSmem) {
-        p->stages = st;
-        p->nbo = 2;
-        p->nba = MAX_NBA;
-        p->smem = tot;
+  for (int pass = 0; pass < 2 && !p->stages; ++pass) {
+    const bool no_halo = pass == 1;
+    p->halo = !no_halo && op_dt != DT_FP8 && a.mode == CM_CONV3 && p->Wt == 128 &&
+              p->Ht == 1 && p->tiles_n == 1 && p->cpt == 1 && halo_bn && bres <= 80 * 1024 &&
+              tiling_override("IDEQ_TC_HALO", 1) != 0;
+    p->slide = p->halo && !p->nw && tiling_override("IDEQ_TC_SLIDE", 0) != 0;
+    // streamed halo: full-row 3x3 convs whose weights do not stay resident
+    p->stream = !p->halo && op_dt != DT_FP8 && !p->nw && a.mode == CM_CONV3 && p->Wt == 128 &&
+                p->Ht == 1 && p->tiles_n == 1 && p->bn <= 128 && p->bn != 32 &&
+                tiling_override("IDEQ_TC_STREAM", 1) != 0;
+    // Two 128-row sub-tiles share each weight chunk (M = 256 per CTA): a third fewer
+    // operand bytes per MMA cycle into each SM, whose L2-to-shared-memory rate bounds
+    // the 128- to 512-channel layers, at the price of coarser tiles.  Taken where it
+    // lowers the number of waves over the SMs (IDEQ_TC_MS = 1 / 2 forces one / two).
+    p->ms = 1;
+    {
+      static int nsm = 0;
+      if (nsm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (nsm <= 0) nsm = 148;
+      }
+      const int force_ms = tiling_override("IDEQ_TC_MS", 0);
+      const bool ms2_ok = !p->halo && !p->nw && op_dt != DT_FP8 && p->bn >= 64 && !img;
+      const long long tm = (long long)a.n * p->tiles_h * p->tiles_w;
+      const long long w1 = (tm * p->tiles_n + nsm - 1) / nsm;
+      const long long w2 = (((tm + 1) / 2) * p->tiles_n + nsm - 1) / nsm;
+      if (ms2_ok && (force_ms == 2 || (force_ms == 0 && w2 < w1))) p->ms = 2;
+    }
+    // shared memory: ring depth and staging buffers, preferring a deep ring
+    // (halo: >= 5 row boxes, three in use and two in flight; else >= 3 stages),
+    // then double-buffered staging
+    const size_t stage = p->halo     ? (size_t)(p->slide ? 1 : 3) * (p->nw ? HALO_BOX_NW : HALO_BOX)
+                         : p->stream ? (size_t)p->ms * HALO_BOX + 3 * (size_t)p->bn * 128
+                                     : ((size_t)p->ms * 128 + (size_t)p->bn) * RB;
+    const size_t resident = p->halo ? bres : 0;
+    p->stages = 0;
+    // short K (depth-to-space, stride-2 and 1x1 layers): the epilogue paces the
+    // kernel, so auxiliary boxes are fetched four panels ahead and the ring is
+    // held to two stages (measured: 2% on the depth-to-space layers, 57 vs 58 us)
+    if (p->naux > 0 && !p->halo && !p->stream && p->nk <= 4 &&
+        tiling_override("IDEQ_TC_NBA", MAX_NBA) == MAX_NBA) {
+      for (int st = 8; st >= 2 && !p->stages; --st) {
+        const size_t tot = fixed_smem(p->nout, p->naux, 2, MAX_NBA, st) + (size_t)st * stage;
+        if (tot <= kMaxSmem) {
+          p->stages = st;
+          p->nbo = 2;
+          p->nba = MAX_NBA;
+          p->smem = tot;
+        }
       }
     }
-  }
-  const int min_stages[2] = {p->halo ? (p->slide ? 5 : 3) : (p->stream ? 2 : 3),
-                             p->halo ? (p->slide ? 4 : 2) : 2};
-  for (int min_st : min_stages) {
-    if (p->stages) break;
-    for (int nbuf : {2, 1}) {
-      int st = 8;
-      auto total = [&](int k) {
-        return fixed_smem(p->nout, p->naux, nbuf, nbuf, k) + resident + k * stage;
-      };
-      while (st > min_st && total(st) > kMaxSmem) --st;
-      if (total(st) <= kMaxSmem) {
-        p->stages = st;
-        p->nbo = p->nba = nbuf;
-        p->smem = total(st);
-        break;
+    const int min_stages[2] = {p->halo ? (p->slide ? 5 : 3) : (p->stream ? 2 : 3),
+                               p->halo ? (p->slide ? 4 : 2) : 2};
+    for (int min_st : min_stages) {
+      if (p->stages) break;
+      for (int nbuf : {2, 1}) {
+        int st = 8;
+        auto total = [&](int k) {
+          return fixed_smem(p->nout, p->naux, nbuf, nbuf, k) + resident + k * stage;
+        };
+        while (st > min_st && total(st) > kMaxSmem) --st;
+        if (total(st) <= kMaxSmem) {
+          p->stages = st;
+          p->nbo = p->nba = nbuf;
+          p->smem = total(st);
+          break;
+        }
       }
+      if (p->stages) break;
     }
-    if (p->stages) break;
   }
   if (!p->stages) {
     *err = "tensor-core conv does not fit in shared memory";
@@ -1057,7 +1091,8 @@ static cudaError_t launch_typed(const TcPlan* p, const TcArgs& t, cudaStream_t s
   if (p->ms == 2) {
     switch (p->bn) {
       case 64: return launch_bn<T, T, 64, false, 2>(p, t, st);
-      default: return launch_bn<T, T, 128, false, 2>(p, t, st);
+      case 128: return launch_bn<T, T, 128, false, 2>(p, t, st);
+      default: return launch_bn<T, T, 256, false, 2>(p, t, st);
     }
   }
   switch (p->bn) {

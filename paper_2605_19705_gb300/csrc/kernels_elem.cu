@@ -384,9 +384,9 @@ __global__ void __launch_bounds__(256) prox_update_kernel(
       const float m = (float)mask[(size_t)b * hw + i % hw];
       const float o = (tau * m * y[base + i] + v) / (tau * m + 1.f);
       xn[base + i] = o;
-      const double d = (double)o - x[base + i];
-      ss += d * d;
-      sx += (double)x[base + i] * x[base + i];
+      const float d = o - x[base + i], xv = x[base + i];
+      ss += (double)(d * d);
+      sx += (double)(xv * xv);
     }
   }
   const double ts = block_sum(ss, red);
@@ -422,9 +422,9 @@ __global__ void __launch_bounds__(256) commit_update_kernel(
     for (int i = blockIdx.x * 256 + threadIdx.x; i < per_img; i += nblk * 256) {
       const float o = cand[base + i];
       xn[base + i] = o;
-      const double d = (double)o - x[base + i];
-      ss += d * d;
-      sx += (double)x[base + i] * x[base + i];
+      const float d = o - x[base + i], xv = x[base + i];
+      ss += (double)(d * d);
+      sx += (double)(xv * xv);
     }
   }
   const double ts = block_sum(ss, red);
@@ -526,7 +526,8 @@ int update_blocks_per_image(int per_img) {
 }
 
 // x_new = z - tau (grad f + lambda grad g) for running images (RED step at z,
-// Eq. ideq), with per-block FP64 partial sums of ||x_new - x||^2 and ||x||^2.
+// Eq. ideq), with per-block FP64 partial sums of ||x_new - x||^2 and ||x||^2
+// (squares of up to four elements formed in FP32, every sum above that in FP64).
 // Frozen images are left untouched.
 __global__ void __launch_bounds__(256) red_update_kernel(
     int per_img, const float* __restrict__ z, const float* __restrict__ gf,
@@ -555,20 +556,21 @@ __global__ void __launch_bounds__(256) red_update_kernel(
         o.z = zv.z - tau * (fv.z + lam * gv.z);
         o.w = zv.w - tau * (fv.w + lam * gv.w);
         o4[i] = o;
-        const double d0 = (double)o.x - xv.x, d1 = (double)o.y - xv.y;
-        const double d2 = (double)o.z - xv.z, d3 = (double)o.w - xv.w;
-        ss += d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3;
-        sx += (double)xv.x * xv.x + (double)xv.y * xv.y + (double)xv.z * xv.z +
-              (double)xv.w * xv.w;
+        // the four squares in FP32 (o - x is exact when the two are within a factor
+        // of two, as near a fixed point), accumulated in FP64: FP64 arithmetic per
+        // element would bound this pass on this GPU
+        const float d0 = o.x - xv.x, d1 = o.y - xv.y, d2 = o.z - xv.z, d3 = o.w - xv.w;
+        ss += (double)(d0 * d0 + d1 * d1 + (d2 * d2 + d3 * d3));
+        sx += (double)(xv.x * xv.x + xv.y * xv.y + (xv.z * xv.z + xv.w * xv.w));
       }
     } else {
       for (int i = blockIdx.x * 256 + threadIdx.x; i < per_img; i += nblk * 256) {
         float o = z[base + i] - tau * (gf[base + i] + lam * gg[base + i]);
         if (addv) o += addv[base + i];
         xn[base + i] = o;
-        const double d = (double)o - x[base + i];
-        ss += d * d;
-        sx += (double)x[base + i] * x[base + i];
+        const float d = o - x[base + i], xv = x[base + i];
+        ss += (double)(d * d);
+        sx += (double)(xv * xv);
       }
     }
   }

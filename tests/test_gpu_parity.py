@@ -654,3 +654,24 @@ def test_graph_cache_tracks_rician_sigma():
         assert not b.ideq_solve_graphed(ctx_h)
         torch.cuda.synchronize()
         assert torch.equal(xg, xh), sigma
+
+
+@pytest.mark.parametrize("name,over", [("C1a", dict(n=2, h=64, w=64)),
+                                       ("C1a", dict(n=1, h=136, w=200)),
+                                       ("C1a", dict(n=1)),
+                                       ("C3", dict(n=2, h=40, w=56))])
+def test_grad_reg_two_subtile_convs_match_oracle(name, over, monkeypatch):
+    """Tiles of two 128-row sub-tiles sharing each weight chunk (M = 256 per CTA),
+    forced on every conv that can take them (IDEQ_TC_MS=2): plain tiles with two
+    accumulator buffers (N <= 128) and with one (N = 256), and the streamed-halo
+    form with two row boxes per stage; odd tile counts leave a last sub-tile past
+    the batch (loaded as zeros, stored nowhere).  FP16, 2e-3 as for the other forms."""
+    monkeypatch.setenv("IDEQ_TC_MS", "2")
+    cfg, wl, net, ops, ys = setup(name, **over)
+    b = B()
+    ctx = ctx_for(cfg, wl, b.IDEQ_FP16)
+    z = np.random.default_rng(5).uniform(0, 1, ys.shape).astype(np.float32)
+    g = to_np(b.ideq_grad_reg(ctx, torch.tensor(z, device="cuda")))
+    for i in range(z.shape[0]):
+        ref, gv = nets.grad_g(net, z[i].astype(np.float64))
+        assert rel(g[i], ref) < 2e-3, (i, rel(g[i], ref))
