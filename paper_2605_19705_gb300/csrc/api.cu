@@ -38,6 +38,12 @@ struct ideq_ctx {
   double* reg_loss = nullptr;
   float* reg_dlam = nullptr;
   int reg_t = 0;
+  // implicit backward: dl/dx_hat scaled by a power of two to unit RMS (so that the
+  // 16-bit tangent passes of the adjoint iteration stay in their normal range) and
+  // its mean square; the results are scaled back exactly
+  float* adj_v = nullptr;
+  size_t adj_v_bytes = 0;
+  float* adj_ms = nullptr;
   std::string err;
   int* d_err = nullptr;       // device error flag of bounded waits
   int* h_running = nullptr;   // pinned
@@ -623,7 +629,7 @@ ideq_status ideq_destroy(ideq_ctx* ctx) {
   ctx->warm_plan.reset();
   ctx->warm_w.reset();
   for (float* p : {ctx->warm_m, ctx->warm_v, ctx->warm_g, ctx->reg_m, ctx->reg_v, ctx->reg_g,
-                   ctx->reg_cot, ctx->reg_dlam})
+                   ctx->reg_cot, ctx->reg_dlam, ctx->adj_v, ctx->adj_ms})
     if (p) cudaFree(p);
   if (ctx->reg_loss) cudaFree(ctx->reg_loss);
   ctx->w.reset();
@@ -871,6 +877,22 @@ ideq_status ideq_solve_backward(ideq_ctx* ctx, const ideq_operator* op, ideq_sha
   cudaStream_t st = ctx->stream;
   const int n = shape.n, per = ctx->sv_per;
   const size_t bytes = (size_t)n * per * 4;
+  if (ctx->adj_v_bytes < bytes) {
+    CK(cudaStreamSynchronize(st));
+    if (ctx->adj_v) cudaFree(ctx->adj_v);
+    ctx->adj_v = nullptr;
+    ctx->adj_v_bytes = 0;
+    CK(cudaMalloc((void**)&ctx->adj_v, bytes));
+    ctx->adj_v_bytes = bytes;
+  }
+  if (!ctx->adj_ms) CK(cudaMalloc((void**)&ctx->adj_ms, 16));
+  // v = dl/dx_hat times 2^-e, e = round(log2 RMS(v)): the adjoint equation and every
+  // gradient below are linear in v, so the results are multiplied back by 2^e
+  const long long numel = (long long)n * per;
+  CK(launch_dot(numel, dl_dx, dl_dx, 1.f / (float)numel, ctx->dot_part, ctx->adj_ms, st));
+  CK(launch_ldexp(numel, dl_dx, ctx->adj_ms, 0, -1, ctx->adj_v, st));
+  ctx->launches += 3;
+  const float* v = ctx->adj_v;
   // fixed point: N(xbar), r and grad g(xbar) with every t-chain cotangent kept
   CK(cudaMemcpyAsync(T->z, x_bar, bytes, cudaMemcpyDeviceToDevice, st));
   CK(launch_zero_d(n, ctx->gsum, st));
@@ -878,8 +900,8 @@ ideq_status ideq_solve_backward(ideq_ctx* ctx, const ideq_operator* op, ideq_sha
   CK(run_steps(T->tchain, ctx->d_err, st, &ctx->prof, &ctx->launches));
   // adjoint: u = J_R^T u + v with J_R = I - tau (H_f + lambda H_g) at xbar
   if (ap->mode == IDEQ_ADJ_IMPLICIT) {
-    CK(cudaMemcpyAsync(ctx->xb[0], dl_dx, bytes, cudaMemcpyDeviceToDevice, st));
-    CK(cudaMemcpyAsync(ctx->xb[1], dl_dx, bytes, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(ctx->xb[0], v, bytes, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(ctx->xb[1], v, bytes, cudaMemcpyDeviceToDevice, st));
     CK(launch_solver_init(n, ctx->sv, 0.f, st));
     for (int it = 0; it < ap->max_iter; ++it) {
       const int par = it & 1;
@@ -890,7 +912,7 @@ ideq_status ideq_solve_backward(ideq_ctx* ctx, const ideq_operator* op, ideq_sha
       CK(run_steps(T->pchain, ctx->d_err, st, &ctx->prof, &ctx->launches));
       CK(data_grad(ctx, od, shape, T->zd, nullptr, ctx->gf, ctx->tmp, ctx->sv.fsum));
       CK(launch_red_update(n, per, ctx->sv_nblk, T->zd, ctx->gf, T->hvp, uk, up, p->lambda,
-                           p->tau, ctx->sv.status, ctx->sv.part_s, ctx->sv.part_x, st, dl_dx));
+                           p->tau, ctx->sv.status, ctx->sv.part_s, ctx->sv.part_x, st, v));
       CK(launch_finalize(n, ctx->sv_nblk, ctx->sv, 1 - par, ap->beta, INFINITY, ap->tol,
                          ap->max_iter, 0.f, 1, 0, st));
       ctx->launches += 3;
@@ -902,7 +924,7 @@ ideq_status ideq_solve_backward(ideq_ctx* ctx, const ideq_operator* op, ideq_sha
     }
     CK(launch_gather_parity(n, per, ctx->sv.parity, ctx->xb[0], ctx->xb[1], ctx->ubuf, st));
   } else {
-    CK(cudaMemcpyAsync(ctx->ubuf, dl_dx, bytes, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(ctx->ubuf, v, bytes, cudaMemcpyDeviceToDevice, st));
     CK(launch_solver_init(n, ctx->sv, 0.f, st));
   }
   // dl/dlambda = -tau <u, grad g(xbar)>
@@ -913,7 +935,10 @@ ideq_status ideq_solve_backward(ideq_ctx* ctx, const ideq_operator* op, ideq_sha
   CK(run_steps(T->pchain, ctx->d_err, st, &ctx->prof, &ctx->launches));
   CK(cudaMemsetAsync(dl_dtheta, 0, ctx->w->nparams * 4, st));
   CK(T->run_wgrad(dl_dtheta, p->tau * p->lambda, true, st, &ctx->launches, ctx->d_err));
-  ctx->launches += 2;
+  // undo the scaling of v
+  CK(launch_ldexp(ctx->w->nparams, dl_dtheta, ctx->adj_ms, 0, 1, dl_dtheta, st));
+  CK(launch_ldexp(1, dl_dlambda, ctx->adj_ms, 0, 1, dl_dlambda, st));
+  ctx->launches += 4;
   if (info) CK(launch_fill_info(n, ctx->sv, *info, st));
   if ((s = check_timeout(ctx)) != IDEQ_OK) return s;
   if (ap->mode == IDEQ_ADJ_IMPLICIT) {
@@ -1057,9 +1082,15 @@ ideq_status ideq_warm_train_step(ideq_ctx* ctx, ideq_shape shape, const float* a
   if (!scr) return fail(ctx, IDEQ_ERR_NOMEM, "scratch");
   part = (double*)scr;
   CK(launch_mse_grad(numel, T->out_img, target, T->cot_img, part, loss, st));
+  // the reverse chain runs on 2^k dl/dx0, 2^k ~ numel (exact): the mean's 1/numel
+  // would leave 16-bit cotangents subnormal; the gradient is scaled back by 2^-k
+  int k = 0;
+  while ((1LL << (k + 1)) <= numel && k < 60) ++k;
+  CK(launch_ldexp(numel, T->cot_img, nullptr, k, 1, T->cot_img, st));
   CK(run_steps(T->tchain, ctx->d_err, st, &ctx->prof, &ctx->launches));
   CK(cudaMemsetAsync(ctx->warm_g, 0, W->nparams * 4, st));
   CK(T->run_wgrad(ctx->warm_g, 1.f, false, st, &ctx->launches, ctx->d_err));
+  CK(launch_ldexp(W->nparams, ctx->warm_g, nullptr, k, -1, ctx->warm_g, st));
   ctx->warm_t += 1;
   CK(launch_adam(W->nparams, W->master, ctx->warm_g, ctx->warm_m, ctx->warm_v, ctx->warm_t, lr,
                  0.9f, 0.999f, 1e-8f, st));

@@ -161,14 +161,29 @@ struct ImgMap {
   int nrun;
   uint32_t run;
   bool masked;
+  uint64_t tbl;  // n <= 16: 4-bit image index of the j-th computed image at bits 4j..4j+3
   IDEQ_DEV int img(int j) const {
     if (!masked) return j;
+    if (run < (1u << 16)) return (int)((tbl >> (4 * j)) & 15u);
     uint32_t m = run;
     for (int i = 0; i < j; ++i) m &= m - 1u;  // drop the j lowest set bits
     return __ffs(m) - 1;
   }
 };
 constexpr int kMaxMaskImages = 32;  // launches of more images compute every image
+
+// The 4-bit lookup table of ImgMap for the images 0..15 set in `run`.
+IDEQ_DEV uint64_t img_table(uint32_t run) {
+  uint64_t t = 0;
+  int j = 0;
+#pragma unroll
+  for (int b = 0; b < 16; ++b)
+    if ((run >> b) & 1u) {
+      t |= (uint64_t)b << (4 * j);
+      ++j;
+    }
+  return t;
+}
 
 // Tile t covers MS consecutive 128-row M-tiles (sub-tiles) and BN columns of the
 // computed images.  An M-tile index past the last one maps to an image index >= n,
@@ -342,7 +357,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   // their SMs.
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  const ImgMap im{masked ? __popc(run) : a.n, run, masked};
+  const ImgMap im{masked ? __popc(run) : a.n, run, masked, masked ? img_table(run) : 0ull};
   const int ntiles = ((im.nrun * a.tiles_h * a.tiles_w + MS - 1) / MS) * a.tiles_n;
   // this CTA's tiles: t_first + i * t_step, i < my_tiles (a contiguous range in
   // the halo form, a grid-strided sequence otherwise)
@@ -894,10 +909,9 @@ TcPlan* tc_plan_create(const ConvArgs& a, int op_dt, int epi_dt, std::string* er
     p->stream = !p->halo && op_dt != DT_FP8 && !p->nw && a.mode == CM_CONV3 && p->Wt == 128 &&
                 p->Ht == 1 && p->tiles_n == 1 && p->bn <= 128 && p->bn != 32 &&
                 tiling_override("IDEQ_TC_STREAM", 1) != 0;
-    // Two 128-row sub-tiles share each weight chunk (M = 256 per CTA): a third fewer
-    // operand bytes per MMA cycle into each SM, whose L2-to-shared-memory rate bounds
-    // the 128- to 512-channel layers, at the price of coarser tiles.  Taken where it
-    // lowers the number of waves over the SMs (IDEQ_TC_MS = 1 / 2 forces one / two).
+    // Two 128-row sub-tiles can share each weight chunk (M = 256 per CTA): a third
+    // fewer operand bytes per MMA cycle into each SM, at the price of coarser tiles,
+    // fewer ring stages and, for N = 256, a single accumulator buffer.
     p->ms = 1;
     {
       static int nsm = 0;
@@ -912,7 +926,10 @@ TcPlan* tc_plan_create(const ConvArgs& a, int op_dt, int epi_dt, std::string* er
       const long long tm = (long long)a.n * p->tiles_h * p->tiles_w;
       const long long w1 = (tm * p->tiles_n + nsm - 1) / nsm;
       const long long w2 = (((tm + 1) / 2) * p->tiles_n + nsm - 1) / nsm;
-      if (ms2_ok && (force_ms == 2 || (force_ms == 0 && w2 < w1))) p->ms = 2;
+      // measured on 8 x RGB 256^2 (C1a): the wave rule made the step slower (conv
+    // launches 51.8 vs 47.1 us on average), so two sub-tiles are used only when
+    // forced with IDEQ_TC_MS=2 (IDEQ_TC_MS=3 applies the wave rule)
+    if (ms2_ok && (force_ms == 2 || (force_ms == 3 && w2 < w1))) p->ms = 2;
     }
     // shared memory: ring depth and staging buffers, preferring a deep ring
     // (halo: >= 5 row boxes, three in use and two in flight; else >= 3 stages),

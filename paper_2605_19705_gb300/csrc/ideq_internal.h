@@ -242,6 +242,10 @@ int update_blocks_per_image(int per_img);
 cudaError_t launch_axpby(long long n, float a, const float* x, float b, const float* y,
                          float* out, cudaStream_t st);
 cudaError_t launch_zero_d(long long n, double* p, cudaStream_t st);
+// out = x * 2^(sign e) (exact; may run in place): e = round(log2 sqrt(*ms)) from a
+// device mean square ms (0 when ms is 0 or not finite), or e_host when ms is null
+cudaError_t launch_ldexp(long long n, const float* x, const float* ms, int e_host, int sign,
+                         float* out, cudaStream_t st);
 // *out = scale * <a, b> (n floats), FP64 accumulation; part holds >= 128 doubles.
 cudaError_t launch_dot(long long n, const float* a, const float* b, float scale, double* part,
                        float* out, cudaStream_t st);

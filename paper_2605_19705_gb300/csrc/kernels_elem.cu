@@ -4,6 +4,7 @@
 #include "ideq_internal.h"
 
 #include <cmath>
+#include <cstdlib>
 
 namespace ideq {
 
@@ -518,11 +519,19 @@ cudaError_t launch_rician_grad(int n, int per_img, const float* x, const float* 
   return cudaGetLastError();
 }
 
-// Blocks per image of the update kernels: one per 4096 values (256 threads x 16),
-// at most 64 (measured: a 4x finer split was slower on 8 x 3 x 256^2, 30 vs 26 us).
+// Blocks per image of the update kernels: one per kUpdateElems values, at most
+// kUpdateMaxBlocks (IDEQ_UPDATE_ELEMS / IDEQ_UPDATE_MAXBLK override them, read once).
+static int update_cfg(const char* name, int dflt) {
+  const char* v = std::getenv(name);
+  const int x = (v && *v) ? std::atoi(v) : dflt;
+  return x > 0 ? x : dflt;
+}
+
 int update_blocks_per_image(int per_img) {
-  const int b = (per_img + 256 * 16 - 1) / (256 * 16);
-  return std::max(1, std::min(b, 64));
+  static const int elems = update_cfg("IDEQ_UPDATE_ELEMS", 4096);
+  static const int maxb = update_cfg("IDEQ_UPDATE_MAXBLK", 64);
+  const int b = (per_img + elems - 1) / elems;
+  return std::max(1, std::min(b, maxb));
 }
 
 // x_new = z - tau (grad f + lambda grad g) for running images (RED step at z,
@@ -768,6 +777,27 @@ cudaError_t launch_gather_parity(int n, int per_img, const int* parity, const fl
   const long long total = (long long)n * per_img;
   const int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 8);
   gather_parity_kernel<<<blocks, 256, 0, st>>>(per_img, total, parity, b0, b1, out);
+  return cudaGetLastError();
+}
+
+// out = x * 2^(sign * e), an exact scaling: e = round(log2(rms)) from the mean
+// square *ms (device) when ms is given (0 when ms is zero or not finite), else e_host.
+__global__ void ldexp_kernel(long long n, const float* x, const float* ms, int e_host, int sign,
+                             float* out) {
+  int e = e_host;
+  if (ms) {
+    const float m = *ms;
+    e = (m > 0.f && isfinite(m)) ? (int)rintf(0.5f * log2f(m)) : 0;
+  }
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = ldexpf(x[i], sign * e);
+}
+
+cudaError_t launch_ldexp(long long n, const float* x, const float* ms, int e_host, int sign,
+                         float* out, cudaStream_t st) {
+  const int blocks = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152 * 8));
+  ldexp_kernel<<<blocks, 256, 0, st>>>(n, x, ms, e_host, sign, out);
   return cudaGetLastError();
 }
 
