@@ -463,6 +463,15 @@ def run_profile_steps(args):
     xt = torch.tensor(wl["x_true"], device="cuda")
     op, y = make_op_and_y(B, cfg, wl, ctx, xt, "cuda")
     xk = B.ideq_apply_AT(ctx, op, y)
+    if args.workload == "C3":  # the parameter gradient: JFB backward passes at A^T y
+        v = (2.0 * (xk - xt) / xk.numel()).contiguous()
+        g = torch.zeros(wl["weights"].size, device="cuda")
+        dl = torch.zeros(1, device="cuda")
+        p = B.make_params(cfg["lam"], cfg["tau"], cfg["beta"])
+        for _ in range(args.ncu_steps):
+            B.ideq_solve_backward(ctx, op, y, xk, v, p, B.make_adj(B.IDEQ_ADJ_JFB), g, dl)
+        torch.cuda.synchronize()
+        return
     xkm1 = xk.clone()
     params = B.make_params(cfg["lam"], cfg["tau"], cfg["beta"])
     for _ in range(args.ncu_steps):

@@ -956,17 +956,26 @@ TcPlan* tc_plan_create(const ConvArgs& a, int op_dt, int epi_dt, std::string* er
     }
     const int min_stages[2] = {p->halo ? (p->slide ? 5 : 3) : (p->stream ? 2 : 3),
                                p->halo ? (p->slide ? 4 : 2) : 2};
+    // staging depths (output buffers, auxiliary buffers), most preferred first: both
+    // double-buffered; then, where that does not fit, a deeper auxiliary prefetch
+    // before a second output buffer (an auxiliary box that is not yet loaded stalls
+    // the epilogue for a full load latency; IDEQ_TC_AUXDEEP=0 keeps nbo = nba)
+    static const int kStaging[][2] = {{2, 2}, {1, 2}, {1, 1}};
+    const bool aux_deep = tiling_override("IDEQ_TC_AUXDEEP", 1) != 0;
     for (int min_st : min_stages) {
       if (p->stages) break;
-      for (int nbuf : {2, 1}) {
+      for (const auto& sb : kStaging) {
+        const int nbo = sb[0], nba = p->naux > 0 ? sb[1] : sb[0];
+        if (!aux_deep && nbo != nba) continue;
         int st = 8;
         auto total = [&](int k) {
-          return fixed_smem(p->nout, p->naux, nbuf, nbuf, k) + resident + k * stage;
+          return fixed_smem(p->nout, p->naux, nbo, nba, k) + resident + k * stage;
         };
         while (st > min_st && total(st) > kMaxSmem) --st;
         if (total(st) <= kMaxSmem) {
           p->stages = st;
-          p->nbo = p->nba = nbuf;
+          p->nbo = nbo;
+          p->nba = nba;
           p->smem = total(st);
           break;
         }

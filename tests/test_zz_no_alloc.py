@@ -100,7 +100,9 @@ def test_noalloc_nullable_outputs_size_limit_and_unaligned_views():
     B.ideq_red_update_noalloc(zu, fu, gu, xu, ou, lam, tau, s_u, x_u)
     torch.cuda.synchronize()
     assert torch.allclose(ou, ref, rtol=1e-6, atol=1e-6)
-    assert torch.allclose(s_u, s_ref, rtol=1e-9) and torch.allclose(x_u, x_ref, rtol=1e-9)
+    # the float4 path forms squares of four elements in FP32 before the FP64 sums, the
+    # scalar path one element at a time: the sums agree to a few FP32 roundings
+    assert torch.allclose(s_u, s_ref, rtol=1e-6) and torch.allclose(x_u, x_ref, rtol=1e-6)
     # 2 * n * blocks > 65536 partial sums: refused before any launch
     n_big = 32769  # one block per one-value image
     t = torch.zeros(n_big, 1, 1, 1, device="cuda")
