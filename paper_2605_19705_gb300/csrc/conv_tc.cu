@@ -70,6 +70,7 @@ struct TcPlan {
       nba = 2, ms = 1;
   bool halo = false, slide = false, stream = false, nw = false;
   bool pdl = true;       // launched with programmatic stream serialisation
+  bool cg2 = false;      // CTA pairs with two-SM MMAs (clusters of two)
   bool split64 = false;  // 64-column tiles: epilogue halves on alternate tiles
   int Wt = 0, Ht = 0, tiles_w = 0, tiles_h = 0, tiles_n = 0, nk = 0, cpt = 0;
   dim3 grid;
@@ -260,7 +261,11 @@ IDEQ_DEV TileCoord halo_coord(const TcArgs& a, const ImgMap& im, int t) {
 
 // NW ("narrow rows"): the ring's K rows are 64 bytes (32 16-bit channels, for
 // layers of 32 input channels) under the 64-byte swizzle, two MMAs per K chunk.
-template <typename TA, typename T, int BN, bool HALO, int MS, bool NW>
+// CG2: tiles of 256 rows computed by the CTA pair of a cluster of two with
+// two-SM MMAs (tcgen05 .cta_group::2): each CTA loads its own 128 rows of A and
+// half of the N rows of B (per-SM operand bytes per MMA cycle fall by a third for
+// N = 256), the even CTA issues the MMAs, each CTA's epilogue drains its own rows.
+template <typename TA, typename T, int BN, bool HALO, int MS, bool NW, bool CG2 = false>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     conv_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                    const __grid_constant__ CUtensorMap tmB,
@@ -270,10 +275,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                    const __grid_constant__ CUtensorMap tmX1,
                    const __grid_constant__ CUtensorMap tmX2, TcArgs a) {
   static_assert(!HALO || MS == 1, "the halo form has one 128-row sub-tile");
+  static_assert(!CG2 || (!HALO && !NW && MS == 1 && sizeof(TA) == 2 && BN >= 128),
+                "CTA pairs: plain or streamed 16-bit tiles of 128 or 256 columns");
   static_assert(!NW || (MS == 1 && sizeof(TA) == 2), "narrow rows: 16-bit, one sub-tile");
   constexpr int RB = NW ? 64 : 128;     // bytes of one K row of a ring tile
   constexpr int A_TILE = 128 * RB;      // one 128-pixel A tile of one K chunk
-  constexpr int B_BYTES = BN * RB;
+  constexpr int B_BYTES = (CG2 ? BN / 2 : BN) * RB;  // this CTA's rows of B per K chunk
+  constexpr int MSUB = CG2 ? 2 : MS;    // 128-row sub-tiles per tile (CTA pair: one each)
   constexpr int KSTEPS = RB / 32;       // MMAs per K chunk (32 bytes of K each)
   constexpr int HBOX = NW ? HALO_BOX_NW : HALO_BOX;  // one halo row box
   // ring slot: the A (and B) boxes of one K chunk; in the halo form the three row
@@ -316,6 +324,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t drain = smem_u32(bars + 2 * ST + 4);
   const uint32_t bres = smem_u32(bars + 2 * ST + 5);
   const uint32_t auxbar0 = smem_u32(bars + 2 * ST + 6);  // [warp][MAX_NBA]
+  const uint32_t rank = CG2 ? cluster_ctarank() : 0u;  // 0: issues the pair's MMAs
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
       mbar_init(full0 + 8 * s, 1);
@@ -323,7 +332,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull0 + 8 * b, 1);
-      mbar_init(tempty0 + 8 * b, spl ? EPI_WARPS / 2 : EPI_WARPS);
+      // a pair's accumulator is released by the epilogue warps of both CTAs
+      mbar_init(tempty0 + 8 * b, CG2 ? 2 * EPI_WARPS : (spl ? EPI_WARPS / 2 : EPI_WARPS));
     }
     for (int b = 0; b < MAX_NBA * EPI_WARPS; ++b) mbar_init(auxbar0 + 8 * b, 1);
     mbar_init(drain, 1);
@@ -332,11 +342,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(tmem_slot)),
-                 "r"((uint32_t)(NACC * TCOLS))
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    if constexpr (CG2) {  // one warp of each CTA of the pair, collectively
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(tmem_slot)),
+                   "r"((uint32_t)(NACC * TCOLS))
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(tmem_slot)),
+                   "r"((uint32_t)(NACC * TCOLS))
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
   }
   // The images to compute: every warp reads the per-image skip flags into a
   // bitmask.  The flags are written only by kernels that are not convolutions (the
@@ -348,6 +366,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (masked) run = __ballot_sync(0xffffffffu, lane < a.n && a.skip[lane] == 0);
   tc_fence_before();
   __syncthreads();
+  if constexpr (CG2) cluster_sync();  // both CTAs' barriers initialised before any remote use
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   // Programmatic dependent launch: the set-up above may overlap the tail of the
@@ -358,19 +377,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const ImgMap im{masked ? __popc(run) : a.n, run, masked, masked ? img_table(run) : 0ull};
-  const int ntiles = ((im.nrun * a.tiles_h * a.tiles_w + MS - 1) / MS) * a.tiles_n;
+  const int ntiles = ((im.nrun * a.tiles_h * a.tiles_w + MSUB - 1) / MSUB) * a.tiles_n;
   // this CTA's tiles: t_first + i * t_step, i < my_tiles (a contiguous range in
-  // the halo form, a grid-strided sequence otherwise)
+  // the halo form, a grid-strided sequence otherwise; a CTA pair shares its tiles)
   int t_first, t_step, my_tiles;
   if (HALO && a.slide) {
     t_first = (int)(((long long)blockIdx.x * ntiles) / gridDim.x);
     my_tiles = (int)(((long long)(blockIdx.x + 1) * ntiles) / gridDim.x) - t_first;
     t_step = 1;
   } else {
-    t_first = blockIdx.x;
-    t_step = gridDim.x;
-    my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int unit = CG2 ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+    const int units = CG2 ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+    t_first = unit;
+    t_step = units;
+    my_tiles = unit < ntiles ? (ntiles - 1 - unit) / units + 1 : 0;
   }
+  const int tsub0 = CG2 ? (int)rank : 0;  // this CTA's sub-tile of a pair tile
+  const int bn_off = CG2 ? (int)rank * (BN / 2) : 0;  // this CTA's first row of B
 
   if (warp == 0) {
     if (lane == 0) {
@@ -427,53 +450,75 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             ok = false;
             break;
           }
-          mbar_expect_tx(full0 + 8 * s, STAGE_TX);
+          if (rank == 0) mbar_expect_tx(full0 + 8 * s, (CG2 ? 2u : 1u) * STAGE_TX);
           const int dy = kc / a.cpt, c = kc - dy * a.cpt;
+          if constexpr (CG2) {  // both halves of the stage complete on the even CTA's barrier
+            const uint32_t fb = mapa_shared(full0 + 8 * s, 0);
+            const TileCoord sc = tile_coord(a, im, t, BN, MSUB, tsub0);
+            tma_load_4d_cg2(smem_u32(sA + s * A_STAGE), &tmA, c * KCH, sc.w0 - 1, sc.h0 + dy - 1,
+                            sc.img, fb);
+            for (int dx = 0; dx < 3; ++dx)
+              tma_load_2d_cg2(smem_u32(sB + s * B_STAGE + dx * B_BYTES), &tmB,
+                              ((3 * dy + dx) * a.cpt + c) * KCH, sc.n0 + bn_off, fb);
+          } else {
 #pragma unroll
-          for (int sub = 0; sub < MS; ++sub) {  // one row box per 128-pixel sub-tile
-            const TileCoord sc = tile_coord(a, im, t, BN, MS, sub);
-            tma_load_4d(smem_u32(sA + s * A_STAGE + sub * HALO_BOX), &tmA, c * KCH, sc.w0 - 1,
-                        sc.h0 + dy - 1, sc.img, full0 + 8 * s);
+            for (int sub = 0; sub < MS; ++sub) {  // one row box per 128-pixel sub-tile
+              const TileCoord sc = tile_coord(a, im, t, BN, MSUB, sub + tsub0);
+              tma_load_4d(smem_u32(sA + s * A_STAGE + sub * HALO_BOX), &tmA, c * KCH, sc.w0 - 1,
+                          sc.h0 + dy - 1, sc.img, full0 + 8 * s);
+            }
+            const TileCoord tc = tile_coord(a, im, t, BN, MSUB, tsub0);
+            for (int dx = 0; dx < 3; ++dx)
+              tma_load_2d(smem_u32(sB + s * B_STAGE + dx * B_BYTES), &tmB,
+                          ((3 * dy + dx) * a.cpt + c) * KCH, tc.n0, full0 + 8 * s);
           }
-          const TileCoord tc = tile_coord(a, im, t, BN, MS, 0);
-          for (int dx = 0; dx < 3; ++dx)
-            tma_load_2d(smem_u32(sB + s * B_STAGE + dx * B_BYTES), &tmB,
-                        ((3 * dy + dx) * a.cpt + c) * KCH, tc.n0, full0 + 8 * s);
           ++g;
         }
       }
       for (int i = 0; i < my_tiles && ok && !HALO && !STREAM; ++i) {
         const int t = t_first + i * t_step;
-        const TileCoord tc = tile_coord(a, im, t, BN, MS, 0);
+        const TileCoord tc = tile_coord(a, im, t, BN, MSUB, tsub0);
         for (int kc = 0; kc < a.nk; ++kc) {
           const int s = g % ST, j = g / ST;
           if (j > 0 && !mbar_wait(empty0 + 8 * s, (j - 1) & 1, a.err, 1)) {
             ok = false;
             break;
           }
-          mbar_expect_tx(full0 + 8 * s, STAGE_TX);
+          if (rank == 0) mbar_expect_tx(full0 + 8 * s, (CG2 ? 2u : 1u) * STAGE_TX);
+          // a CTA pair's halves of the stage complete on the even CTA's barrier
+          const uint32_t fb = CG2 ? mapa_shared(full0 + 8 * s, 0) : full0 + 8 * s;
           const uint32_t dA = smem_u32(sA + s * A_STAGE);
           {
             const uint32_t dB = smem_u32(sB + s * B_STAGE);
 #pragma unroll
             for (int sub = 0; sub < MS; ++sub) {
-              const TileCoord sc = sub == 0 ? tc : tile_coord(a, im, t, BN, MS, sub);
+              const TileCoord sc = sub == 0 ? tc : tile_coord(a, im, t, BN, MSUB, sub + tsub0);
               const uint32_t dAs = dA + sub * A_TILE;
               if (a.mode == CM_DOWN) {
                 const int k0 = kc * KCH;
                 const int di = k0 / (2 * a.Cin), rem = k0 - di * 2 * a.Cin;
-                tma_load_5d(dAs, &tmA, rem, sc.w0, di, sc.h0, sc.img, full0 + 8 * s);
+                if (CG2)
+                  tma_load_5d_cg2(dAs, &tmA, rem, sc.w0, di, sc.h0, sc.img, fb);
+                else
+                  tma_load_5d(dAs, &tmA, rem, sc.w0, di, sc.h0, sc.img, fb);
               } else {
                 int tap = 4, c0 = kc * KCH;
                 if (a.mode == CM_CONV3) {
                   tap = kc / a.cpt;
                   c0 = (kc - tap * a.cpt) * KCH;
                 }
-                tma_load_4d(dAs, &tmA, c0, sc.w0 + tap % 3 - 1, sc.h0 + tap / 3 - 1, sc.img,
-                            full0 + 8 * s);
+                if (CG2)
+                  tma_load_4d_cg2(dAs, &tmA, c0, sc.w0 + tap % 3 - 1, sc.h0 + tap / 3 - 1,
+                                  sc.img, fb);
+                else
+                  tma_load_4d(dAs, &tmA, c0, sc.w0 + tap % 3 - 1, sc.h0 + tap / 3 - 1, sc.img,
+                              fb);
               }
             }
-            tma_load_2d(dB, &tmB, kc * KCH, tc.n0, full0 + 8 * s);
+            if (CG2)
+              tma_load_2d_cg2(dB, &tmB, kc * KCH, tc.n0 + bn_off, fb);
+            else
+              tma_load_2d(dB, &tmB, kc * KCH, tc.n0, fb);
           }
           ++g;
         }
@@ -484,9 +529,62 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int i = first; i < g; ++i) {
         const int s = i % ST, j = i / ST;
         if (ok) ok = mbar_wait(empty0 + 8 * s, j & 1, a.err, 2);
-        if (!ok) mbar_wait(full0 + 8 * s, j & 1, a.err, 2);  // our own copies in flight
+        // our own copies in flight (a CTA pair's are all counted on the even CTA's
+        // barriers, which it waits for here before the pair's final cluster barrier)
+        if (!ok && rank == 0) mbar_wait(full0 + 8 * s, j & 1, a.err, 2);
       }
       if (HALO && !ok) mbar_wait(bres, 0, a.err, 2);
+    }
+  } else if (CG2 && warp == 1) {
+    if (lane == 0 && rank == 0) {
+      // even CTA of a pair: two-SM MMAs, M = 256 (128 rows of A from each CTA),
+      // N = BN (half of B from each CTA); commits release both CTAs' stages and
+      // hand both CTAs their accumulator
+      constexpr uint32_t idesc = umma_idesc_16(256, BN, Fmt<TA>::v);
+      bool ok = true;
+      int g = 0;
+      for (int lt = 0; lt < my_tiles && ok; ++lt) {
+        const int b = lt % NACC, u = lt / NACC;
+        if (u > 0 && !mbar_wait(tempty0 + 8 * b, (u - 1) & 1, a.err, 5)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t td = tmem + (uint32_t)(b * TCOLS);
+        const int nkc = STREAM ? 3 * a.cpt : a.nk;
+        for (int kc = 0; kc < nkc; ++kc) {
+          const int s = g % ST, j = g / ST;
+          if (!mbar_wait(full0 + 8 * s, j & 1, a.err, 3)) {  // both CTAs' halves
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          if (STREAM) {
+            const uint32_t abox = smem_u32(sA + s * A_STAGE);
+#pragma unroll 1
+            for (int dx = 0; dx < 3; ++dx) {
+              const uint64_t bd = umma_desc_sw128(smem_u32(sB + s * B_STAGE + dx * B_BYTES));
+              const uint64_t ad = umma_desc_sw128_rows(abox, dx);
+#pragma unroll
+              for (int kk = 0; kk < KSTEPS; ++kk)
+                umma_cg2(td, ad + 2 * kk, bd + 2 * kk, idesc, (kc | dx | kk) != 0 ? 1u : 0u);
+            }
+          } else {
+            const uint64_t bd = umma_desc_sw128(smem_u32(sB + s * B_STAGE));
+            const uint64_t ad = umma_desc_sw128(smem_u32(sA + s * A_STAGE));
+#pragma unroll
+            for (int kk = 0; kk < KSTEPS; ++kk)
+              umma_cg2(td, ad + 2 * kk, bd + 2 * kk, idesc, (kc | kk) != 0 ? 1u : 0u);
+          }
+          umma_commit_cg2_both(empty0 + 8 * s);
+          ++g;
+        }
+        if (ok) umma_commit_cg2_both(tfull0 + 8 * b);
+      }
+      if (!ok) {  // let every issued MMA finish before TMEM is released
+        umma_commit_cg2(drain);
+        mbar_wait(drain, 0, a.err, 6);
+      }
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -626,7 +724,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(tempty0 + 8 * b);
-        const TileCoord tc = HALO ? halo_coord(a, im, t) : tile_coord(a, im, t, BN, MS, 0);
+        const TileCoord tc = HALO ? halo_coord(a, im, t) : tile_coord(a, im, t, BN, MSUB, tsub0);
         const int m = 32 * q + lane;
         const int x = tc.w0 + m % a.Wt, y = tc.h0 + m / a.Wt;
         double ssq = 0.0;
@@ -675,7 +773,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       auto aux_load = [&](int k) {
         const int i = k / npan, r = k - i * npan, sub = r / nper, p = r - sub * nper;
         const int t = t_first + (lt0 + i * lstep) * t_step;
-        const TileCoord nc = HALO ? halo_coord(a, im, t) : tile_coord(a, im, t, BN, MS, sub);
+        const TileCoord nc = HALO ? halo_coord(a, im, t) : tile_coord(a, im, t, BN, MSUB, sub + tsub0);
         const int buf = k % a.nba;
         const uint32_t bar = xbar + 8 * buf;
         mbar_expect_tx(bar, (uint32_t)(a.naux * WBOX));
@@ -710,11 +808,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           if (pp == npan - 1) {  // last read of this accumulator: hand it back
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(tempty0 + 8 * b);
+            if (lane == 0) {
+              if (CG2)  // to the CTA that issues the pair's MMAs
+                mbar_arrive_remote(mapa_shared(tempty0 + 8 * b, 0));
+              else
+                mbar_arrive(tempty0 + 8 * b);
+            }
           }
           if constexpr (sizeof(TA) == 1) {  // FP8 operands: undo the two scales
             const float sa = *a.a_scale;
-            const float* ws = a.w_scale + tile_coord(a, im, t, BN, MS, sub).n0 + PW * p + colh;
+            const float* ws = a.w_scale + tile_coord(a, im, t, BN, MSUB, sub + tsub0).n0 + PW * p + colh;
 #pragma unroll
             for (int i = 0; i < 32; ++i) v[i] *= sa * __ldg(ws + i);
           }
@@ -723,7 +826,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           fence_async_smem();
           __syncwarp();
           if (lane == 0) {
-            const TileCoord tc = HALO ? halo_coord(a, im, t) : tile_coord(a, im, t, BN, MS, sub);
+            const TileCoord tc = HALO ? halo_coord(a, im, t) : tile_coord(a, im, t, BN, MSUB, sub + tsub0);
             for (int i = 0; i < a.nout; ++i)
               epi_tma(true, a, tmO[i], ob + (uint32_t)(i * WBOX), tc, q,
                       tc.n0 + PW * p + colh, 0);
@@ -743,11 +846,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
+  // a pair's CTAs leave together: the even CTA's MMAs read the odd CTA's shared
+  // memory and its commits arrive on the odd CTA's barriers until the last tile
+  if constexpr (CG2) cluster_sync();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"((uint32_t)(NACC * TCOLS))
-                 : "memory");
+    if constexpr (CG2)
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                   "r"((uint32_t)(NACC * TCOLS))
+                   : "memory");
+    else
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                   "r"((uint32_t)(NACC * TCOLS))
+                   : "memory");
   }
 }
 
@@ -931,12 +1042,19 @@ TcPlan* tc_plan_create(const ConvArgs& a, int op_dt, int epi_dt, std::string* er
     // forced with IDEQ_TC_MS=2 (IDEQ_TC_MS=3 applies the wave rule)
     if (ms2_ok && (force_ms == 2 || (force_ms == 3 && w2 < w1))) p->ms = 2;
     }
+    // CTA pairs with two-SM MMAs for the 128- and 256-column 16-bit tiles of the
+    // plain and streamed forms, when IDEQ_TC_CG2=1.  Measured on 8 x RGB 256^2
+    // (C1a): no faster than single-CTA tiles (conv launches of one iteration
+    // 3383 vs 3355 us), so single-CTA tiles stay the default.
+    p->cg2 = !p->halo && !p->nw && op_dt != DT_FP8 && (p->bn == 128 || p->bn == 256) &&
+             p->ms == 1 && !img && tiling_override("IDEQ_TC_CG2", 0) == 1;
+    const size_t bcta = p->cg2 ? (size_t)p->bn / 2 : (size_t)p->bn;  // rows of B per CTA
     // shared memory: ring depth and staging buffers, preferring a deep ring
     // (halo: >= 5 row boxes, three in use and two in flight; else >= 3 stages),
     // then double-buffered staging
     const size_t stage = p->halo     ? (size_t)(p->slide ? 1 : 3) * (p->nw ? HALO_BOX_NW : HALO_BOX)
-                         : p->stream ? (size_t)p->ms * HALO_BOX + 3 * (size_t)p->bn * 128
-                                     : ((size_t)p->ms * 128 + (size_t)p->bn) * RB;
+                         : p->stream ? (size_t)p->ms * HALO_BOX + 3 * bcta * 128
+                                     : ((size_t)p->ms * 128 + bcta) * RB;
     const size_t resident = p->halo ? bres : 0;
     p->stages = 0;
     // short K (depth-to-space, stride-2 and 1x1 layers): the epilogue paces the
@@ -997,8 +1115,12 @@ TcPlan* tc_plan_create(const ConvArgs& a, int op_dt, int epi_dt, std::string* er
       if (sms <= 0) sms = 148;
     }
     const long long tiles_m = (long long)a.n * p->tiles_h * p->tiles_w;
-    const long long tiles = ((tiles_m + p->ms - 1) / p->ms) * p->tiles_n;
-    p->grid = dim3((unsigned)std::min<long long>(tiles, sms), 1, 1);
+    const int per = p->cg2 ? 2 : p->ms;  // 128-row sub-tiles per tile
+    const long long tiles = ((tiles_m + per - 1) / per) * p->tiles_n;
+    if (p->cg2)  // one CTA pair per tile, pairs on neighbouring SMs
+      p->grid = dim3((unsigned)(2 * std::min<long long>(tiles, sms / 2)), 1, 1);
+    else
+      p->grid = dim3((unsigned)std::min<long long>(tiles, sms), 1, 1);
   }
   auto map_type = [](int d) {
     return d == DT_FP8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
@@ -1030,7 +1152,8 @@ TcPlan* tc_plan_create(const ConvArgs& a, int op_dt, int epi_dt, std::string* er
     const int K = a.K();
     cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)N};
     cuuint64_t strides[1] = {(cuuint64_t)K * es};
-    cuuint32_t box[2] = {(cuuint32_t)KCH, (cuuint32_t)p->bn};
+    // a CTA of a pair loads half of the tile's rows of B
+    cuuint32_t box[2] = {(cuuint32_t)KCH, (cuuint32_t)(p->cg2 ? p->bn / 2 : p->bn)};
     ok = ok && encode(enc, &p->tmB, dt, 2, a.wB, dims, strides, box, swz);
   }
   const void* outs[2] = {a.out, a.out2};
@@ -1054,11 +1177,11 @@ TcPlan* tc_plan_create(const ConvArgs& a, int op_dt, int epi_dt, std::string* er
 
 void tc_plan_destroy(TcPlan* p) { delete p; }
 
-template <typename TA, typename T, int BN, bool HALO, int MS, bool NW = false>
+template <typename TA, typename T, int BN, bool HALO, int MS, bool NW = false, bool CG2 = false>
 static cudaError_t launch_bn(const TcPlan* p, const TcArgs& ta, cudaStream_t st) {
   static bool attr_set = false;  // per instantiation; set before first launch
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<TA, T, BN, HALO, MS, NW>,
+    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<TA, T, BN, HALO, MS, NW, CG2>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kMaxSmem);
     if (e != cudaSuccess) return e;
@@ -1069,12 +1192,19 @@ static cudaError_t launch_bn(const TcPlan* p, const TcArgs& ta, cudaStream_t st)
   cfg.blockDim = dim3(TC_THREADS, 1, 1);
   cfg.dynamicSmemBytes = p->smem;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = p->pdl ? 1 : 0;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, conv_tc_kernel<TA, T, BN, HALO, MS, NW>, p->tmA, p->tmB,
+  if (CG2) {  // clusters of two CTAs (a portable cluster size)
+    attr[1].id = cudaLaunchAttributeClusterDimension;
+    attr[1].val.clusterDim.x = 2;
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = 1;
+    cfg.numAttrs = 2;
+  }
+  return cudaLaunchKernelEx(&cfg, conv_tc_kernel<TA, T, BN, HALO, MS, NW, CG2>, p->tmA, p->tmB,
                             p->tmO[0], p->tmO[1], p->tmX[0], p->tmX[1], p->tmX[2], ta);
 }
 
@@ -1113,6 +1243,10 @@ static cudaError_t launch_typed(const TcPlan* p, const TcArgs& t, cudaStream_t s
       case 64: return launch_bn<T, T, 64, true, 1>(p, t, st);
       default: return launch_bn<T, T, 128, true, 1>(p, t, st);
     }
+  }
+  if (p->cg2) {  // CTA pairs: plain or streamed tiles of 128 or 256 columns
+    if (p->bn == 128) return launch_bn<T, T, 128, false, 1, false, true>(p, t, st);
+    return launch_bn<T, T, 256, false, 1, false, true>(p, t, st);
   }
   if (p->ms == 2) {
     switch (p->bn) {

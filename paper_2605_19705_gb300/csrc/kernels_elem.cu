@@ -536,7 +536,7 @@ int update_blocks_per_image(int per_img) {
 
 // x_new = z - tau (grad f + lambda grad g) for running images (RED step at z,
 // Eq. ideq), with per-block FP64 partial sums of ||x_new - x||^2 and ||x||^2
-// (squares of up to four elements formed in FP32, every sum above that in FP64).
+// (squares summed in FP32 over at most 16 elements, every sum above that in FP64).
 // Frozen images are left untouched.
 __global__ void __launch_bounds__(256) red_update_kernel(
     int per_img, const float* __restrict__ z, const float* __restrict__ gf,
@@ -557,6 +557,12 @@ __global__ void __launch_bounds__(256) red_update_kernel(
       const float4* g4 = (const float4*)(gg + base);
       const float4* x4 = (const float4*)(x + base);
       float4* o4 = (float4*)(xn + base);
+      // squares summed in FP32 over at most 16 elements (four float4 iterations;
+      // o - x is exact when the two are within a factor of two, as near a fixed
+      // point), every sum above that in FP64: FP64 arithmetic per element would
+      // bound this pass on this GPU
+      float s32 = 0.f, x32 = 0.f;
+      int cnt = 0;
       for (int i = blockIdx.x * 256 + threadIdx.x; i < n4; i += nblk * 256) {
         const float4 zv = z4[i], fv = f4[i], gv = g4[i], xv = x4[i];
         float4 o;
@@ -565,13 +571,18 @@ __global__ void __launch_bounds__(256) red_update_kernel(
         o.z = zv.z - tau * (fv.z + lam * gv.z);
         o.w = zv.w - tau * (fv.w + lam * gv.w);
         o4[i] = o;
-        // the four squares in FP32 (o - x is exact when the two are within a factor
-        // of two, as near a fixed point), accumulated in FP64: FP64 arithmetic per
-        // element would bound this pass on this GPU
         const float d0 = o.x - xv.x, d1 = o.y - xv.y, d2 = o.z - xv.z, d3 = o.w - xv.w;
-        ss += (double)(d0 * d0 + d1 * d1 + (d2 * d2 + d3 * d3));
-        sx += (double)(xv.x * xv.x + xv.y * xv.y + (xv.z * xv.z + xv.w * xv.w));
+        s32 += d0 * d0 + d1 * d1 + (d2 * d2 + d3 * d3);
+        x32 += xv.x * xv.x + xv.y * xv.y + (xv.z * xv.z + xv.w * xv.w);
+        if (++cnt == 4) {
+          ss += (double)s32;
+          sx += (double)x32;
+          s32 = x32 = 0.f;
+          cnt = 0;
+        }
       }
+      ss += (double)s32;
+      sx += (double)x32;
     } else {
       for (int i = blockIdx.x * 256 + threadIdx.x; i < per_img; i += nblk * 256) {
         float o = z[base + i] - tau * (gf[base + i] + lam * gg[base + i]);

@@ -32,7 +32,7 @@
 namespace ideq {
 
 constexpr int WG_THREADS = 192;  // producer, MMA issuer, 4 epilogue warps
-constexpr int WG_BOX = 8192;     // one 64 x 64 16-bit box: 64 rows of 128 B
+constexpr int WG_BOX = 8192;     // one 64-pixel x 64-channel 16-bit box: 64 rows of 128 B
 constexpr int WG_STAGES_MAX = 6;
 
 struct WgTcArgs {
@@ -40,6 +40,9 @@ struct WgTcArgs {
   int Cin, N, K;         // N = Cout, K = 9 Cin (CM_CONV3) or 4 Cin (CM_DOWN)
   int Wt, Ht, tiles_w, tiles_h, nbox;  // 64-pixel boxes (Wt x Ht) of the output grid
   int bn, mt, nt, splits, stages;
+  // channels per box of A (input) and B (cotangent): 64 (128-byte rows, 128-byte
+  // swizzle) or 32 (64-byte rows, 64-byte swizzle, for 32-channel sides)
+  int ca, cb;
   float* part;           // [splits][N][K]
   int* err;
 };
@@ -52,23 +55,25 @@ struct WgTcPlan {
   int dt;
 };
 
-// MN-major shared-memory descriptor, 128-byte swizzle: a K step of 8 rows is one
-// 1024-byte swizzle atom (stride byte offset), consecutive 64-element MN blocks
-// are one box (WG_BOX bytes) apart (leading byte offset).
-IDEQ_DEV uint64_t umma_desc_mn_sw128(uint32_t saddr) {
+// MN-major shared-memory descriptor: rows of `c` 16-bit MN elements (64: 128-byte
+// rows under the 128-byte swizzle; 32: 64-byte rows under the 64-byte swizzle); a K
+// step of 8 rows is one swizzle atom (stride byte offset), consecutive MN blocks of
+// c elements are one box (64 rows) apart (leading byte offset).
+IDEQ_DEV uint64_t umma_desc_mn(uint32_t saddr, int c) {
+  const uint32_t row = 2u * (uint32_t)c, box = 64u * row;
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)((uint32_t)WG_BOX >> 4) << 16;
-  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)(box >> 4) << 16;
+  d |= (uint64_t)((8u * row) >> 4) << 32;
   d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
+  d |= (uint64_t)(c == 64 ? 2 : 4) << 61;
   return d;
 }
 
 // A (input) box j of M tile mt: the (tap, first channel) it starts at.
 IDEQ_DEV void wg_a_box(const WgTcArgs& a, int mt, int j, int* tap, int* c0) {
   const int taps = a.mode == CM_CONV3 ? 9 : 4;
-  const int m0 = mt * 128 + 64 * j;
+  const int m0 = mt * 128 + a.ca * j;
   int t = m0 / a.Cin;
   if (t >= taps) t = taps - 1;  // past the last tap (9 taps of 64 channels): rows never stored
   *tap = t;
@@ -83,8 +88,10 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int ST = a.stages;
-  const int nb = a.bn / 64;                 // cotangent boxes per stage
-  const int STAGE = (2 + nb) * WG_BOX;
+  const int na = 128 / a.ca;                // input boxes per stage (128 M rows)
+  const int nb = a.bn / a.cb;               // cotangent boxes per stage
+  const int ABOX = 128 * a.ca, BBOX = 128 * a.cb;  // bytes of one box (64 rows)
+  const int STAGE = na * ABOX + nb * BBOX;   // = 16 KB + BN x 128 B
   uint64_t* bars = (uint64_t*)(smem + ST * STAGE);
   uint32_t* tmem_slot = (uint32_t*)(bars + 2 * ST + 5);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -94,7 +101,7 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
   const int units = a.splits * a.nt * a.mt;
   const int my_units =
       (int)blockIdx.x < units ? (units - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-  const uint32_t tcols = (uint32_t)(2 * a.bn);  // 128, 256 or 512
+  const uint32_t tcols = (uint32_t)(2 * a.bn);  // 64, 128, 256 or 512
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
@@ -145,8 +152,8 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
         int sp, nti, mti, q0, q1;
         unit_of(i, &sp, &nti, &mti);
         box_range(sp, &q0, &q1);
-        int tap[2], c0[2];
-        for (int j = 0; j < 2; ++j) wg_a_box(a, mti, j, &tap[j], &c0[j]);
+        int tap[4], c0[4];
+        for (int j = 0; j < na; ++j) wg_a_box(a, mti, j, &tap[j], &c0[j]);
         for (int q = q0; q < q1; ++q) {
           const int s = g % ST, ph = g / ST;
           if (ph > 0 && !mbar_wait(empty0 + 8 * s, (ph - 1) & 1, a.err, 21)) {
@@ -158,16 +165,16 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
           const int y0 = (rr / a.tiles_w) * a.Ht, x0 = (rr % a.tiles_w) * a.Wt;
           mbar_expect_tx(full0 + 8 * s, (uint32_t)(STAGE));
           const uint32_t dst = smem_u32(smem + s * STAGE);
-          for (int j = 0; j < 2; ++j) {
+          for (int j = 0; j < na; ++j) {
             if (a.mode == CM_CONV3)
-              tma_load_4d(dst + j * WG_BOX, &tmA, c0[j], x0 + tap[j] % 3 - 1, y0 + tap[j] / 3 - 1,
+              tma_load_4d(dst + j * ABOX, &tmA, c0[j], x0 + tap[j] % 3 - 1, y0 + tap[j] / 3 - 1,
                           img, full0 + 8 * s);
             else  // stride-2 2x2: tap q = (di, dj) of the fine grid
-              tma_load_5d(dst + j * WG_BOX, &tmA, (tap[j] & 1) * a.Cin + c0[j], x0, tap[j] >> 1,
+              tma_load_5d(dst + j * ABOX, &tmA, (tap[j] & 1) * a.Cin + c0[j], x0, tap[j] >> 1,
                           y0, img, full0 + 8 * s);
           }
           for (int j = 0; j < nb; ++j)
-            tma_load_4d(dst + (2 + j) * WG_BOX, &tmB, nti * a.bn + 64 * j, x0, y0, img,
+            tma_load_4d(dst + na * ABOX + j * BBOX, &tmB, nti * a.bn + a.cb * j, x0, y0, img,
                         full0 + 8 * s);
           ++g;
         }
@@ -207,8 +214,9 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
           const uint32_t base = smem_u32(smem + s * STAGE);
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {  // 16 pixels (two 8-row atoms) per MMA
-            const uint64_t ad = umma_desc_mn_sw128(base + 2048u * kk);
-            const uint64_t bd = umma_desc_mn_sw128(base + 2 * WG_BOX + 2048u * kk);
+            const uint64_t ad = umma_desc_mn(base + (uint32_t)(32 * a.ca * kk), a.ca);
+            const uint64_t bd =
+                umma_desc_mn(base + (uint32_t)(na * ABOX + 32 * a.cb * kk), a.cb);
             umma<T>(td, ad, bd, idesc, (q > q0 || kk > 0) ? 1u : 0u);
           }
           umma_commit(empty0 + 8 * s);
@@ -262,20 +270,25 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
 // ------------------------------------------------------------------ host side
 
 static bool wg_encode(CUtensorMap* m, CUtensorMapDataType dt, int rank, const void* base,
-                      const cuuint64_t* dims, const cuuint64_t* strides, const cuuint32_t* box) {
+                      const cuuint64_t* dims, const cuuint64_t* strides, const cuuint32_t* box,
+                      bool narrow) {
   auto enc = tensor_map_encoder();
   if (!enc) return false;
   cuuint32_t es[5] = {1, 1, 1, 1, 1};
   return enc(m, dt, rank, const_cast<void*>(base), dims, strides, box, es,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_INTERLEAVE_NONE,
+             narrow ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
+
+// channels of one operand box: 64, or 32 for a side of exactly 32 channels
+static int wg_box_ch(int c) { return c % 64 == 0 ? 64 : 32; }
 
 bool wgrad_tc_supported(const ConvArgs& a, int in_dt, int cot_dt) {
   if (in_dt != cot_dt || (in_dt != DT_BF16 && in_dt != DT_F16)) return false;
   if (a.in_nchw || a.out_nchw || a.outmap != OM_IDENT) return false;
   if (a.mode != CM_CONV3 && a.mode != CM_DOWN) return false;
-  if (a.Cin % 64 != 0 || a.Cout % 64 != 0) return false;
+  if (!(a.Cin % 64 == 0 || a.Cin == 32) || !(a.Cout % 64 == 0 || a.Cout == 32)) return false;
   if (a.M() == 0) return false;
   return true;
 }
@@ -283,7 +296,8 @@ bool wgrad_tc_supported(const ConvArgs& a, int in_dt, int cot_dt) {
 static int wg_bn(int N) {
   if (N % 256 == 0) return 256;
   if (N % 128 == 0) return 128;
-  return 64;
+  if (N % 64 == 0) return 64;
+  return 32;
 }
 
 int wgrad_tc_splits(const ConvArgs& a) {
@@ -325,7 +339,9 @@ WgTcPlan* wgrad_tc_plan_create(const ConvArgs& a, int dt, const void* in, const 
   t.nt = t.N / t.bn;
   t.splits = wgrad_tc_splits(a);
   t.part = part;
-  const size_t stage = (size_t)(2 + t.bn / 64) * WG_BOX;
+  t.ca = wg_box_ch(a.Cin);
+  t.cb = wg_box_ch(a.Cout);
+  const size_t stage = (size_t)WG_BOX * 2 + (size_t)t.bn * 128;
   const size_t fixed = 1024 + (2 * WG_STAGES_MAX + 5) * 8 + 16;
   t.stages = WG_STAGES_MAX;
   while (t.stages > 2 && fixed + t.stages * stage > 227 * 1024) --t.stages;
@@ -342,21 +358,21 @@ WgTcPlan* wgrad_tc_plan_create(const ConvArgs& a, int dt, const void* in, const 
     const cuuint64_t Hi = 2 * (cuuint64_t)a.H, Wi = 2 * (cuuint64_t)a.W, C = a.Cin;
     cuuint64_t dims[5] = {2 * C, (cuuint64_t)a.W, 2, (cuuint64_t)a.H, (cuuint64_t)a.n};
     cuuint64_t strides[4] = {2 * C * 2, Wi * C * 2, 2 * Wi * C * 2, Hi * Wi * C * 2};
-    cuuint32_t box[5] = {64, (cuuint32_t)t.Wt, 1, (cuuint32_t)t.Ht, 1};
-    ok = wg_encode(&p->tmA, mdt, 5, in, dims, strides, box);
+    cuuint32_t box[5] = {(cuuint32_t)t.ca, (cuuint32_t)t.Wt, 1, (cuuint32_t)t.Ht, 1};
+    ok = wg_encode(&p->tmA, mdt, 5, in, dims, strides, box, t.ca == 32);
   } else {
     const cuuint64_t C = a.Cin;
     cuuint64_t dims[4] = {C, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.n};
     cuuint64_t strides[3] = {C * 2, (cuuint64_t)a.W * C * 2, (cuuint64_t)a.H * a.W * C * 2};
-    cuuint32_t box[4] = {64, (cuuint32_t)t.Wt, (cuuint32_t)t.Ht, 1};
-    ok = wg_encode(&p->tmA, mdt, 4, in, dims, strides, box);
+    cuuint32_t box[4] = {(cuuint32_t)t.ca, (cuuint32_t)t.Wt, (cuuint32_t)t.Ht, 1};
+    ok = wg_encode(&p->tmA, mdt, 4, in, dims, strides, box, t.ca == 32);
   }
   {
     const cuuint64_t C = a.Cout;
     cuuint64_t dims[4] = {C, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.n};
     cuuint64_t strides[3] = {C * 2, (cuuint64_t)a.W * C * 2, (cuuint64_t)a.H * a.W * C * 2};
-    cuuint32_t box[4] = {64, (cuuint32_t)t.Wt, (cuuint32_t)t.Ht, 1};
-    ok = ok && wg_encode(&p->tmB, mdt, 4, cot, dims, strides, box);
+    cuuint32_t box[4] = {(cuuint32_t)t.cb, (cuuint32_t)t.Wt, (cuuint32_t)t.Ht, 1};
+    ok = ok && wg_encode(&p->tmB, mdt, 4, cot, dims, strides, box, t.cb == 32);
   }
   if (!ok) {
     delete p;

@@ -675,3 +675,30 @@ def test_grad_reg_two_subtile_convs_match_oracle(name, over, monkeypatch):
     for i in range(z.shape[0]):
         ref, gv = nets.grad_g(net, z[i].astype(np.float64))
         assert rel(g[i], ref) < 2e-3, (i, rel(g[i], ref))
+
+
+@pytest.mark.parametrize("name,over,prec", [("C1a", dict(n=2, h=64, w=64), "fp16"),
+                                            ("C1a", dict(n=1, h=136, w=200), "fp16"),
+                                            ("C1a", dict(n=3), "bf16"),
+                                            ("C3", dict(n=2, h=40, w=56), "fp16")])
+def test_grad_reg_cta_pair_convs_match_single_cta(name, over, prec, monkeypatch):
+    """Tiles of 256 rows on a CTA pair (two-SM tcgen05 MMAs, half of B in each CTA's
+    shared memory; plain, streamed-halo, stride-2 and depth-to-space layers with 128
+    or 256 columns) against the single-CTA tiles (IDEQ_TC_CG2=0) on the same inputs,
+    and both against the oracle.  Odd tile counts leave the odd CTA of the last pair a
+    sub-tile past the batch.  The two forms sum the same products in the same K order
+    per tile, so they agree to a unit of the 16-bit outputs."""
+    cfg, wl, net, ops, ys = setup(name, **over)
+    b = B()
+    z = torch.tensor(np.random.default_rng(5).uniform(0, 1, ys.shape).astype(np.float32),
+                     device="cuda")
+    out = {}
+    for cg2 in ("1", "0"):
+        monkeypatch.setenv("IDEQ_TC_CG2", cg2)
+        ctx = ctx_for(cfg, wl, PREC[prec]())
+        out[cg2] = to_np(b.ideq_grad_reg(ctx, z))
+    assert rel(out["1"], out["0"]) < (2e-3 if prec == "bf16" else 5e-4), rel(out["1"], out["0"])
+    zz = to_np(z)
+    for i in range(zz.shape[0]):
+        ref, gv = nets.grad_g(net, zz[i])
+        assert rel(out["1"][i], ref) < (1e-2 if prec == "bf16" else 2e-3)
