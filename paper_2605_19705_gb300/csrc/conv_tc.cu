@@ -405,6 +405,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           tma_load_2d(smem_u32(sB + kc * B_BYTES), &tmB, kc * KCH, 0, bres);
       }
       int g = 0;  // ring position across tiles (row boxes in the halo form)
+      // slot and phase of ring position g, advanced without division: a runtime
+      // divide in these loops measurably slows the MMA issue and the copies
+      int rs = 0;
+      uint32_t rph = 0u;
       bool ok = true;
       if (HALO && !a.slide) {  // one slot of three row boxes per tile
         for (int i = 0; i < my_tiles && ok; ++i) {
@@ -444,14 +448,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
       for (int i = 0; i < my_tiles && ok && STREAM; ++i) {  // streamed halo
         const int t = t_first + i * t_step;
-        for (int kc = 0; kc < 3 * a.cpt; ++kc) {  // (row dy, channel chunk c)
-          const int s = g % ST, j = g / ST;
-          if (j > 0 && !mbar_wait(empty0 + 8 * s, (j - 1) & 1, a.err, 1)) {
+        for (int kc = 0, dy = 0, c = 0; kc < 3 * a.cpt; ++kc) {  // (row dy, channel chunk c)
+          const int s = rs;
+          if (g >= ST && !mbar_wait(empty0 + 8 * s, rph ^ 1u, a.err, 1)) {
             ok = false;
             break;
           }
           if (rank == 0) mbar_expect_tx(full0 + 8 * s, (CG2 ? 2u : 1u) * STAGE_TX);
-          const int dy = kc / a.cpt, c = kc - dy * a.cpt;
           if constexpr (CG2) {  // both halves of the stage complete on the even CTA's barrier
             const uint32_t fb = mapa_shared(full0 + 8 * s, 0);
             const TileCoord sc = tile_coord(a, im, t, BN, MSUB, tsub0);
@@ -473,14 +476,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                           ((3 * dy + dx) * a.cpt + c) * KCH, tc.n0, full0 + 8 * s);
           }
           ++g;
+          if (++rs == ST) {
+            rs = 0;
+            rph ^= 1u;
+          }
+          if (++c == a.cpt) {
+            c = 0;
+            ++dy;
+          }
         }
       }
       for (int i = 0; i < my_tiles && ok && !HALO && !STREAM; ++i) {
         const int t = t_first + i * t_step;
         const TileCoord tc = tile_coord(a, im, t, BN, MSUB, tsub0);
+        // K position of chunk kc: tap and channel offset (3x3), or the input row di
+        // of the 2x2 window and the offset in it (stride 2)
+        int ktap = 0, kcc = 0;
         for (int kc = 0; kc < a.nk; ++kc) {
-          const int s = g % ST, j = g / ST;
-          if (j > 0 && !mbar_wait(empty0 + 8 * s, (j - 1) & 1, a.err, 1)) {
+          const int s = rs;
+          if (g >= ST && !mbar_wait(empty0 + 8 * s, rph ^ 1u, a.err, 1)) {
             ok = false;
             break;
           }
@@ -495,8 +509,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               const TileCoord sc = sub == 0 ? tc : tile_coord(a, im, t, BN, MSUB, sub + tsub0);
               const uint32_t dAs = dA + sub * A_TILE;
               if (a.mode == CM_DOWN) {
-                const int k0 = kc * KCH;
-                const int di = k0 / (2 * a.Cin), rem = k0 - di * 2 * a.Cin;
+                const int di = ktap, rem = kcc;
                 if (CG2)
                   tma_load_5d_cg2(dAs, &tmA, rem, sc.w0, di, sc.h0, sc.img, fb);
                 else
@@ -504,8 +517,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               } else {
                 int tap = 4, c0 = kc * KCH;
                 if (a.mode == CM_CONV3) {
-                  tap = kc / a.cpt;
-                  c0 = (kc - tap * a.cpt) * KCH;
+                  tap = ktap;
+                  c0 = kcc;
                 }
                 if (CG2)
                   tma_load_4d_cg2(dAs, &tmA, c0, sc.w0 + tap % 3 - 1, sc.h0 + tap / 3 - 1,
@@ -521,6 +534,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               tma_load_2d(dB, &tmB, kc * KCH, tc.n0, fb);
           }
           ++g;
+          if (++rs == ST) {
+            rs = 0;
+            rph ^= 1u;
+          }
+          // next K chunk: CM_CONV3 walks the channels of one tap, CM_DOWN the
+          // 2 Cin elements of one input row of the window
+          kcc += KCH;
+          if (kcc == (a.mode == CM_DOWN ? 2 * a.Cin : a.Cin)) {
+            kcc = 0;
+            ++ktap;
+          }
         }
       }
       // tail: wait until the MMA warp released every slot still in use, so no
@@ -542,7 +566,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       // hand both CTAs their accumulator
       constexpr uint32_t idesc = umma_idesc_16(256, BN, Fmt<TA>::v);
       bool ok = true;
-      int g = 0;
+      int rs = 0;  // ring slot and phase, advanced without division
+      uint32_t rph = 0u;
       for (int lt = 0; lt < my_tiles && ok; ++lt) {
         const int b = lt % NACC, u = lt / NACC;
         if (u > 0 && !mbar_wait(tempty0 + 8 * b, (u - 1) & 1, a.err, 5)) {
@@ -553,8 +578,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const uint32_t td = tmem + (uint32_t)(b * TCOLS);
         const int nkc = STREAM ? 3 * a.cpt : a.nk;
         for (int kc = 0; kc < nkc; ++kc) {
-          const int s = g % ST, j = g / ST;
-          if (!mbar_wait(full0 + 8 * s, j & 1, a.err, 3)) {  // both CTAs' halves
+          const int s = rs;
+          if (!mbar_wait(full0 + 8 * s, rph, a.err, 3)) {  // both CTAs' halves
             ok = false;
             break;
           }
@@ -577,7 +602,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               umma_cg2(td, ad + 2 * kk, bd + 2 * kk, idesc, (kc | kk) != 0 ? 1u : 0u);
           }
           umma_commit_cg2_both(empty0 + 8 * s);
-          ++g;
+          if (++rs == ST) {
+            rs = 0;
+            rph ^= 1u;
+          }
         }
         if (ok) umma_commit_cg2_both(tfull0 + 8 * b);
       }
@@ -592,6 +620,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       bool ok = true;
       if (HALO) ok = mbar_wait(bres, 0, a.err, 9);
       int g = 0, base = 0;  // base: ring position of the tile's row y-1 box (HALO)
+      int rs = 0;           // ring slot and phase of the plain and streamed forms,
+      uint32_t rph = 0u;    // advanced without division
       for (int lt = 0; lt < my_tiles && ok; ++lt) {
         const int t = t_first + lt * t_step;
         const int b = lt % NACC, u = lt / NACC;
@@ -654,8 +684,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             umma_commit(empty0 + 8 * ((base + dy) % ST));
         } else if (STREAM) {
           for (int kc = 0; kc < 3 * a.cpt; ++kc) {
-            const int s = g % ST, j = g / ST;
-            if (!mbar_wait(full0 + 8 * s, j & 1, a.err, 3)) {
+            const int s = rs;
+            if (!mbar_wait(full0 + 8 * s, rph, a.err, 3)) {
               ok = false;
               break;
             }
@@ -674,13 +704,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               }
             }
             umma_commit(empty0 + 8 * s);
-            ++g;
+            if (++rs == ST) {
+              rs = 0;
+              rph ^= 1u;
+            }
           }
           if (ok) umma_commit(tfull0 + 8 * b);
         } else {
           for (int kc = 0; kc < a.nk; ++kc) {
-            const int s = g % ST, j = g / ST;
-            if (!mbar_wait(full0 + 8 * s, j & 1, a.err, 3)) {
+            const int s = rs;
+            if (!mbar_wait(full0 + 8 * s, rph, a.err, 3)) {
               ok = false;
               break;
             }
@@ -695,7 +728,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                           (kc | kk) != 0 ? 1u : 0u);
             }
             umma_commit(empty0 + 8 * s);
-            ++g;
+            if (++rs == ST) {
+              rs = 0;
+              rph ^= 1u;
+            }
           }
           if (ok) umma_commit(tfull0 + 8 * b);
         }
@@ -1043,11 +1079,15 @@ TcPlan* tc_plan_create(const ConvArgs& a, int op_dt, int epi_dt, std::string* er
     if (ms2_ok && (force_ms == 2 || (force_ms == 3 && w2 < w1))) p->ms = 2;
     }
     // CTA pairs with two-SM MMAs for the 128- and 256-column 16-bit tiles of the
-    // plain and streamed forms, when IDEQ_TC_CG2=1.  Measured on 8 x RGB 256^2
-    // (C1a): no faster than single-CTA tiles (conv launches of one iteration
-    // 3383 vs 3355 us), so single-CTA tiles stay the default.
+    // plain and streamed forms.  Each SM then loads a third fewer operand bytes per
+    // MMA cycle; this pays where the copies bound the main loop, i.e. long K.
+    // Measured on 8 x RGB 256^2 (C1a): 256- and 512-channel 3x3 layers 12-14%
+    // faster as pairs; the streamed 128-channel layers and the short-K stride-2 and
+    // depth-to-space layers slower.  IDEQ_TC_CG2=1 pairs every eligible layer, 0 none.
+    const int cg2_mode = tiling_override("IDEQ_TC_CG2", -1);
     p->cg2 = !p->halo && !p->nw && op_dt != DT_FP8 && (p->bn == 128 || p->bn == 256) &&
-             p->ms == 1 && !img && tiling_override("IDEQ_TC_CG2", 0) == 1;
+             p->ms == 1 && !img && cg2_mode != 0 &&
+             (cg2_mode == 1 || (!p->stream && p->nk >= 32));
     const size_t bcta = p->cg2 ? (size_t)p->bn / 2 : (size_t)p->bn;  // rows of B per CTA
     // shared memory: ring depth and staging buffers, preferring a deep ring
     // (halo: >= 5 row boxes, three in use and two in flight; else >= 3 stages),
