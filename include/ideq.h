@@ -262,7 +262,10 @@ ideq_status ideq_warm_get(ideq_ctx *ctx, float *weights);
  * allocate while serving.  It performs the RED update of Algorithm 1 on caller
  * buffers, without a context:
  *   x_new = z - tau (grad_f + lambda grad_g)
- *   step_sq[b] = ||x_new_b - x_b||^2,  x_sq[b] = ||x_b||^2   (FP64, per image)
+ *   step_sq[b] = ||x_new_b - x_b||^2,  x_sq[b] = ||x_b||^2   (per image)
+ * The squares are summed in FP32 over at most 16 elements and every sum above
+ * that in FP64, so the two norms carry a relative error below 16 FP32 ulps
+ * (about 1e-6) -- far below any stopping tolerance they are compared with.
  * n images of per_img floats each, contiguous (NCHW), device pointers; step_sq
  * and x_sq are device arrays of n doubles (nullable).  It calls no cudaMalloc or
  * cudaFree: its per-block partial sums live in one static device array of 65536
