@@ -71,6 +71,7 @@ struct TcPlan {
   bool halo = false, slide = false, stream = false, nw = false;
   bool pdl = true;       // launched with programmatic stream serialisation
   bool cg2 = false;      // CTA pairs with two-SM MMAs (clusters of two)
+  bool stk = false;      // halo form with stacked vertical taps (sliding row runs)
   bool split64 = false;  // 64-column tiles: epilogue halves on alternate tiles
   int Wt = 0, Ht = 0, tiles_w = 0, tiles_h = 0, tiles_n = 0, nk = 0, cpt = 0;
   dim3 grid;
@@ -265,7 +266,15 @@ IDEQ_DEV TileCoord halo_coord(const TcArgs& a, const ImgMap& im, int t) {
 // two-SM MMAs (tcgen05 .cta_group::2): each CTA loads its own 128 rows of A and
 // half of the N rows of B (per-SM operand bytes per MMA cycle fall by a third for
 // N = 256), the even CTA issues the MMAs, each CTA's epilogue drains its own rows.
-template <typename TA, typename T, int BN, bool HALO, int MS, bool NW, bool CG2 = false>
+// STK (stacked taps; sliding halo form, N <= 64): the three vertical taps of one
+// horizontal offset are stacked along N, so one MMA of N = 3 BN reads an input row
+// box once for the three output rows it feeds (rows y+1, y, y-1).  The weights
+// sit in shared memory in (dx, 2 - dy) order, the accumulators of consecutive
+// output rows in a ring of eight TMEM blocks; each input row box is read once.
+// MMAs of N = 64 are bound by the operand reads from shared memory (A: 4 KB per
+// MMA whatever N is), so this cuts those reads per output row from 216 to ~124 KB.
+template <typename TA, typename T, int BN, bool HALO, int MS, bool NW, bool CG2 = false,
+          bool STK = false>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     conv_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                    const __grid_constant__ CUtensorMap tmB,
@@ -278,6 +287,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   static_assert(!CG2 || (!HALO && !NW && MS == 1 && sizeof(TA) == 2 && BN >= 128),
                 "CTA pairs: plain or streamed 16-bit tiles of 128 or 256 columns");
   static_assert(!NW || (MS == 1 && sizeof(TA) == 2), "narrow rows: 16-bit, one sub-tile");
+  static_assert(!STK || (HALO && !NW && BN <= 64), "stacked taps: halo form, N <= 64");
   constexpr int RB = NW ? 64 : 128;     // bytes of one K row of a ring tile
   constexpr int A_TILE = 128 * RB;      // one 128-pixel A tile of one K chunk
   constexpr int B_BYTES = (CG2 ? BN / 2 : BN) * RB;  // this CTA's rows of B per K chunk
@@ -306,7 +316,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   constexpr int TCOLS = MS * BN;  // TMEM columns of one accumulator buffer (2 x >= 32 allocated)
   // accumulator buffers: two (the epilogue of one tile overlaps the MMAs of the
   // next) while they fit the 512 TMEM columns, else one (M = 256 x N = 256 tiles)
-  constexpr int NACC = TCOLS <= 256 ? 2 : 1;
+  // (stacked taps: a ring of eight, one per output row in flight)
+  constexpr int NACC = STK ? 8 : (TCOLS <= 256 ? 2 : 1);
+  constexpr int NTB = STK ? 8 : 2;  // accumulator full / empty barriers of each kind
   const int ST = a.stages;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -315,22 +327,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint8_t* sOut = sB + (HALO ? a.nk * B_BYTES : ST * B_STAGE);  // [warp][nbo][nout][WBOX]
   uint8_t* sAux = sOut + a.nbo * a.nout * PANEL;                 // [warp][nba][naux][WBOX]
   uint64_t* bars = (uint64_t*)(sAux + a.nba * a.naux * PANEL);
-  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * ST + 6 + MAX_NBA * EPI_WARPS);
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * ST + 2 * NTB + 2 + MAX_NBA * EPI_WARPS);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + ST);
   const uint32_t tfull0 = smem_u32(bars + 2 * ST);
-  const uint32_t tempty0 = smem_u32(bars + 2 * ST + 2);
-  const uint32_t drain = smem_u32(bars + 2 * ST + 4);
-  const uint32_t bres = smem_u32(bars + 2 * ST + 5);
-  const uint32_t auxbar0 = smem_u32(bars + 2 * ST + 6);  // [warp][MAX_NBA]
+  const uint32_t tempty0 = smem_u32(bars + 2 * ST + NTB);
+  const uint32_t drain = smem_u32(bars + 2 * ST + 2 * NTB);
+  const uint32_t bres = smem_u32(bars + 2 * ST + 2 * NTB + 1);
+  const uint32_t auxbar0 = smem_u32(bars + 2 * ST + 2 * NTB + 2);  // [warp][MAX_NBA]
   const uint32_t rank = CG2 ? cluster_ctarank() : 0u;  // 0: issues the pair's MMAs
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NTB; ++b) {
       mbar_init(tfull0 + 8 * b, 1);
       // a pair's accumulator is released by the epilogue warps of both CTAs
       mbar_init(tempty0 + 8 * b, CG2 ? 2 * EPI_WARPS : (spl ? EPI_WARPS / 2 : EPI_WARPS));
@@ -401,8 +413,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
       if (HALO) {  // resident weights: every K chunk of B once
         mbar_expect_tx(bres, (uint32_t)(a.nk * B_BYTES));
-        for (int kc = 0; kc < a.nk; ++kc)
-          tma_load_2d(smem_u32(sB + kc * B_BYTES), &tmB, kc * KCH, 0, bres);
+        for (int kc = 0; kc < a.nk; ++kc) {  // kc: tap 3 dy + dx (one K chunk per tap)
+          const int blk = STK ? (kc % 3) * 3 + 2 - kc / 3 : kc;
+          tma_load_2d(smem_u32(sB + blk * B_BYTES), &tmB, kc * KCH, 0, bres);
+        }
       }
       int g = 0;  // ring position across tiles (row boxes in the halo form)
       // slot and phase of ring position g, advanced without division: a runtime
@@ -413,8 +427,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (HALO && !a.slide) {  // one slot of three row boxes per tile
         for (int i = 0; i < my_tiles && ok; ++i) {
           const TileCoord tc = halo_coord(a, im, t_first + i * t_step);
-          const int s = g % ST, j = g / ST;
-          if (j > 0 && !mbar_wait(empty0 + 8 * s, (j - 1) & 1, a.err, 1)) {
+          const int s = rs;
+          if (g >= ST && !mbar_wait(empty0 + 8 * s, rph ^ 1u, a.err, 1)) {
             ok = false;
             break;
           }
@@ -423,6 +437,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             tma_load_4d(smem_u32(sA + s * A_STAGE + dy * HBOX), &tmA, 0, tc.w0 - 1,
                         tc.h0 + dy - 1, tc.img, full0 + 8 * s);
           ++g;
+          if (++rs == ST) {
+            rs = 0;
+            rph ^= 1u;
+          }
         }
       } else if (HALO) {  // sliding: single row boxes, reused across consecutive rows
         for (int i = 0; i < my_tiles && ok; ++i) {
@@ -560,7 +578,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (HALO && !ok) mbar_wait(bres, 0, a.err, 2);
     }
   } else if (CG2 && warp == 1) {
-    if (lane == 0 && rank == 0) {
+    if (rank == 0) {  // the whole warp, converged: one elected lane issues
       // even CTA of a pair: two-SM MMAs, M = 256 (128 rows of A from each CTA),
       // N = BN (half of B from each CTA); commits release both CTAs' stages and
       // hand both CTAs their accumulator
@@ -570,7 +588,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       uint32_t rph = 0u;
       for (int lt = 0; lt < my_tiles && ok; ++lt) {
         const int b = lt % NACC, u = lt / NACC;
-        if (u > 0 && !mbar_wait(tempty0 + 8 * b, (u - 1) & 1, a.err, 5)) {
+        if (u > 0 && !mbar_wait_warp(tempty0 + 8 * b, (u - 1) & 1, a.err, 5)) {
           ok = false;
           break;
         }
@@ -579,78 +597,171 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int nkc = STREAM ? 3 * a.cpt : a.nk;
         for (int kc = 0; kc < nkc; ++kc) {
           const int s = rs;
-          if (!mbar_wait(full0 + 8 * s, rph, a.err, 3)) {  // both CTAs' halves
+          if (!mbar_wait_warp(full0 + 8 * s, rph, a.err, 3)) {  // both CTAs' halves
             ok = false;
             break;
           }
           tc_fence_after();
           if (STREAM) {
-            const uint32_t abox = smem_u32(sA + s * A_STAGE);
-#pragma unroll 1
+            const uint64_t a0 = umma_desc_sw128(smem_u32(sA + s * A_STAGE));
+            const uint64_t b0 = umma_desc_sw128(smem_u32(sB + s * B_STAGE));
+#pragma unroll
             for (int dx = 0; dx < 3; ++dx) {
-              const uint64_t bd = umma_desc_sw128(smem_u32(sB + s * B_STAGE + dx * B_BYTES));
-              const uint64_t ad = umma_desc_sw128_rows(abox, dx);
+              const uint64_t bd = b0 + (uint64_t)((dx * B_BYTES) >> 4);
+              const uint64_t ad = a0 + (uint64_t)((128 * dx) >> 4);
 #pragma unroll
               for (int kk = 0; kk < KSTEPS; ++kk)
-                umma_cg2(td, ad + 2 * kk, bd + 2 * kk, idesc, (kc | dx | kk) != 0 ? 1u : 0u);
+                umma_cg2_el(td, ad + 2 * kk, bd + 2 * kk, idesc, (kc | dx | kk) != 0 ? 1u : 0u);
             }
           } else {
             const uint64_t bd = umma_desc_sw128(smem_u32(sB + s * B_STAGE));
             const uint64_t ad = umma_desc_sw128(smem_u32(sA + s * A_STAGE));
 #pragma unroll
             for (int kk = 0; kk < KSTEPS; ++kk)
-              umma_cg2(td, ad + 2 * kk, bd + 2 * kk, idesc, (kc | kk) != 0 ? 1u : 0u);
+              umma_cg2_el(td, ad + 2 * kk, bd + 2 * kk, idesc, (kc | kk) != 0 ? 1u : 0u);
           }
-          umma_commit_cg2_both(empty0 + 8 * s);
+          umma_commit_cg2_both_el(empty0 + 8 * s);
           if (++rs == ST) {
             rs = 0;
             rph ^= 1u;
           }
         }
-        if (ok) umma_commit_cg2_both(tfull0 + 8 * b);
+        if (ok) umma_commit_cg2_both_el(tfull0 + 8 * b);
       }
       if (!ok) {  // let every issued MMA finish before TMEM is released
-        umma_commit_cg2(drain);
-        mbar_wait(drain, 0, a.err, 6);
+        umma_commit_cg2_el(drain);
+        mbar_wait_warp(drain, 0, a.err, 6);
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
+    {  // the whole warp, converged: one elected lane issues
       constexpr uint32_t idesc = umma_idesc_16(128, BN, Fmt<TA>::v);
       bool ok = true;
-      if (HALO) ok = mbar_wait(bres, 0, a.err, 9);
+      if (HALO) ok = mbar_wait_warp(bres, 0, a.err, 9);
       int g = 0, base = 0;  // base: ring position of the tile's row y-1 box (HALO)
-      int rs = 0;           // ring slot and phase of the plain and streamed forms,
+      int rs = 0;           // ring slot and phase (all forms but the sliding one),
       uint32_t rph = 0u;    // advanced without division
+      if constexpr (STK) {
+        // Stacked taps: walk the input row boxes in the order the producer loads
+        // them.  A run of rows of one strip (seg output rows) reads seg + 2 boxes;
+        // box i (-1 <= i <= seg, local rows) feeds stack position p (0: dy = 2,
+        // 1: dy = 1, 2: dy = 0) of output row i - 1 + p, where that row is in the run.
+        // Row i + 1 (p = 2) gets its first product here: on the first MMA step that
+        // part is issued on its own without accumulation.
+        constexpr uint32_t id1 = umma_idesc_16(128, BN, Fmt<TA>::v);
+        constexpr uint32_t id2 = umma_idesc_16(128, 2 * BN, Fmt<TA>::v);
+        constexpr uint32_t id3 = umma_idesc_16(128, 3 * BN, Fmt<TA>::v);
+        const uint64_t bw0 = umma_desc<NW>(smem_u32(sB));
+        int lt = 0;
+        while (lt < my_tiles && ok) {
+          const int t = t_first + lt;  // contiguous runs (t_step = 1)
+          const int seg = min(my_tiles - lt, a.tiles_h - t % a.tiles_h);
+          for (int i = -1; i <= seg && ok; ++i) {
+            const int s = rs;
+            const int p_lo = i >= 1 ? 0 : 1 - i, p_hi = min(2, seg - i);
+            const bool fresh = p_hi == 2;  // output row i + 1 starts here
+            if (fresh) {  // its accumulator block must have been drained
+              const int ln = lt + i + 1;
+              if (ln >= NACC &&
+                  !mbar_wait_warp(tempty0 + 8 * (ln % NACC), ((ln / NACC) - 1) & 1, a.err, 5)) {
+                ok = false;
+                break;
+              }
+            }
+            if (!mbar_wait_warp(full0 + 8 * s, rph, a.err, 3)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            // positions [pl, ph] as MMAs: one, or two where the block ring wraps
+            // (d: accumulator column, bo: B descriptor offset, id: N)
+            uint32_t d1 = 0, d2 = 0, bo1 = 0, bo2 = 0, i1 = 0, i2 = 0;
+            auto pieces = [&](int pl, int ph) -> int {
+              if (pl > ph) return 0;
+              const int blk = (lt + i - 1 + pl) % NACC, c = ph - pl + 1;
+              const int c1 = min(c, NACC - blk);
+              d1 = tmem + (uint32_t)(blk * TCOLS);
+              bo1 = (uint32_t)((pl * B_BYTES) >> 4);
+              i1 = c1 == 1 ? id1 : (c1 == 2 ? id2 : id3);
+              if (c1 == c) return 1;
+              d2 = tmem;
+              bo2 = (uint32_t)(((pl + c1) * B_BYTES) >> 4);
+              i2 = c - c1 == 1 ? id1 : id2;
+              return 2;
+            };
+            // first step: the accumulating positions, then the new row
+            const int nf = pieces(p_lo, fresh ? 1 : p_hi);
+            const uint32_t fd1 = d1, fd2 = d2, fbo1 = bo1, fbo2 = bo2, fi1 = i1, fi2 = i2;
+            const uint32_t dn = tmem + (uint32_t)(((lt + i + 1) % NACC) * TCOLS);
+            const uint32_t bon = (uint32_t)((2 * B_BYTES) >> 4);
+            // the other steps: all positions, accumulating
+            const int ng = pieces(p_lo, p_hi);
+            const uint64_t a0 = umma_desc<NW>(smem_u32(sA + s * A_STAGE));
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+#pragma unroll
+              for (int kk = 0; kk < KSTEPS; ++kk) {
+                const uint64_t ad = a0 + (uint64_t)((dx * RB) >> 4) + 2 * kk;
+                const uint64_t bd = bw0 + (uint64_t)((dx * 3 * B_BYTES) >> 4) + 2 * kk;
+                if (dx == 0 && kk == 0) {
+                  if (nf >= 1) umma_el<TA>(fd1, ad, bd + fbo1, fi1, 1u);
+                  if (nf >= 2) umma_el<TA>(fd2, ad, bd + fbo2, fi2, 1u);
+                  if (fresh) umma_el<TA>(dn, ad, bd + bon, id1, 0u);
+                } else {
+                  if (ng >= 1) umma_el<TA>(d1, ad, bd + bo1, i1, 1u);
+                  if (ng >= 2) umma_el<TA>(d2, ad, bd + bo2, i2, 1u);
+                }
+              }
+            }
+            umma_commit_el(empty0 + 8 * s);  // the box is read once
+            if (p_lo == 0) umma_commit_el(tfull0 + 8 * ((lt + i - 1) % NACC));  // row i-1 done
+            if (++rs == ST) {
+              rs = 0;
+              rph ^= 1u;
+            }
+          }
+          lt += seg;
+        }
+      } else
       for (int lt = 0; lt < my_tiles && ok; ++lt) {
         const int t = t_first + lt * t_step;
         const int b = lt % NACC, u = lt / NACC;
-        if (u > 0 && !mbar_wait(tempty0 + 8 * b, (u - 1) & 1, a.err, 5)) {
+        if (u > 0 && !mbar_wait_warp(tempty0 + 8 * b, (u - 1) & 1, a.err, 5)) {
           ok = false;
           break;
         }
         tc_fence_after();
         const uint32_t td = tmem + (uint32_t)(b * TCOLS);
         if (HALO && !a.slide) {
-          const int s = g % ST, j = g / ST;
-          if (!mbar_wait(full0 + 8 * s, j & 1, a.err, 3)) {
+          const int s = rs;
+          if (!mbar_wait_warp(full0 + 8 * s, rph, a.err, 3)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t abase = smem_u32(sA + s * A_STAGE);
-#pragma unroll 1
+          // The 36 (or 18) MMAs of the tile back to back: the descriptors of the
+          // taps are the slot's and the weights' base descriptors plus constant
+          // address offsets (the start address field holds address / 16, and no
+          // shared-memory address reaches its carry), so nothing but MMAs is issued
+          // between them; the pipe drains on any gap in the issue.
+          const uint64_t a0 = umma_desc<NW>(smem_u32(sA + s * A_STAGE));
+          const uint64_t b0 = umma_desc<NW>(smem_u32(sB));
+#pragma unroll
           for (int tap = 0; tap < 9; ++tap) {
             const int dy = tap / 3, dx = tap - 3 * dy;
-            const uint64_t ad = umma_desc_rows<NW>(abase + dy * HBOX, dx);
-            const uint64_t bd = umma_desc<NW>(smem_u32(sB + tap * B_BYTES));
+            const uint64_t ad = a0 + (uint64_t)((dy * HBOX + dx * RB) >> 4);
+            const uint64_t bd = b0 + (uint64_t)((tap * B_BYTES) >> 4);
 #pragma unroll
             for (int kk = 0; kk < KSTEPS; ++kk)
-              umma<TA>(td, ad + 2 * kk, bd + 2 * kk, idesc, (tap | kk) != 0 ? 1u : 0u);
+              umma_el<TA>(td, ad + 2 * kk, bd + 2 * kk, idesc, (tap | kk) != 0 ? 1u : 0u);
           }
-          umma_commit(empty0 + 8 * s);
-          umma_commit(tfull0 + 8 * b);
+          umma_commit_el(empty0 + 8 * s);
+          umma_commit_el(tfull0 + 8 * b);
           ++g;
+          if (++rs == ST) {
+            rs = 0;
+            rph ^= 1u;
+          }
         } else if (HALO) {
           const bool fresh = lt == 0 || t % a.tiles_h == 0;
           if (fresh) {
@@ -662,7 +773,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
           for (int dy = 0; dy < 3 && ok; ++dy) {
             const int box = base + dy;
-            ok = mbar_wait(full0 + 8 * (box % ST), (box / ST) & 1, a.err, 3);
+            ok = mbar_wait_warp(full0 + 8 * (box % ST), (box / ST) & 1, a.err, 3);
           }
           if (!ok) break;
           tc_fence_after();
@@ -674,46 +785,48 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const uint64_t bd = umma_desc<NW>(smem_u32(sB + tap * B_BYTES));
 #pragma unroll
             for (int kk = 0; kk < KSTEPS; ++kk)
-              umma<TA>(td, ad + 2 * kk, bd + 2 * kk, idesc, (tap | kk) != 0 ? 1u : 0u);
+              umma_el<TA>(td, ad + 2 * kk, bd + 2 * kk, idesc, (tap | kk) != 0 ? 1u : 0u);
           }
-          umma_commit(tfull0 + 8 * b);
+          umma_commit_el(tfull0 + 8 * b);
           // release the boxes the next tile does not read: row y-1, or all three
           // when the next tile starts a new strip run (or there is none)
           const bool next_fresh = lt + 1 == my_tiles || (t + 1) % a.tiles_h == 0;
           for (int dy = 0; dy < (next_fresh ? 3 : 1); ++dy)
-            umma_commit(empty0 + 8 * ((base + dy) % ST));
+            umma_commit_el(empty0 + 8 * ((base + dy) % ST));
         } else if (STREAM) {
           for (int kc = 0; kc < 3 * a.cpt; ++kc) {
             const int s = rs;
-            if (!mbar_wait(full0 + 8 * s, rph, a.err, 3)) {
+            if (!mbar_wait_warp(full0 + 8 * s, rph, a.err, 3)) {
               ok = false;
               break;
             }
             tc_fence_after();
-            const uint32_t abox = smem_u32(sA + s * A_STAGE);
-#pragma unroll 1
+            // three taps of one row box back to back (constant descriptor offsets)
+            const uint64_t a0 = umma_desc_sw128(smem_u32(sA + s * A_STAGE));
+            const uint64_t b0 = umma_desc_sw128(smem_u32(sB + s * B_STAGE));
+#pragma unroll
             for (int dx = 0; dx < 3; ++dx) {
-              const uint64_t bd = umma_desc_sw128(smem_u32(sB + s * B_STAGE + dx * B_BYTES));
+              const uint64_t bd = b0 + (uint64_t)((dx * B_BYTES) >> 4);
 #pragma unroll
               for (int sub = 0; sub < MS; ++sub) {
-                const uint64_t ad = umma_desc_sw128_rows(abox + sub * HALO_BOX, dx);
+                const uint64_t ad = a0 + (uint64_t)((sub * HALO_BOX + 128 * dx) >> 4);
 #pragma unroll
                 for (int kk = 0; kk < KSTEPS; ++kk)
-                  umma<TA>(td + sub * BN, ad + 2 * kk, bd + 2 * kk, idesc,
+                  umma_el<TA>(td + sub * BN, ad + 2 * kk, bd + 2 * kk, idesc,
                            (kc | dx | kk) != 0 ? 1u : 0u);
               }
             }
-            umma_commit(empty0 + 8 * s);
+            umma_commit_el(empty0 + 8 * s);
             if (++rs == ST) {
               rs = 0;
               rph ^= 1u;
             }
           }
-          if (ok) umma_commit(tfull0 + 8 * b);
+          if (ok) umma_commit_el(tfull0 + 8 * b);
         } else {
           for (int kc = 0; kc < a.nk; ++kc) {
             const int s = rs;
-            if (!mbar_wait(full0 + 8 * s, rph, a.err, 3)) {
+            if (!mbar_wait_warp(full0 + 8 * s, rph, a.err, 3)) {
               ok = false;
               break;
             }
@@ -724,21 +837,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               const uint64_t ad = umma_desc<NW>(smem_u32(sA + s * A_STAGE + sub * A_TILE));
 #pragma unroll
               for (int kk = 0; kk < KSTEPS; ++kk)
-                umma<TA>(td + sub * BN, ad + 2 * kk, bd + 2 * kk, idesc,
+                umma_el<TA>(td + sub * BN, ad + 2 * kk, bd + 2 * kk, idesc,
                           (kc | kk) != 0 ? 1u : 0u);
             }
-            umma_commit(empty0 + 8 * s);
+            umma_commit_el(empty0 + 8 * s);
             if (++rs == ST) {
               rs = 0;
               rph ^= 1u;
             }
           }
-          if (ok) umma_commit(tfull0 + 8 * b);
+          if (ok) umma_commit_el(tfull0 + 8 * b);
         }
       }
       if (!ok) {  // let every issued MMA finish before TMEM is released
-        umma_commit(drain);
-        mbar_wait(drain, 0, a.err, 6);
+        umma_commit_el(drain);
+        mbar_wait_warp(drain, 0, a.err, 6);
       }
     }
   } else if constexpr (IMG) {
@@ -750,7 +863,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     bool ok = true;
     for (int lt = half; lt < my_tiles && ok; lt += 2) {
       const int t = t_first + lt * t_step;
-      const int b = lt & 1, u = lt >> 1;
+      const int b = lt % NACC, u = lt / NACC;
       ok = __all_sync(0xffffffffu, mbar_wait(tfull0 + 8 * b, u & 1, a.err, 4));
       if (!ok) break;
       tc_fence_after();
@@ -954,9 +1067,9 @@ bool tc_supported(const ConvArgs& a, int op_dt) {
   return true;
 }
 
-static size_t fixed_smem(int nout, int naux, int nbo, int nba, int stages) {
+static size_t fixed_smem(int nout, int naux, int nbo, int nba, int stages, int ntb = 2) {
   return 1024 + (size_t)(nbo * nout + nba * naux) * PANEL +
-         (2 * stages + 6 + MAX_NBA * EPI_WARPS) * 8 + 16;
+         (2 * stages + 2 * ntb + 2 + MAX_NBA * EPI_WARPS) * 8 + 16;
 }
 
 constexpr size_t kMaxSmem = 227 * 1024;
@@ -1052,6 +1165,13 @@ TcPlan* tc_plan_create(const ConvArgs& a, int op_dt, int epi_dt, std::string* er
               p->Ht == 1 && p->tiles_n == 1 && p->cpt == 1 && halo_bn && bres <= 80 * 1024 &&
               tiling_override("IDEQ_TC_HALO", 1) != 0;
     p->slide = p->halo && !p->nw && tiling_override("IDEQ_TC_SLIDE", 0) != 0;
+    // stacked vertical taps (N = 3 BN per MMA) over sliding row runs, for the
+    // halo layers of <= 64 output columns, when IDEQ_TC_STACK=1.  Measured on the
+    // 64-channel 256^2 layers of 8 x RGB 256^2 (C1a): 70-78 us against 63-72 us for
+    // the 9-tap tiles, although the stacked MMA sequence alone runs 1.6x faster; the
+    // epilogue and the sliding row runs bound these layers, so the 9-tap tiles stay.
+    p->stk = p->halo && !p->nw && p->bn <= 64 && tiling_override("IDEQ_TC_STACK", 0) == 1;
+    if (p->stk) p->slide = true;
     // streamed halo: full-row 3x3 convs whose weights do not stay resident
     p->stream = !p->halo && op_dt != DT_FP8 && !p->nw && a.mode == CM_CONV3 && p->Wt == 128 &&
                 p->Ht == 1 && p->tiles_n == 1 && p->bn <= 128 && p->bn != 32 &&
@@ -1103,7 +1223,8 @@ TcPlan* tc_plan_create(const ConvArgs& a, int op_dt, int epi_dt, std::string* er
     if (p->naux > 0 && !p->halo && !p->stream && p->nk <= 4 &&
         tiling_override("IDEQ_TC_NBA", MAX_NBA) == MAX_NBA) {
       for (int st = 8; st >= 2 && !p->stages; --st) {
-        const size_t tot = fixed_smem(p->nout, p->naux, 2, MAX_NBA, st) + (size_t)st * stage;
+        const size_t tot =
+            fixed_smem(p->nout, p->naux, 2, MAX_NBA, st, p->stk ? 8 : 2) + (size_t)st * stage;
         if (tot <= kMaxSmem) {
           p->stages = st;
           p->nbo = 2;
@@ -1127,7 +1248,7 @@ TcPlan* tc_plan_create(const ConvArgs& a, int op_dt, int epi_dt, std::string* er
         if (!aux_deep && nbo != nba) continue;
         int st = 8;
         auto total = [&](int k) {
-          return fixed_smem(p->nout, p->naux, nbo, nba, k) + resident + k * stage;
+          return fixed_smem(p->nout, p->naux, nbo, nba, k, p->stk ? 8 : 2) + resident + k * stage;
         };
         while (st > min_st && total(st) > kMaxSmem) --st;
         if (total(st) <= kMaxSmem) {
@@ -1217,11 +1338,12 @@ TcPlan* tc_plan_create(const ConvArgs& a, int op_dt, int epi_dt, std::string* er
 
 void tc_plan_destroy(TcPlan* p) { delete p; }
 
-template <typename TA, typename T, int BN, bool HALO, int MS, bool NW = false, bool CG2 = false>
+template <typename TA, typename T, int BN, bool HALO, int MS, bool NW = false, bool CG2 = false,
+          bool STK = false>
 static cudaError_t launch_bn(const TcPlan* p, const TcArgs& ta, cudaStream_t st) {
   static bool attr_set = false;  // per instantiation; set before first launch
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<TA, T, BN, HALO, MS, NW, CG2>,
+    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<TA, T, BN, HALO, MS, NW, CG2, STK>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kMaxSmem);
     if (e != cudaSuccess) return e;
@@ -1244,7 +1366,7 @@ static cudaError_t launch_bn(const TcPlan* p, const TcArgs& ta, cudaStream_t st)
     attr[1].val.clusterDim.z = 1;
     cfg.numAttrs = 2;
   }
-  return cudaLaunchKernelEx(&cfg, conv_tc_kernel<TA, T, BN, HALO, MS, NW, CG2>, p->tmA, p->tmB,
+  return cudaLaunchKernelEx(&cfg, conv_tc_kernel<TA, T, BN, HALO, MS, NW, CG2, STK>, p->tmA, p->tmB,
                             p->tmO[0], p->tmO[1], p->tmX[0], p->tmX[1], p->tmX[2], ta);
 }
 
@@ -1275,9 +1397,11 @@ static cudaError_t launch_typed(const TcPlan* p, const TcArgs& t, cudaStream_t s
   }
   if (p->bn == 32) return launch_bn<T, T, 32, false, 1>(p, t, st);
   if (p->bn == 16) {
+    if (p->stk) return launch_bn<T, T, 16, true, 1, false, false, true>(p, t, st);
     if (p->halo) return launch_bn<T, T, 16, true, 1>(p, t, st);
     return launch_bn<T, T, 16, false, 1>(p, t, st);
   }
+  if (p->stk) return launch_bn<T, T, 64, true, 1, false, false, true>(p, t, st);
   if (p->halo) {
     switch (p->bn) {
       case 64: return launch_bn<T, T, 64, true, 1>(p, t, st);

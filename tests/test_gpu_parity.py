@@ -702,3 +702,29 @@ def test_grad_reg_cta_pair_convs_match_single_cta(name, over, prec, monkeypatch)
     for i in range(zz.shape[0]):
         ref, gv = nets.grad_g(net, zz[i])
         assert rel(out["1"][i], ref) < (1e-2 if prec == "bf16" else 2e-3)
+
+
+@pytest.mark.parametrize("name,over,prec", [("C1a", dict(n=2, h=40, w=128), "fp16"),
+                                            ("C1a", dict(n=1, h=136, w=200), "fp16"),
+                                            ("C1a", dict(n=3, h=48, w=256), "bf16")])
+def test_grad_reg_stacked_tap_convs_match_nine_tap(name, over, prec, monkeypatch):
+    """The stacked-tap form of the full-row 3x3 layers of <= 64 output channels
+    (IDEQ_TC_STACK=1: one MMA of N = 3 x 64 per input row and horizontal offset,
+    accumulators of consecutive output rows in a ring of TMEM blocks, contiguous row
+    runs per CTA that cross strip and image boundaries) against the 9-tap tiles on
+    the same inputs, and against the oracle.  Row counts not a multiple of the CTA
+    count leave runs of uneven length; 136 rows x 200 columns gives a ragged strip."""
+    cfg, wl, net, ops, ys = setup(name, **over)
+    b = B()
+    z = torch.tensor(np.random.default_rng(9).uniform(0, 1, ys.shape).astype(np.float32),
+                     device="cuda")
+    out = {}
+    for stk in ("1", "0"):
+        monkeypatch.setenv("IDEQ_TC_STACK", stk)
+        ctx = ctx_for(cfg, wl, PREC[prec]())
+        out[stk] = to_np(b.ideq_grad_reg(ctx, z))
+    assert rel(out["1"], out["0"]) < (2e-3 if prec == "bf16" else 5e-4), rel(out["1"], out["0"])
+    zz = to_np(z)
+    for i in range(zz.shape[0]):
+        ref, gv = nets.grad_g(net, zz[i])
+        assert rel(out["1"][i], ref) < (1e-2 if prec == "bf16" else 2e-3)
