@@ -270,8 +270,8 @@ ideq_status ideq_warm_get(ideq_ctx *ctx, float *weights);
  * and x_sq are device arrays of n doubles (nullable).  It calls no cudaMalloc or
  * cudaFree: its per-block partial sums live in one static device array of 65536
  * doubles (512 KiB) that every GPU loading the library keeps until the process
- * exits.  It needs 2 * n * min(64, ceil(per_img / 4096)) of them; larger requests
- * (for instance more than 512 images of 256K floats or more) return
+ * exits.  It needs 2 * n * min(64, ceil(per_img / 8192)) of them; larger requests
+ * (for instance more than 1024 images of 256K floats or more) return
  * IDEQ_ERR_ARG.  The first call on a device
  * looks up that array's device address (cudaGetSymbolAddress) with the device
  * current, so make it before any stream capture.  All calls share the array:

@@ -381,8 +381,8 @@ def ideq_solve_graphed(ctx: Context) -> bool:
 def ideq_red_update_noalloc(z, grad_f, grad_g, x, x_new, lam, tau, step_sq=None, x_sq=None):
     """Context-free RED update for callers that cannot allocate device memory.
 
-    x_new = z - tau (grad_f + lam grad_g) with per-image FP64 ||x_new - x||^2 and
-    ||x||^2; every tensor is a caller-owned CUDA tensor (images (n, c, h, w) f32,
+    x_new = z - tau (grad_f + lam grad_g) with per-image ||x_new - x||^2 and ||x||^2
+    (FP64 sums of FP32 partial sums over <= 16 elements); every tensor is a caller-owned CUDA tensor (images (n, c, h, w) f32,
     norms (n,) f64).  Runs on torch's current stream; allocates nothing."""
     import torch
     n = z.shape[0]
