@@ -62,6 +62,14 @@ struct TcArgs {
   double* sumsq;
   const int* skip;  // per image, nonzero: frozen, its tiles are not computed (nullable)
   int* err;
+  // direct epilogue: outputs stored and auxiliary inputs read by the epilogue
+  // threads themselves (NHWC, Cout channels), no staging in shared memory
+  int direct;
+  void* gout0;
+  void* gout1;
+  const void* gaux0;
+  const void* gaux1;
+  const void* gaux2;
 };
 
 struct TcPlan {
@@ -72,6 +80,7 @@ struct TcPlan {
   bool pdl = true;       // launched with programmatic stream serialisation
   bool cg2 = false;      // CTA pairs with two-SM MMAs (clusters of two)
   bool stk = false;      // halo form with stacked vertical taps (sliding row runs)
+  bool direct = false;   // epilogue without shared-memory staging
   bool split64 = false;  // 64-column tiles: epilogue halves on alternate tiles
   int Wt = 0, Ht = 0, tiles_w = 0, tiles_h = 0, tiles_n = 0, nk = 0, cpt = 0;
   dim3 grid;
@@ -214,6 +223,51 @@ constexpr int PANEL = EPI_WARPS * WBOX;  // one staging buffer of one tensor, al
 // the 32 tile rows 32q .. 32q+31 (q = the warp's TMEM lane quadrant) and the 32
 // columns starting at `col`, as a 4-D NHWC box (32 channels x min(Wt, 32) x
 // 32 / min(Wt, 32) pixels), or through the 5-D depth-to-space view for OM_D2S.
+// Direct form of epi_chunk: the auxiliary values of the thread's row come from
+// global memory (read-only for this kernel) and the results go straight to global
+// memory; every pointer is at this row's first column and 16-byte aligned.
+template <typename T, int EPI, int ACT>
+IDEQ_DEV void epi_chunk_g(const float (&v)[32], const T* x0p, const T* x1p, const T* x2p,
+                          T* o1, T* o2) {
+  using Tr = EpiTraits<EPI>;
+  uint4 w0[4], w1[4], w2[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {  // all loads first: one latency for the row
+    if (Tr::naux > 0) w0[c] = __ldg((const uint4*)(x0p + 8 * c));
+    if (Tr::naux > 1) w1[c] = __ldg((const uint4*)(x1p + 8 * c));
+    if (Tr::naux > 2) w2[c] = __ldg((const uint4*)(x2p + 8 * c));
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    float x0[8] = {}, x1[8] = {}, x2[8] = {}, r[8], r2[8] = {};
+    if (Tr::naux > 0) unpack8<T>(w0[c], x0);
+    if (Tr::naux > 1) unpack8<T>(w1[c], x1);
+    if (Tr::naux > 2) unpack8<T>(w2[c], x2);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) r[i] = epi_one<EPI, ACT>(v[8 * c + i], x0[i], x1[i], x2[i], r2[i]);
+    *(uint4*)(o1 + 8 * c) = pack8<T>(r);
+    if (Tr::out2) *(uint4*)(o2 + 8 * c) = pack8<T>(r2);
+  }
+}
+
+template <typename T>
+IDEQ_DEV void epi_apply_g(int epi, int act, const float (&v)[32], const T* x0, const T* x1,
+                          const T* x2, T* o1, T* o2) {
+  switch (epi) {
+    case EP_ACT:
+      if (act == 0)
+        epi_chunk_g<T, EP_ACT, 0>(v, x0, x1, x2, o1, o2);
+      else
+        epi_chunk_g<T, EP_ACT, 1>(v, x0, x1, x2, o1, o2);
+      break;
+    case EP_ADD: epi_chunk_g<T, EP_ADD, 0>(v, x0, x1, x2, o1, o2); break;
+    case EP_MUL: epi_chunk_g<T, EP_MUL, 0>(v, x0, x1, x2, o1, o2); break;
+    case EP_MUL_KEEP: epi_chunk_g<T, EP_MUL_KEEP, 0>(v, x0, x1, x2, o1, o2); break;
+    case EP_DUAL: epi_chunk_g<T, EP_DUAL, 0>(v, x0, x1, x2, o1, o2); break;
+    default: epi_chunk_g<T, EP_STORE, 0>(v, x0, x1, x2, o1, o2); break;
+  }
+}
+
 IDEQ_DEV void epi_tma(bool store, const TcArgs& a, const CUtensorMap* tm, uint32_t sm,
                       const TileCoord& tc, int q, int col, uint32_t bar) {
   const int m0 = 32 * q;
@@ -931,7 +985,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                   nc.n0 + PW * p + colh, bar);
       };
       int aux_issued = 0;
-      if (lane == 0 && a.naux > 0)
+      const bool direct = a.direct != 0;
+      if (lane == 0 && a.naux > 0 && !direct)
         for (; aux_issued < a.nba && aux_issued < npc; ++aux_issued) aux_load(aux_issued);
       int pc = 0;
       bool ok = true;
@@ -943,6 +998,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         tc_fence_after();
         for (int pp = 0; pp < npan && ok; ++pp, ++pc) {
           const int sub = pp / nper, p = pp - sub * nper;
+          if (direct) {  // no staging: TMEM -> registers -> global memory
+            float v[32];
+            tmem_ld32(tmem + (uint32_t)(b * TCOLS + sub * BN + PW * p + colh) +
+                          ((uint32_t)(q * 32) << 16),
+                      v);
+            if (pp == npan - 1) {
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) {
+                if (CG2)
+                  mbar_arrive_remote(mapa_shared(tempty0 + 8 * b, 0));
+                else
+                  mbar_arrive(tempty0 + 8 * b);
+              }
+            }
+            const TileCoord tc = HALO ? halo_coord(a, im, t) : tile_coord(a, im, t, BN, MSUB, sub + tsub0);
+            const int m = 32 * q + lane;
+            const int x = tc.w0 + m % a.Wt, y = tc.h0 + m / a.Wt;
+            if (tc.img < a.n && x < a.W && y < a.H) {
+              const size_t e = (((size_t)tc.img * a.H + y) * a.W + x) * (size_t)a.Cout +
+                               (size_t)(tc.n0 + PW * p + colh);
+              epi_apply_g<T>(a.epi, a.act, v, (const T*)a.gaux0 + e, (const T*)a.gaux1 + e,
+                             (const T*)a.gaux2 + e, (T*)a.gout0 + e, (T*)a.gout1 + e);
+            }
+            continue;
+          }
           const int sb = pc % a.nbo, ab = pc % a.nba;
           if (lane == 0 && pc >= a.nbo) bulk_wait_read(a.nbo - 1);  // staging box sb read out
           __syncwarp();
@@ -1217,10 +1298,33 @@ TcPlan* tc_plan_create(const ConvArgs& a, int op_dt, int epi_dt, std::string* er
                                      : ((size_t)p->ms * 128 + bcta) * RB;
     const size_t resident = p->halo ? bres : 0;
     p->stages = 0;
+    // direct epilogue (halo and streamed forms: full-row tiles whose 64- and 128-column
+    // MMAs keep the shared-memory port busy, so staged epilogue traffic waits): the
+    // epilogue threads read their auxiliary values and store their results in global
+    // memory themselves, and the staging space goes to the ring (IDEQ_TC_DIRECT=0
+    // keeps the staged epilogue)
+    p->direct = (p->halo || p->stream) && a.outmap == OM_IDENT && !img && op_dt != DT_FP8 &&
+                tiling_override("IDEQ_TC_DIRECT", 1) != 0;
+    if (p->direct) {
+      const int min_st = p->halo ? (p->slide ? 5 : 2) : 2;
+      auto total = [&](int k) {
+        return fixed_smem(p->nout, p->naux, 0, 0, k, p->stk ? 8 : 2) + resident + k * stage;
+      };
+      int st = 8;
+      while (st > min_st && total(st) > kMaxSmem) --st;
+      if (total(st) <= kMaxSmem) {
+        p->stages = st;
+        p->nbo = 0;
+        p->nba = 0;
+        p->smem = total(st);
+      } else {
+        p->direct = false;
+      }
+    }
     // short K (depth-to-space, stride-2 and 1x1 layers): the epilogue paces the
     // kernel, so auxiliary boxes are fetched four panels ahead and the ring is
     // held to two stages (measured: 2% on the depth-to-space layers, 57 vs 58 us)
-    if (p->naux > 0 && !p->halo && !p->stream && p->nk <= 4 &&
+    if (!p->stages && p->naux > 0 && !p->halo && !p->stream && p->nk <= 4 &&
         tiling_override("IDEQ_TC_NBA", MAX_NBA) == MAX_NBA) {
       for (int st = 8; st >= 2 && !p->stages; --st) {
         const size_t tot =
@@ -1461,6 +1565,13 @@ cudaError_t launch_conv_tc(const TcPlan* p, const ConvArgs& a, int* err_flag, cu
   t.a_scale = a.a_scale;
   t.w_scale = a.w_scale;
   t.err = err_flag;
+  t.direct = p->direct ? 1 : 0;
+  // unused slots point at the first output (never dereferenced)
+  t.gout0 = a.out;
+  t.gout1 = p->nout > 1 && a.out2 ? a.out2 : a.out;
+  t.gaux0 = p->naux > 0 ? a.aux0 : a.out;
+  t.gaux1 = p->naux > 1 ? a.aux1 : a.out;
+  t.gaux2 = p->naux > 2 ? a.aux2 : a.out;
   if (p->epi_dt == DT_F16) return launch_typed<__half>(p, t, st);
   return launch_typed<__nv_bfloat16>(p, t, st);
 }
