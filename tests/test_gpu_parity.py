@@ -728,3 +728,28 @@ def test_grad_reg_stacked_tap_convs_match_nine_tap(name, over, prec, monkeypatch
     for i in range(zz.shape[0]):
         ref, gv = nets.grad_g(net, zz[i])
         assert rel(out["1"][i], ref) < (1e-2 if prec == "bf16" else 2e-3)
+
+
+@pytest.mark.parametrize("name,over,prec", [("C1a", dict(n=2, h=40, w=128), "fp16"),
+                                            ("C1a", dict(n=1, h=136, w=200), "bf16")])
+def test_grad_reg_direct_epilogue_matches_staged(name, over, prec, monkeypatch):
+    """The full-row (halo and streamed) 3x3 layers with the direct epilogue (results
+    and auxiliary inputs through global memory from the epilogue threads) against
+    the staged epilogue (shared-memory boxes and TMA stores, IDEQ_TC_DIRECT=0) on the
+    same inputs: the same accumulators through the same epilogue arithmetic, so the
+    outputs agree to the last bit; 200 columns leave a ragged second strip whose
+    pixels past the image must not be stored."""
+    cfg, wl, net, ops, ys = setup(name, **over)
+    b = B()
+    z = torch.tensor(np.random.default_rng(13).uniform(0, 1, ys.shape).astype(np.float32),
+                     device="cuda")
+    out = {}
+    for d in ("1", "0"):
+        monkeypatch.setenv("IDEQ_TC_DIRECT", d)
+        ctx = ctx_for(cfg, wl, PREC[prec]())
+        out[d] = to_np(b.ideq_grad_reg(ctx, z))
+    assert rel(out["1"], out["0"]) < 1e-7, rel(out["1"], out["0"])
+    zz = to_np(z)
+    for i in range(zz.shape[0]):
+        ref, gv = nets.grad_g(net, zz[i])
+        assert rel(out["1"][i], ref) < (1e-2 if prec == "bf16" else 2e-3)
