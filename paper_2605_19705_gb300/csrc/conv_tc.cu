@@ -1284,11 +1284,12 @@ TcPlan* tc_plan_create(const ConvArgs& a, int op_dt, int epi_dt, std::string* er
     // MMA cycle; this pays where the copies bound the main loop, i.e. long K.
     // Measured on 8 x RGB 256^2 (C1a): 256- and 512-channel 3x3 layers 12-14%
     // faster as pairs; the streamed 128-channel layers and the short-K stride-2 and
-    // depth-to-space layers slower.  IDEQ_TC_CG2=1 pairs every eligible layer, 0 none.
+    // depth-to-space layers slower.  IDEQ_TC_CG2=1 pairs every eligible layer, 2 the
+    // long-K and the streamed ones, 0 none.
     const int cg2_mode = tiling_override("IDEQ_TC_CG2", -1);
     p->cg2 = !p->halo && !p->nw && op_dt != DT_FP8 && (p->bn == 128 || p->bn == 256) &&
              p->ms == 1 && !img && cg2_mode != 0 &&
-             (cg2_mode == 1 || (!p->stream && p->nk >= 32));
+             (cg2_mode == 1 || (!p->stream && p->nk >= 32) || (cg2_mode == 2 && p->stream));
     const size_t bcta = p->cg2 ? (size_t)p->bn / 2 : (size_t)p->bn;  // rows of B per CTA
     // shared memory: ring depth and staging buffers, preferring a deep ring
     // (halo: >= 5 row boxes, three in use and two in flight; else >= 3 stages),
