@@ -188,25 +188,26 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
+    {  // the whole warp, converged: one elected lane issues (as in the conv kernel)
       // A and B both MN-major (bits 15 and 16 of the instruction descriptor)
       const uint32_t idesc = umma_idesc_16(128, a.bn, Fmt<T>::v) | (1u << 15) | (1u << 16);
-      int g = 0;
+      int rs = 0;  // ring slot and phase, advanced without division
+      uint32_t rph = 0u;
       bool ok = true;
       for (int i = 0; i < my_units && ok; ++i) {
         int sp, nti, mti, q0, q1;
         unit_of(i, &sp, &nti, &mti);
         box_range(sp, &q0, &q1);
         const int b = i & 1, u = i >> 1;
-        if (u > 0 && !mbar_wait(tempty0 + 8 * b, (u - 1) & 1, a.err, 23)) {
+        if (u > 0 && !mbar_wait_warp(tempty0 + 8 * b, (u - 1) & 1, a.err, 23)) {
           ok = false;
           break;
         }
         tc_fence_after();
         const uint32_t td = tmem + (uint32_t)(b * a.bn);
         for (int q = q0; q < q1; ++q) {
-          const int s = g % ST, ph = g / ST;
-          if (!mbar_wait(full0 + 8 * s, ph & 1, a.err, 24)) {
+          const int s = rs;
+          if (!mbar_wait_warp(full0 + 8 * s, rph, a.err, 24)) {
             ok = false;
             break;
           }
@@ -217,16 +218,19 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
             const uint64_t ad = umma_desc_mn(base + (uint32_t)(32 * a.ca * kk), a.ca);
             const uint64_t bd =
                 umma_desc_mn(base + (uint32_t)(na * ABOX + 32 * a.cb * kk), a.cb);
-            umma<T>(td, ad, bd, idesc, (q > q0 || kk > 0) ? 1u : 0u);
+            umma_el<T>(td, ad, bd, idesc, (q > q0 || kk > 0) ? 1u : 0u);
           }
-          umma_commit(empty0 + 8 * s);
-          ++g;
+          umma_commit_el(empty0 + 8 * s);
+          if (++rs == ST) {
+            rs = 0;
+            rph ^= 1u;
+          }
         }
-        if (ok) umma_commit(tfull0 + 8 * b);
+        if (ok) umma_commit_el(tfull0 + 8 * b);
       }
       if (!ok) {  // let every issued MMA finish before TMEM is released
-        umma_commit(drain);
-        mbar_wait(drain, 0, a.err, 25);
+        umma_commit_el(drain);
+        mbar_wait_warp(drain, 0, a.err, 25);
       }
     }
   } else {
