@@ -1,6 +1,8 @@
 // Internal declarations of the i-DEQ CUDA library (not part of the C ABI).
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <string>
@@ -62,10 +64,13 @@ struct ConvArgs {
   // per-image flags (device, n ints; nullable): nonzero = the image is frozen in a
   // solve and its outputs are not needed, so the launch may skip its work
   const int* skip = nullptr;
+  // algorithmic K when the GEMM's K is padded (image-side 3x3 convs run as one
+  // 32-wide K chunk of im2col taps: 9 c of them carry work), else 0
+  int k_algo = 0;
   IDEQ_HD int N() const { return outmap == OM_D2S ? 4 * Cout : Cout; }
   IDEQ_HD int K() const { return mode == CM_CONV3 ? 9 * Cin : (mode == CM_DOWN ? 4 * Cin : Cin); }
   IDEQ_HD long long M() const { return (long long)n * H * W; }
-  IDEQ_HD double flops() const { return 2.0 * (double)M() * N() * K(); }
+  IDEQ_HD double flops() const { return 2.0 * (double)M() * N() * (k_algo > 0 ? k_algo : K()); }
 };
 
 // Element types of NHWC activations: DT_F32, DT_BF16 or DT_F16 (common.cuh);
@@ -92,6 +97,15 @@ cudaError_t launch_conv_tc(const TcPlan* p, const ConvArgs& a, int* err_flag, cu
 
 // Weight forms: GEMM B matrices from the PyTorch-layout weights.
 enum WForm { WF_CONV3_FWD = 0, WF_CONV3_DGRAD, WF_DOWN_FWD, WF_DOWN_DGRAD, WF_UP_FWD, WF_UP_DGRAD };
+
+// Image-side 3x3 convs on the tensor cores: im2col of the 9 c taps of an f32
+// planar (NCHW) image into one 32-channel 16-bit NHWC row per pixel (k = tap c + ci,
+// zero past 9 c and outside the image; frozen images skipped), and the GEMM weights
+// [N][9 c] widened to [N][32] with zeros, in both 16-bit types.
+cudaError_t launch_im2col3(int n, int c, int H, int W, const float* in, const int* skip,
+                           void* out, int out_dt, cudaStream_t st);
+cudaError_t launch_i2c_weights(const float* w32, int N, int K, __half* h, __nv_bfloat16* b,
+                               cudaStream_t st);
 cudaError_t launch_weight_form(int form, int cin, int cout, const float* src, float* dst_f32,
                                void* dst_bf16, void* dst_f16, cudaStream_t st);
 void weight_form_dims(int form, int cin, int cout, int* N, int* K);  // the form's [N][K]

@@ -1064,6 +1064,69 @@ cudaError_t launch_adam(long long n, float* p, const float* g, float* m, float* 
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- im2col of the
+// image-side 3x3 convs: one thread per pixel writes its 32-entry row (9 c taps,
+// k = (3 dy + dx) c + ci, then zeros) as four 16-byte stores.
+template <typename T> IDEQ_DEV T to16(float v);
+template <> IDEQ_DEV __half to16<__half>(float v) { return __float2half_rn(v); }
+template <> IDEQ_DEV __nv_bfloat16 to16<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+template <typename T>
+__global__ void __launch_bounds__(256) im2col3_kernel(int c, int H, int W,
+                                                      const float* __restrict__ in,
+                                                      const int* __restrict__ skip,
+                                                      T* __restrict__ out) {
+  const int b = blockIdx.y;
+  if (skip && skip[b]) return;  // frozen image of a solve: not needed
+  const int p = blockIdx.x * 256 + threadIdx.x;
+  if (p >= H * W) return;
+  const int y = p / W, x = p - y * W;
+  const float* img = in + (size_t)b * c * H * W;
+  __align__(16) T row[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) row[k] = to16<T>(0.f);
+  for (int t = 0; t < 9; ++t) {
+    const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
+    const bool inside = yy >= 0 && yy < H && xx >= 0 && xx < W;
+    for (int ci = 0; ci < c; ++ci) {
+      const int k = t * c + ci;
+      if (k < 32) row[k] = to16<T>(inside ? __ldg(img + ((size_t)ci * H + yy) * W + xx) : 0.f);
+    }
+  }
+  uint4* o = (uint4*)(out + ((size_t)b * H * W + p) * 32);
+  const uint4* r = (const uint4*)row;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) o[q] = r[q];
+}
+
+cudaError_t launch_im2col3(int n, int c, int H, int W, const float* in, const int* skip,
+                           void* out, int out_dt, cudaStream_t st) {
+  if (9 * c > 32 || (out_dt != DT_F16 && out_dt != DT_BF16)) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)((H * W + 255) / 256), (unsigned)n);
+  if (out_dt == DT_F16)
+    im2col3_kernel<__half><<<grid, 256, 0, st>>>(c, H, W, in, skip, (__half*)out);
+  else
+    im2col3_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(c, H, W, in, skip, (__nv_bfloat16*)out);
+  return cudaGetLastError();
+}
+
+__global__ void i2c_weights_kernel(const float* __restrict__ w32, int N, int K,
+                                   __half* __restrict__ h, __nv_bfloat16* __restrict__ bw) {
+  const int i = blockIdx.x * 256 + threadIdx.x;
+  if (i >= N * 32) return;
+  const int nn = i / 32, k = i - nn * 32;
+  const float v = k < K ? w32[(size_t)nn * K + k] : 0.f;
+  h[i] = __float2half_rn(v);
+  bw[i] = __float2bfloat16_rn(v);
+}
+
+cudaError_t launch_i2c_weights(const float* w32, int N, int K, __half* h, __nv_bfloat16* b,
+                               cudaStream_t st) {
+  if (K > 32) return cudaErrorInvalidValue;
+  i2c_weights_kernel<<<(N * 32 + 255) / 256, 256, 0, st>>>(w32, N, K, h, b);
+  return cudaGetLastError();
+}
+
 }  // namespace ideq
 
 // ===================================================================== FP8 forms

@@ -10,6 +10,7 @@
 #include "net.h"
 
 #include <algorithm>
+#include <cstdlib>
 
 namespace ideq {
 
@@ -139,6 +140,23 @@ bool NetWeights::build(const ideq_net_desc& d, std::string* err) {
       *err = "cudaMemset(weight forms) failed";
       return false;
     }
+    // image-side 3x3 directions with K = 9 x (image channels) <= 32: one K chunk
+    if (l.fwd_form == WF_CONV3_FWD && Kf <= 32) {
+      l.i2c_fwd_h = (__half*)al((size_t)Nf * 32 * 2);
+      l.i2c_fwd_b = (__nv_bfloat16*)al((size_t)Nf * 32 * 2);
+      if (!l.i2c_fwd_h || !l.i2c_fwd_b) {
+        *err = "cudaMalloc(weight forms) failed";
+        return false;
+      }
+    }
+    if (l.dg_form == WF_CONV3_DGRAD && Kd <= 32) {
+      l.i2c_dg_h = (__half*)al((size_t)Nd * 32 * 2);
+      l.i2c_dg_b = (__nv_bfloat16*)al((size_t)Nd * 32 * 2);
+      if (!l.i2c_dg_h || !l.i2c_dg_b) {
+        *err = "cudaMalloc(weight forms) failed";
+        return false;
+      }
+    }
     int N, K;
     if (l.cin >= kFp8MinChannels) {
       weight_form_dims(l.fwd_form, l.cin, l.cout, &N, &K);
@@ -171,6 +189,16 @@ cudaError_t NetWeights::reform(cudaStream_t st) {
                                   l.dg32, l.dg16, l.dgh, st);
     if (e != cudaSuccess) return e;
     int N, K;
+    if (l.i2c_fwd_h) {
+      weight_form_dims_padded(l.fwd_form, l.cin, l.cout, l.pcin, l.pcout, &N, &K);
+      if ((e = launch_i2c_weights(l.fwd32, N, K, l.i2c_fwd_h, l.i2c_fwd_b, st)) != cudaSuccess)
+        return e;
+    }
+    if (l.i2c_dg_h) {
+      weight_form_dims_padded(l.dg_form, l.cin, l.cout, l.pcin, l.pcout, &N, &K);
+      if ((e = launch_i2c_weights(l.dg32, N, K, l.i2c_dg_h, l.i2c_dg_b, st)) != cudaSuccess)
+        return e;
+    }
     if (l.fwd8) {
       weight_form_dims(l.fwd_form, l.cin, l.cout, &N, &K);
       if ((e = launch_weight_fp8(l.fwd32, N, K, l.fwd8, l.fwd8s, st)) != cudaSuccess) return e;
@@ -222,6 +250,49 @@ struct Builder {
   }
 
   // Append one conv of `layer` (forward or input-gradient form).
+  // The image-side input conv (3x3, f32 planar image in, 16-bit NHWC features out,
+  // K = 9 c <= 32) on the tensor cores: an im2col pass writes one 32-channel row per
+  // pixel, then a 1x1 narrow-row tcgen05 conv with the [N][32] weight form.  False
+  // (step unchanged) where that form or the tensor-core path does not apply.
+  bool i2c_step(Step& s, const Layer& L, bool dgrad, int adt) {
+    ConvArgs& a = s.a;
+    if (adt == DT_F32 || !a.in_nchw || a.out_nchw || a.mode != CM_CONV3 ||
+        a.outmap != OM_IDENT || 9 * a.Cin > 32)
+      return false;
+    // read at plan build: IDEQ_IMG_TC=1 selects this form; by default the SIMT edge
+    // kernels run these layers (this form's speed is not measured yet)
+    const char* env = std::getenv("IDEQ_IMG_TC");
+    const bool on = env && *env && std::atoi(env) == 1;
+    const __half* wh = dgrad ? L.i2c_dg_h : L.i2c_fwd_h;
+    const __nv_bfloat16* wb = dgrad ? L.i2c_dg_b : L.i2c_fwd_b;
+    if (!on || !wh || !wb) return false;
+    ConvArgs b = a;
+    b.mode = CM_PIX;
+    b.Cin = 32;
+    b.in_nchw = 0;
+    b.k_algo = 9 * a.Cin;
+    b.wB = adt == DT_F16 ? (const void*)wh : (const void*)wb;
+    const long long px = (long long)P->n * a.H * a.W;
+    b.in = reinterpret_cast<void*>(1);  // placeholder for the support test
+    if (!tc_supported(b, adt)) return false;
+    void* buf = P->alloc((size_t)px * 32 * 2);
+    if (!buf) return false;
+    b.in = buf;
+    std::string e;
+    TcPlan* tc = tc_plan_create(b, adt, adt, &e);
+    if (!tc) return false;
+    s.i2c_px = px;
+    s.i2c_src = (const float*)a.in;
+    s.i2c_dst = buf;
+    s.i2c_c = a.Cin;
+    s.i2c_H = a.H;
+    s.i2c_W = a.W;
+    s.in_dt = adt;
+    s.tc = tc;
+    a = b;
+    return true;
+  }
+
   void conv(std::vector<Step>& list, const Layer& L, bool dgrad, int mode, int outmap, int gh,
             int gw, int cin, int cout, const void* in, void* out, int epi,
             const void* aux0 = nullptr, void* out2 = nullptr, bool in_nchw = false,
@@ -289,6 +360,7 @@ struct Builder {
         *err = e;
         ok = false;
       }
+    } else if (i2c_step(s, L, dgrad, adt)) {  // image -> feature side, as im2col + 1x1
     } else if (adt != DT_F32 && !in_nchw && tc_supported(a)) {  // incl. feature -> image
       if (adt == DT_F16)
         a.wB = dgrad ? (const void*)L.dgh : (const void*)L.fwdh;
@@ -517,6 +589,12 @@ cudaError_t run_steps(const std::vector<Step>& steps, int* err_flag, cudaStream_
           cudaSuccess)
         return e;
       if (launches) *launches += 2;
+    }
+    if (s.i2c_px > 0) {  // im2col rows of the image-side input conv
+      if ((e = launch_im2col3(s.a.n, s.i2c_c, s.i2c_H, s.i2c_W, s.i2c_src, s.a.skip, s.i2c_dst,
+                              s.in_dt, st)) != cudaSuccess)
+        return e;
+      if (launches) *launches += 1;
     }
     if (s.tc) {
       const bool p = prof && prof->on;

@@ -34,6 +34,12 @@ struct Layer {
   float* fwd8s = nullptr;
   uint8_t* dg8 = nullptr;
   float* dg8s = nullptr;
+  // [N][32] 16-bit forms of 3x3 directions whose K = 9 x (image channels) <= 32:
+  // the image-side input convs (head forward, tail input gradient) as one K chunk
+  __half* i2c_fwd_h = nullptr;
+  __nv_bfloat16* i2c_fwd_b = nullptr;
+  __half* i2c_dg_h = nullptr;
+  __nv_bfloat16* i2c_dg_b = nullptr;
 };
 
 constexpr int kFp8MinChannels = 256;  // convs with at least this many input channels
@@ -68,6 +74,13 @@ struct Step {
   uint8_t* q_dst = nullptr;
   float* q_amax = nullptr;
   float* q_scale = nullptr;
+  // image-side input convs on the tensor cores (i2c_px > 0): the f32 planar image
+  // i2c_src (i2c_c channels, i2c_H x i2c_W) is first written as im2col rows into
+  // i2c_dst, the conv's 32-channel input
+  long long i2c_px = 0;
+  const float* i2c_src = nullptr;
+  void* i2c_dst = nullptr;
+  int i2c_c = 0, i2c_H = 0, i2c_W = 0;
 };
 
 // Execution plan for one (n, H, W, precision): activation buffers and the

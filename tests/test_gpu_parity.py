@@ -753,3 +753,31 @@ def test_grad_reg_direct_epilogue_matches_staged(name, over, prec, monkeypatch):
     for i in range(zz.shape[0]):
         ref, gv = nets.grad_g(net, zz[i])
         assert rel(out["1"][i], ref) < (1e-2 if prec == "bf16" else 2e-3)
+
+
+@pytest.mark.parametrize("name,over,prec", [("C1a", dict(n=2, h=40, w=56), "fp16"),
+                                            ("C1a", dict(n=1, h=136, w=200), "bf16"),
+                                            ("C5", dict(n=2, h=64, w=64), "fp16")])
+def test_grad_reg_image_side_tensor_core_convs_match_simt(name, over, prec, monkeypatch):
+    """The image-side input convs (head forward, tail input gradient: 3x3 from c image
+    channels to the first features) as im2col rows of the 9 c taps (one 32-channel K
+    chunk, zero past 9 c and outside the image) and a 1x1 tcgen05 conv
+    (IDEQ_IMG_TC=1), against the SIMT edge kernels on the same inputs and against the
+    oracle; RGB and the 2-channel MRI net, ragged sizes.  The tensor-core form rounds
+    the f32 image and the head weights to the 16-bit operand type (unit roundoff 2^-11
+    FP16, 2^-9 BF16: measured 2.1e-3 between the BF16 forms at 136 x 200), so the two
+    forms are held to the 16-bit tolerances of the oracle comparisons."""
+    cfg, wl, net, ops, ys = setup(name, **over)
+    b = B()
+    z = torch.tensor(np.random.default_rng(17).uniform(0, 1, ys.shape).astype(np.float32),
+                     device="cuda")
+    out = {}
+    for v in ("1", "0"):
+        monkeypatch.setenv("IDEQ_IMG_TC", v)
+        ctx = ctx_for(cfg, wl, PREC[prec]())
+        out[v] = to_np(b.ideq_grad_reg(ctx, z))
+    assert rel(out["1"], out["0"]) < (1e-2 if prec == "bf16" else 2e-3), rel(out["1"], out["0"])
+    zz = to_np(z)
+    for i in range(zz.shape[0]):
+        ref, gv = nets.grad_g(net, zz[i])
+        assert rel(out["1"][i], ref) < (1e-2 if prec == "bf16" else 2e-3)
