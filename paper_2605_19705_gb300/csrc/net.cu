@@ -273,8 +273,7 @@ struct Builder {
     b.k_algo = 9 * a.Cin;
     b.wB = adt == DT_F16 ? (const void*)wh : (const void*)wb;
     const long long px = (long long)P->n * a.H * a.W;
-    b.in = reinterpret_cast<void*>(1);  // placeholder for the support test
-    if (!tc_supported(b, adt)) return false;
+    if (!tc_supported(b, adt)) return false;  // (b.in is replaced by the im2col rows below)
     void* buf = P->alloc((size_t)px * 32 * 2);
     if (!buf) return false;
     b.in = buf;
